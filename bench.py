@@ -1,0 +1,336 @@
+"""Benchmark of the temporal 3-path sampling estimator on one GB300.
+
+A step is one pass of the whole hot path over the resident graph: path
+weights and their exact prefix sum with the sampling index (Claim 1, Alg. 1),
+then k sampled 3-paths with CheckMotif / ListCount and the reduction of the
+estimate (Alg. 2-5).  The workload is the 20M-edge Chung-Lu graph (n = 1M,
+power-law exponent 2.1, maximum degree ~1e5, 30% multi-edges, bursty times
+over 1e8 s) with the path+chord motif a->b, b->c, c->d, a->d (in that time
+order), delta = 3600 s and k = 1e8 samples per step.
+
+Printed: one JSON line with samples/s (device, graph resident), the same
+metric end to end through tc_estimate_from_host with pinned host buffers, the
+roofline of the dominant kernel (the sampler), the oracle's CPU rate and the
+SM clocks seen during the timed region.
+
+``--impl reference`` times the CPU oracle instead (the reference arm).
+Under torchrun each rank runs the full path on its own GPU over its own
+sample-id range (weak scaling); the integer sums merge exactly afterwards.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "temporal-path samples/sec"
+UNIT = "samples/s"
+SECTOR = 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--samples", type=int, default=None, help="samples per step (default: the config's k)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def workload():
+    from paper_2409_08975_gb300 import synth
+    return synth.mid()
+
+
+def cpu_baseline(cfg, k_total, sample_k=300_000):
+    """The oracle as it stands on the host cores: weights and prefix over the
+    whole graph timed in full, the sampler timed on sample_k samples and
+    scaled to k_total samples per step."""
+    import oracle
+    og = oracle.build_csr(cfg["n"], cfg["src"], cfg["dst"], cfg["t"], sort="lexsort")
+    plan = oracle.compile_motif(cfg["motif"])
+    t0 = time.perf_counter()
+    w = oracle.path_weights(og, plan, cfg["delta"])["w"]
+    pre = oracle.prefix_sum(w)
+    t_prep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.sample_run(og, plan, cfg["delta"], pre, sample_k, 0, 0)
+    t_samp = time.perf_counter() - t0
+    per = t_samp / sample_k
+    value = k_total / (t_prep + per * k_total)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "serial C oracle: weights+prefix over all %d edges timed in full (%.2f s); sampler timed "
+                      "on %d samples (%.2f s) and scaled to k=%d per step" % (og.m, t_prep, sample_k, t_samp,
+                                                                               k_total)}, og, plan, pre
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg = workload()
+    k = args.samples or cfg["k"]
+    import oracle
+    og = oracle.build_csr(cfg["n"], cfg["src"], cfg["dst"], cfg["t"], sort="lexsort")
+    plan = oracle.compile_motif(cfg["motif"])
+    t0 = time.perf_counter()
+    pre = oracle.prefix_sum(oracle.path_weights(og, plan, cfg["delta"])["w"])
+    t_prep = time.perf_counter() - t0
+    step_k = 100_000
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.sample_run(og, plan, cfg["delta"], pre, step_k, 0, s * step_k)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    per = sum(times) / (len(times) * step_k)
+    step_s = t_prep + per * k
+    value = k / step_s
+    sample = ("serial C oracle on the host: weights+prefix over all %d edges once (%.2f s), each step %d samples "
+              "(%.3f s mean), scaled to k=%d samples per step" % (og.m, t_prep, step_k, per * step_k, k))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": config_dict(cfg, k, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def config_dict(cfg, k, world):
+    return {"workload": "mid: Chung-Lu n=1M m=20M gamma=2.1 max_deg~1e5 30% multi-edges, bursty times over 1e8 s; "
+                        "motif a->b,b->c,c->d,a->d (path+chord), delta=3600, k=1e8 samples per step",
+            "n": int(cfg["n"]), "m": int(len(cfg["src"])), "motif": "path+chord", "delta": int(cfg["delta"]),
+            "k": int(k), "seed": 0, "parallelism": "dp%d (sample-id ranges)" % world,
+            "l2": "inputs larger than L2 (graph + index ~2.4 GB resident)"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2409_08975_gb300 import _build, tc
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    tc.lib()
+
+    cfg = workload()
+    k = args.samples or cfg["k"]
+    n, m, delta = cfg["n"], len(cfg["src"]), cfg["delta"]
+    stream = torch.cuda.current_stream()
+    mot = tc.make_motif(cfg["motif"])
+
+    src_d = torch.from_numpy(cfg["src"]).cuda()
+    dst_d = torch.from_numpy(cfg["dst"]).cuda()
+    t_d = torch.from_numpy(cfg["t"]).cuda()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    g = tc.tc_build_temporal_csr(n, src_d, dst_d, t_d)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    csr_ms = ev0.elapsed_time(ev1)
+    del src_d, dst_d, t_d
+
+    wts = tc.alloc_weights(g)
+    offset0 = rank * k * 1000
+
+    def step(i, sample_events=None):
+        tc.tc_path_weights(g, mot, delta, out=wts, want_W=False)
+        if sample_events is not None:
+            sample_events[0].record(stream)
+        r = tc.tc_sample_estimate(g, mot, delta, wts, k, seed=0, offset=offset0 + i * k)
+        if sample_events is not None:
+            sample_events[1].record(stream)
+        return r
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = tc.tc_kernel_launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    results = []
+    for i in range(args.steps):
+        results.append(step(args.warmup + i, pairs[i]))
+    end.record(stream)
+    torch.cuda.synchronize()
+    launches = tc.tc_kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * k / (ms_per_step / 1e3)
+    sampler_ms = statistics.mean(a.elapsed_time(b) for a, b in pairs)
+
+    # weights-only timing (the HBM-bound kernels), after the timed region
+    wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in wev:
+        a.record(stream)
+        tc.tc_path_weights(g, mot, delta, out=wts, want_W=False)
+        b.record(stream)
+    torch.cuda.synchronize()
+    weights_ms = statistics.median(a.elapsed_time(b) for a, b in wev)
+
+    r0 = results[-1]
+    checked_frac = r0["checked"] / max(r0["k"], 1)
+    # sampler bytes per sample: guide entry, prefix entry, edge record, e1 and
+    # e3 records (5 sectors); a checked path adds the pair list lookup
+    # (pair_off, pair_dst, pair_eoff, pair_t: 4 sectors)
+    bytes_per_sample = SECTOR * (5 + 4 * checked_frac)
+    peak, peak_kind = load_peaks()
+    achieved = bytes_per_sample * k / (sampler_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_sample (sampler, Alg. 2-4)", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_sample": bytes_per_sample, "sampler_ms": sampler_ms}
+    weights_bytes = 64 * m + 16 * m + 4 * (2 ** max(1, (m - 1).bit_length()))
+    weights = {"ms": weights_ms, "bytes": weights_bytes,
+               "achieved_gbs": weights_bytes / (weights_ms / 1e3) / 1e9,
+               "frac": weights_bytes / (weights_ms / 1e3) / 1e9 / peak}
+
+    # end to end through the host entry point, pinned host buffers
+    src_h = torch.from_numpy(cfg["src"]).pin_memory()
+    dst_h = torch.from_numpy(cfg["dst"]).pin_memory()
+    t_h = torch.from_numpy(cfg["t"]).pin_memory()
+    e2e_times = []
+    for i in range(1 + args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tc.tc_estimate_from_host(n, src_h, dst_h, t_h, mot, delta, k, seed=0)
+        dt = time.perf_counter() - t0
+        if i > 0:
+            e2e_times.append(dt)
+    e2e_s = statistics.mean(e2e_times)
+    # host->device: the three edge arrays; device->host: the id/time check
+    # (4 + 16 B), the pair count (4 B), W and the error word (12 B), the sums (56 B)
+    e2e = {"value": world * k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * m, "d2h_bytes_per_step": 92,
+           "ms_per_step": e2e_s * 1e3}
+
+    base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        base = cpu_baseline(cfg, k)[0]
+
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_dict(cfg, k, world),
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+            "cpu_baseline": base, "csr_build_ms": csr_ms, "weights": weights,
+            "estimate": {"W": r0["W"], "estimate": r0["estimate"], "std_err": r0["std_err"], "hits": r0["hits"],
+                         "checked": r0["checked"]},
+        }))
+    g.destroy()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * tc.h -- C ABI of the GB300 temporal 3-path sampling library.
+ *
+ * Implements the estimator of Pu, Wang, Seshadhri, Aiken, Ganesh, Kolda,
+ * Phillips, "Accurate and Fast Estimation of Temporal Motifs using Path
+ * Sampling" (ICDM 2024):
+ *   - input: a directed temporal multigraph of edges (u, v, t)      (Sec. I-A)
+ *   - motif M = (H, pi, delta) on four vertices                     (Def. 1, 2)
+ *   - path weights w_e = product of windowed degrees               (Claim 1, Alg. 1)
+ *   - sampling of delta-centered 3-paths proportional to w_e       (Alg. 2, Lemma 1)
+ *   - CheckMotif / ListCount completion count per sampled path     (Alg. 3, Alg. 4)
+ *   - estimate C_hat = (sum X / k) * W                             (Alg. 5, Claim 2)
+ *
+ * Conventions for every call:
+ *   - "d_" pointers are CUDA device pointers, "h_" pointers host pointers.
+ *     Device pointers passed in are borrowed: the library never keeps them
+ *     after the call returns.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; calls that return host values synchronise it.
+ *   - Library objects (tc_graph) own device memory taken with
+ *     cudaMallocAsync on the creating stream; *_destroy frees it.
+ *   - No C++ exception crosses the ABI.  Every call returns a tc_status; on
+ *     failure tc_last_error() returns a message for the calling thread.
+ *   - Conditions detected inside kernels (an overflow of the 64-bit counts,
+ *     a vertex id out of range, an exhausted RNG rejection loop) are collected
+ *     in a device error word and returned as a status at the next point where
+ *     the call synchronises.
+ *   - Integer counts are exact: weights, prefix sums and per-sample counts are
+ *     uint64; the sum of squares is 128 bits.  FP64 is used only for the final
+ *     estimate and its standard error, on the host.
+ *   - Limits: 0 <= m < 2^32 - 1 edges, 1 <= n < 2^31 vertices, delta >= 0.
+ *     Windows t - delta and t + delta saturate at the int64 range.
+ *
+ * Edge orders (fixed by this ABI, needed to read back positions):
+ *   canonical order = out-lists: edges sorted by (src, t, input index)
+ *   in-lists        = edges sorted by (dst, t, input index)
+ *   pair lists      = edges sorted by (src, dst, t, input index)
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TC_OK = 0,
+  TC_ERR_INVALID_ARG = 1,      /* bad size, pointer, id, motif or mismatched index */
+  TC_ERR_OOM = 2,              /* device allocation failed */
+  TC_ERR_OVERFLOW = 3,         /* a uint64 count (W, sum of X, X) overflowed */
+  TC_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+  TC_ERR_UNSUPPORTED_MOTIF = 5,/* no anchor 3-path containing edge 0 */
+  TC_ERR_RNG_EXHAUSTED = 6,    /* 64 rejected draws in a row (probability ~0) */
+  TC_ERR_TIMEOUT = 7,          /* a bounded device wait gave up */
+  TC_ERR_BOUNDS = 8            /* a device index check failed */
+} tc_status;
+
+/* Opaque, device-resident temporal graph: out-, in- and pair-lists. */
+typedef struct tc_graph tc_graph;
+
+#define TC_MAX_MOTIF_EDGES 16
+#define TC_WINDOW_STRICT 0 /* end edges strictly before/after the middle (Def. 5) */
+#define TC_WINDOW_CLOSED 1 /* closed windows [t-delta,t], [t,t+delta] (Claim 1)  */
+
+/*
+ * Temporal motif M = (H, pi, delta) without delta (Def. 1).  Edge i of H runs
+ * from vertex label src[i] to dst[i] (labels 0..3, all four used, no
+ * self-loops) and has time rank i: the permutation pi is the identity on the
+ * listed order.  anchor = {e1, middle, e3} motif edge indices forces the
+ * anchor 3-path (it must contain edge 0); {-1,-1,-1} selects it by the rule
+ * of Alg. 5: among the 3-paths over the four vertices that contain edge 0,
+ * the one whose sorted triple of ranks is lexicographically smallest.
+ */
+typedef struct {
+  int32_t num_edges;                 /* 3 .. TC_MAX_MOTIF_EDGES */
+  int8_t src[TC_MAX_MOTIF_EDGES];
+  int8_t dst[TC_MAX_MOTIF_EDGES];
+  int32_t anchor[3];
+  int32_t window;                    /* TC_WINDOW_STRICT or TC_WINDOW_CLOSED */
+} tc_motif;
+
+/* Result of a sampling run (Alg. 5). */
+typedef struct {
+  uint64_t W;          /* total path weight W_delta (Def. 6) */
+  uint64_t k;          /* samples drawn */
+  uint64_t sum_x;      /* sum over samples of X = CheckMotif(P) */
+  uint64_t sum_x2_lo;  /* sum of X^2, low 64 bits */
+  uint64_t sum_x2_hi;  /* sum of X^2, high 64 bits */
+  uint64_t hits;       /* samples with X > 0 */
+  uint64_t checked;    /* samples whose path spans four vertices with the anchor's
+                          time order and span <= delta (reached the list lookups) */
+  double estimate;     /* C_hat = sum_x * W / k (exact integer division, then FP64) */
+  double std_err;      /* W * sqrt(s^2 / k), s^2 the unbiased sample variance of X */
+} tc_estimate;
+
+typedef struct {
+  int64_t n, m;        /* vertices, edges */
+  int64_t num_pairs;   /* distinct (src, dst) pairs */
+  int64_t t_min, t_max;
+} tc_graph_info;
+
+/* Arrays of a graph that tc_graph_copy can export (for inspection and tests). */
+typedef enum {
+  TC_ARRAY_OUT_OFF = 0,   /* uint32[n+1]   out-list offsets per vertex            */
+  TC_ARRAY_OUT_EDGES = 1, /* {int32 src, int32 dst, int64 t}[m], canonical order  */
+  TC_ARRAY_EDGE_PERM = 2, /* uint32[m]     canonical position -> input index      */
+  TC_ARRAY_IN_OFF = 3,    /* uint32[n+1]   in-list offsets per vertex             */
+  TC_ARRAY_IN_EDGES = 4,  /* {int32 src, uint32 canonical, int64 t}[m], in order   */
+  TC_ARRAY_PAIR_OFF = 5,  /* uint32[n+1]   first pair index per source vertex      */
+  TC_ARRAY_PAIR_DST = 6,  /* int32[P]      destination of each pair, by (src, dst) */
+  TC_ARRAY_PAIR_EOFF = 7, /* uint32[P+1]   first pair-list position per pair       */
+  TC_ARRAY_PAIR_T = 8,    /* int64[m]      times in pair order                     */
+  TC_ARRAY_PAIR_EID = 9   /* uint32[m]     pair position -> canonical position     */
+} tc_array;
+
+/*
+ * Build the time-sorted out-, in- and pair-lists of a temporal graph
+ * (Sec. III: adjacency lists sorted by timestamp; Sec. III-B: the lists
+ * L_{u,v} of all u->v edges).
+ *   n          number of vertices; ids must lie in [0, n)
+ *   m          number of edges (0 allowed)
+ *   d_src, d_dst, d_t  device arrays of m entries in input order (borrowed)
+ *   *out       receives the new graph; destroy it with tc_graph_destroy
+ * Errors: TC_ERR_INVALID_ARG (sizes, null pointers, an id outside [0, n)),
+ * TC_ERR_OOM, TC_ERR_CUDA.  Synchronises the stream.
+ */
+tc_status tc_build_temporal_csr(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst,
+                                const int64_t* d_t, void* stream, tc_graph** out);
+
+/* Free a graph (enqueued on the stream it was built on).  NULL is ignored. */
+tc_status tc_graph_destroy(tc_graph* g);
+
+/* Sizes and time range of a graph (host struct). */
+tc_status tc_graph_info_get(const tc_graph* g, tc_graph_info* h_info);
+
+/* Copy one internal array (tc_array) into caller device memory d_dst, whose
+ * size must be at least the array's (listed above).  Enqueued on stream. */
+tc_status tc_graph_copy(const tc_graph* g, int32_t which, void* d_dst, void* stream);
+
+/*
+ * Bytes of device memory a sampling index needs for graph g: per canonical
+ * edge a 32-byte record {int32 u, int32 v, int64 t, uint32 lo1, uint32 d1,
+ * uint32 lo3, uint32 d3} (the edge and both window ranges of Alg. 2), a
+ * 256-byte header, and a guide table of uint32 that maps equal slices of
+ * [0, W) to the first candidate edge of the CDF search.  Independent of the
+ * motif and delta.
+ */
+tc_status tc_sample_index_bytes(const tc_graph* g, size_t* h_bytes);
+
+/*
+ * Path weights and their exact prefix sum (Claim 1, Alg. 1).  For every edge
+ * e = (u, v, t) in canonical order, with the motif's anchor class
+ * <alpha1, alpha3, beta1, beta3> (Def. 5):
+ *   w_e = d^{alpha1}_u[window1(t)] * d^{alpha3}_v[window3(t)]
+ * where the window is [t - delta, t) for beta = '<' and (t, t + delta] for
+ * beta = '>' (closed at t with TC_WINDOW_CLOSED).
+ *   d_w       optional uint64[m]; receives w_e (NULL: not returned)
+ *   d_prefix  uint64[m+1]; prefix[0] = 0, prefix[i+1] = prefix[i] + w_i
+ *   d_index   tc_sample_index_bytes(g) bytes, 256-byte aligned; receives the
+ *             sampling index consumed by tc_sample_estimate
+ *   h_W       optional; receives W = prefix[m] (synchronises the stream)
+ * Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED_MOTIF, TC_ERR_OVERFLOW (W
+ * does not fit 64 bits; reported when h_W is requested), TC_ERR_CUDA.
+ */
+tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delta, uint64_t* d_w,
+                          uint64_t* d_prefix, void* d_index, uint64_t* h_W, void* stream);
+
+/*
+ * Draw k delta-centered 3-paths and count their motif completions
+ * (Alg. 2, 3, 4, 5).  Sample s = sample_offset + i, i < k, uses Philox4x32-10
+ * (Salmon et al., SC'11) with key (seed low, seed high) and counter
+ * (s low, s high, draw, attempt); draw 0 picks the middle edge as the unique
+ * e with prefix[e] <= r < prefix[e+1] for r uniform in [0, W), draws 1 and 2
+ * pick the end edges uniformly in their windows (Lemire's bounded draw with
+ * rejection, at most 64 attempts).  Each path contributes
+ * X = prod over gaps of ListCount (Alg. 3, 4).
+ *   d_prefix, d_index  as filled by tc_path_weights for the same graph,
+ *                      motif and delta (checked on the device)
+ *   d_h       reserved for a learned proposal; pass NULL
+ *   h_out     receives the sums and the estimate (synchronises the stream)
+ * Ranges [offset, offset + k) of one seed can be merged by adding the sums.
+ * Errors: TC_ERR_INVALID_ARG, TC_ERR_OVERFLOW, TC_ERR_RNG_EXHAUSTED,
+ * TC_ERR_CUDA.
+ */
+tc_status tc_sample_estimate(const tc_graph* g, const tc_motif* motif, int64_t delta,
+                             const uint64_t* d_prefix, const void* d_index, const uint16_t* d_h,
+                             uint64_t k, uint64_t seed, uint64_t sample_offset, tc_estimate* h_out,
+                             void* stream);
+
+/*
+ * Same sampling as tc_sample_estimate for `count` samples, writing per sample
+ * (canonical middle edge, list position of e1, list position of e3, X) as 4
+ * uint64 into d_trace[4*count].  e1 lies in the in-list (alpha1 = '-') or
+ * out-list (alpha1 = '+') of the middle edge's source; e3 likewise for its
+ * destination.  For inspection and parity tests.
+ */
+tc_status tc_sample_trace(const tc_graph* g, const tc_motif* motif, int64_t delta,
+                          const uint64_t* d_prefix, const void* d_index, uint64_t count,
+                          uint64_t seed, uint64_t sample_offset, uint64_t* d_trace, void* stream);
+
+/*
+ * Whole method from host arrays: copy the edges to the device, build the
+ * lists, weights, prefix and index, draw k samples and return the estimate.
+ * Device memory is taken and released inside the call.  h_src, h_dst, h_t
+ * are host arrays of m entries (pinned memory makes the copies faster).
+ */
+tc_status tc_estimate_from_host(int64_t n, int64_t m, const int32_t* h_src, const int32_t* h_dst,
+                                const int64_t* h_t, const tc_motif* motif, int64_t delta, uint64_t k,
+                                uint64_t seed, tc_estimate* h_out, void* stream);
+
+/* Fill in the automatic anchor and report its class: h_anchor[3] = (e1,
+ * middle, e3), h_class[4] = (alpha1, alpha3, beta1, beta3) with -1 for '-' /
+ * '<' and +1 for '+' / '>'.  Host only. */
+tc_status tc_motif_plan(const tc_motif* motif, int32_t* h_anchor, int32_t* h_class);
+
+/* Number of kernels this library has launched in this process so far
+ * (a diagnostic for counting launches around a region). */
+uint64_t tc_kernel_launches(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* tc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

@@ -29,7 +29,7 @@ def _p(a):
 
 def _declare(L):
     vp, i64, u64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32
-    L.or_build_csr.argtypes = [i64, i64] + [vp] * 3 + [vp] * 9 + [vp]
+    L.or_build_csr.argtypes = [i64, i64, ctypes.c_int] + [vp] * 3 + [vp] * 9 + [vp]
     L.or_build_csr.restype = ctypes.c_int
     L.or_path_weights.argtypes = [i64, i64] + [vp] * 7 + [vp, i64] + [vp] * 5
     L.or_path_weights.restype = ctypes.c_int
@@ -161,9 +161,10 @@ def compile_motif(edges, anchor=None, closed=False):
 
 class Graph:
     """Time-sorted out-, in- and pair-lists (Sec. III, Sec. III-B) built by
-    comparison sorts with the full keys."""
+    comparison sorts with the full keys: C qsort by default, or numpy's
+    lexsort on the same keys (sort="lexsort") for large graphs."""
 
-    def __init__(self, n, src, dst, t):
+    def __init__(self, n, src, dst, t, sort="qsort"):
         self.n = int(n)
         self.src = np.ascontiguousarray(src, dtype=np.int32)
         self.dst = np.ascontiguousarray(dst, dtype=np.int32)
@@ -178,8 +179,15 @@ class Graph:
         self.pair_off = np.empty(n + 1, np.int64)
         self.pair_dst = np.empty(max(m, 1), np.int32)
         self.pair_eoff = np.empty(m + 1, np.int64)
+        presorted = 0
+        if sort == "lexsort":
+            idx = np.arange(m, dtype=np.int64)
+            self.out_perm[:] = np.lexsort((idx, self.t, self.src))
+            self.in_perm[:] = np.lexsort((idx, self.t, self.dst))
+            self.pair_perm[:] = np.lexsort((idx, self.t, self.dst, self.src))
+            presorted = 1
         P = ctypes.c_int64(0)
-        st = lib().or_build_csr(n, m, _p(self.src), _p(self.dst), _p(self.t), _p(self.out_perm),
+        st = lib().or_build_csr(n, m, presorted, _p(self.src), _p(self.dst), _p(self.t), _p(self.out_perm),
                                 _p(self.out_off), _p(self.in_perm), _p(self.in_off), _p(self.in_eid),
                                 _p(self.pair_perm), _p(self.pair_off), _p(self.pair_dst),
                                 _p(self.pair_eoff), ctypes.byref(P))
@@ -195,8 +203,8 @@ class Graph:
                 _p(self.pair_dst if self.P else np.zeros(1, np.int32)), _p(self.pair_eoff)]
 
 
-def build_csr(n, src, dst, t):
-    return Graph(n, src, dst, t)
+def build_csr(n, src, dst, t, sort="qsort"):
+    return Graph(n, src, dst, t, sort)
 
 
 def path_weights(g, plan, delta):

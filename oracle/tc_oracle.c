@@ -81,18 +81,22 @@ static int cmp_time(const void *pa, const void *pb) {
  *   out_perm[m], out_off[n+1], in_perm[m], in_off[n+1], in_eid[m],
  *   pair_perm[m], pair_off[n+1], pair_dst[m], pair_eoff[m+1]; *P_out = #pairs.
  * *_perm map a list position to the input edge index; in_eid maps an in-list
- * position to the canonical (out-list) position of the same edge.
+ * position to the canonical (out-list) position of the same edge.  With
+ * presorted != 0 the three permutations are taken as given (computed by a
+ * library sort with the same keys) and only the rest is built.
  */
-int or_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+int or_build_csr(int64_t n, int64_t m, int presorted, const int32_t *src, const int32_t *dst,
                  const int64_t *t, int64_t *out_perm, int64_t *out_off,
                  int64_t *in_perm, int64_t *in_off, int64_t *in_eid,
                  int64_t *pair_perm, int64_t *pair_off, int32_t *pair_dst,
                  int64_t *pair_eoff, int64_t *P_out) {
   g_src = src; g_dst = dst; g_t = t;
-  for (int64_t i = 0; i < m; i++) out_perm[i] = in_perm[i] = pair_perm[i] = i;
-  qsort(out_perm, (size_t)m, sizeof(int64_t), cmp_out);
-  qsort(in_perm, (size_t)m, sizeof(int64_t), cmp_in);
-  qsort(pair_perm, (size_t)m, sizeof(int64_t), cmp_pair);
+  if (!presorted) {
+    for (int64_t i = 0; i < m; i++) out_perm[i] = in_perm[i] = pair_perm[i] = i;
+    qsort(out_perm, (size_t)m, sizeof(int64_t), cmp_out);
+    qsort(in_perm, (size_t)m, sizeof(int64_t), cmp_in);
+    qsort(pair_perm, (size_t)m, sizeof(int64_t), cmp_pair);
+  }
 
   /* offsets by counting */
   for (int64_t v = 0; v <= n; v++) out_off[v] = in_off[v] = 0;

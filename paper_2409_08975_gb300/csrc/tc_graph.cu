@@ -1,0 +1,595 @@
+// Temporal list construction (Sec. III: adjacency lists sorted by time;
+// Sec. III-B: per-pair lists L_{u,v}) on the GPU, with this library's own
+// exclusive scans and stable LSD radix sort.
+//
+// Radix sort: least-significant-digit first, 8-bit digits, one pass =
+// per-tile digit histograms, an exclusive scan of the digit-major histogram
+// table, and a stable scatter in which each warp ranks its keys with
+// __match_any_sync (warp-level multisplit) in input order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+
+// ---------------------------------------------------------------------------
+// Exclusive scans (reduce-then-scan).  With an error word, every tile of
+// every level checks in 128 bits that its total plus its offset fits 64 bits,
+// so a grand total beyond 64 bits is always flagged.
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <class T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T x = lane < (kScanThreads / 32) ? s_warp[lane] : T(0);
+    T xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    if (lane < (kScanThreads / 32)) s_warp[lane] = xi - x;
+    if (lane == (kScanThreads / 32) - 1) s_warp[kScanThreads / 32] = xi;
+  }
+  __syncthreads();
+  T res = s_warp[wid] + inc - v;
+  *total = s_warp[kScanThreads / 32];
+  __syncthreads();
+  return res;
+}
+
+// True in every thread when the sum of the block's `acc` values (plus
+// `extra`, added once) does not fit 64 bits; each thread passes its own
+// per-thread overflow flag.  128-bit warp sums, one shared flag.
+__device__ __forceinline__ bool block_sum_overflows(uint64_t acc, bool thread_ovf, uint64_t extra) {
+  __shared__ unsigned int s_flag;
+  __shared__ unsigned long long s_part[kScanThreads / 32][2];
+  unsigned __int128 a = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)a, o);
+    const uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(a >> 64), o);
+    a += ((unsigned __int128)hi << 64) | lo;
+  }
+  if (threadIdx.x == 0) s_flag = 0;
+  if ((threadIdx.x & 31) == 0) {
+    s_part[threadIdx.x >> 5][0] = (uint64_t)a;
+    s_part[threadIdx.x >> 5][1] = (uint64_t)(a >> 64);
+  }
+  __syncthreads();
+  if (thread_ovf) atomicOr(&s_flag, 1u);
+  if (threadIdx.x == 0) {
+    unsigned __int128 tot = extra;
+    for (int w = 0; w < kScanThreads / 32; w++)
+      tot += ((unsigned __int128)s_part[w][1] << 64) | s_part[w][0];
+    if (tot >> 64) atomicOr(&s_flag, 1u);
+  }
+  __syncthreads();
+  const bool r = s_flag != 0;
+  __syncthreads();
+  return r;
+}
+
+// Tile sums.  With an error word (uint64 only) a tile total beyond 64 bits
+// sets kErrOverflow.
+template <class T>
+__global__ void k_tile_reduce(const T* __restrict__ in, uint64_t n, T* __restrict__ sums, uint32_t* err) {
+  __shared__ T s_warp[kScanThreads / 32 + 1];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  T acc = 0;
+  bool ovf = false;
+#pragma unroll
+  for (int j = 0; j < kScanItems; j++) {
+    const uint64_t i = base + j;
+    if (i < n) {
+      T x = in[i];
+      T s = acc + x;
+      if (s < acc) ovf = true;
+      acc = s;
+    }
+  }
+  if (sizeof(T) == 8 && err != nullptr) {
+    if (block_sum_overflows((uint64_t)acc, ovf, 0) && threadIdx.x == 0) atomicOr(err, kErrOverflow);
+  }
+  T total;
+  block_exclusive_scan<T>(acc, s_warp, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// out[i] = offset[tile] + exclusive prefix; the last tile also writes
+// out[n] = total when write_total.
+template <class T>
+__global__ void k_tile_scan(const T* in, uint64_t n, const T* __restrict__ offsets, T* out, bool write_total,
+                            uint32_t* err) {
+  __shared__ T s_warp[kScanThreads / 32 + 1];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T acc = 0;
+  bool ovf = false;
+#pragma unroll
+  for (int j = 0; j < kScanItems; j++) {
+    const uint64_t i = base + j;
+    v[j] = i < n ? in[i] : T(0);
+    const T s = acc + v[j];
+    if (s < acc) ovf = true;
+    acc = s;
+  }
+  const T off = offsets ? offsets[blockIdx.x] : T(0);
+  // uint64 with an error word: this tile's total plus its offset must fit
+  if (sizeof(T) == 8 && err != nullptr) {
+    if (block_sum_overflows((uint64_t)acc, ovf, (uint64_t)off) && threadIdx.x == 0) atomicOr(err, kErrOverflow);
+  }
+  T total;
+  T ex = block_exclusive_scan<T>(acc, s_warp, &total);
+  T run = off + ex;
+#pragma unroll
+  for (int j = 0; j < kScanItems; j++) {
+    const uint64_t i = base + j;
+    if (i < n) out[i] = run;
+    run += v[j];
+  }
+  if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
+}
+
+template <class T>
+static tc_status scan_rec(const T* in, T* out, uint64_t n, bool write_total, uint32_t* d_err, cudaStream_t st) {
+  if (n == 0) {
+    if (write_total) TC_CUDA(cudaMemsetAsync(out, 0, sizeof(T), st));
+    return TC_OK;
+  }
+  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles == 1) {
+    k_tile_scan<T><<<1, kScanThreads, 0, st>>>(in, n, nullptr, out, write_total, d_err);
+    TC_LAUNCHED(1);
+    TC_CUDA(cudaGetLastError());
+    return TC_OK;
+  }
+  T* sums = nullptr;
+  TC_CUDA(cudaMallocAsync(&sums, sizeof(T) * tiles, st));
+  k_tile_reduce<T><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums, d_err);
+  TC_LAUNCHED(1);
+  tc_status s = TC_OK;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) s = cuda_status(e, "k_tile_reduce");
+  // in place: sums[i] <- exclusive prefix of sums (tile offsets)
+  if (s == TC_OK) s = scan_rec<T>(sums, sums, tiles, false, d_err, st);
+  if (s == TC_OK) {
+    k_tile_scan<T><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums, out, write_total, d_err);
+    TC_LAUNCHED(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_status(e, "k_tile_scan");
+  }
+  cudaFreeAsync(sums, st);
+  return s;
+}
+
+tc_status scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint32_t* d_err, cudaStream_t st) {
+  return scan_rec<uint64_t>(in, out, n, true, d_err, st);
+}
+tc_status scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t st) {
+  return scan_rec<uint32_t>(in, out, n, true, nullptr, st);
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (uint32 key, uint32 value).
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadix = 256;
+
+// warp w of a tile owns keys [w * 32 * kSortItems, (w + 1) * 32 * kSortItems)
+__device__ __forceinline__ uint64_t sort_index(uint64_t tile, int warp, int item, int lane) {
+  return tile * kSortTile + (uint64_t)warp * 32 * kSortItems + (uint64_t)item * 32 + lane;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, uint64_t n,
+                                                           int bit, int nbits, uint32_t* __restrict__ hist,
+                                                           uint32_t tiles) {
+  __shared__ uint32_t s_hist[kRadix];
+  for (int i = threadIdx.x; i < kRadix; i += kSortThreads) s_hist[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t mask = (1u << nbits) - 1u;
+#pragma unroll 4
+  for (int j = 0; j < kSortItems; j++) {
+    const uint64_t i = sort_index(blockIdx.x, warp, j, lane);
+    if (i < n) atomicAdd(&s_hist[(keys[i] >> bit) & mask], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[(uint64_t)d * tiles + blockIdx.x] = s_hist[d];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
+                                                              const uint32_t* __restrict__ vin, uint64_t n,
+                                                              int bit, int nbits,
+                                                              const uint32_t* __restrict__ offs,
+                                                              uint32_t tiles, uint32_t* __restrict__ kout,
+                                                              uint32_t* __restrict__ vout) {
+  __shared__ uint32_t s_cnt[kSortWarps][kRadix];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t mask = (1u << nbits) - 1u;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
+  __syncthreads();
+  uint32_t key[kSortItems], val[kSortItems];
+#pragma unroll
+  for (int j = 0; j < kSortItems; j++) {
+    const uint64_t i = sort_index(blockIdx.x, warp, j, lane);
+    key[j] = i < n ? kin[i] : 0u;
+    val[j] = i < n ? vin[i] : 0u;
+  }
+  // phase 1: per-warp digit counts
+#pragma unroll
+  for (int j = 0; j < kSortItems; j++) {
+    const uint64_t i = sort_index(blockIdx.x, warp, j, lane);
+    const uint32_t d = i < n ? ((key[j] >> bit) & mask) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d != 0xFFFFFFFFu && (peers & lt) == 0) s_cnt[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: global tile offset + counts of earlier warps
+  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+    uint32_t run = offs[(uint64_t)d * tiles + blockIdx.x];
+    for (int w = 0; w < kSortWarps; w++) {
+      const uint32_t c = s_cnt[w][d];
+      s_cnt[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  // phase 2: stable scatter in input order
+#pragma unroll
+  for (int j = 0; j < kSortItems; j++) {
+    const uint64_t i = sort_index(blockIdx.x, warp, j, lane);
+    const uint32_t d = i < n ? ((key[j] >> bit) & mask) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d != 0xFFFFFFFFu) {
+      const uint32_t pos = s_cnt[warp][d] + __popc(peers & lt);
+      kout[pos] = key[j];
+      vout[pos] = val[j];
+    }
+    __syncwarp();
+    if (d != 0xFFFFFFFFu && (peers & lt) == 0) s_cnt[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+tc_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint64_t n, int bit0,
+                           int bit1, cudaStream_t st) {
+  if (n <= 1 || bit1 <= bit0) return TC_OK;
+  const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
+  uint32_t* hist = nullptr;
+  TC_CUDA(cudaMallocAsync(&hist, sizeof(uint32_t) * (kRadix * tiles + 1), st));
+  tc_status s = TC_OK;
+  uint32_t *ka = k0, *va = v0, *kb = k1, *vb = v1;
+  for (int bit = bit0; bit < bit1 && s == TC_OK; bit += 8) {
+    const int nbits = std::min(8, bit1 - bit);
+    k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, n, bit, nbits, hist, (uint32_t)tiles);
+    TC_LAUNCHED(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { s = cuda_status(e, "k_sort_hist"); break; }
+    s = scan_rec<uint32_t>(hist, hist, kRadix * tiles, false, nullptr, st);
+    if (s != TC_OK) break;
+    k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, va, n, bit, nbits, hist, (uint32_t)tiles, kb,
+                                                             vb);
+    TC_LAUNCHED(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { s = cuda_status(e, "k_sort_scatter"); break; }
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (s == TC_OK && ka != k0) {
+    cudaError_t e = cudaMemcpyAsync(k0, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v0, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) s = cuda_status(e, "radix copy-back");
+  }
+  cudaFreeAsync(hist, st);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Graph build.
+
+__global__ void k_check_ids(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                            const int64_t* __restrict__ t, uint64_t m, int64_t n, uint32_t* err,
+                            long long* tminmax) {
+  long long lo = INT64_MAX, hi = INT64_MIN;
+  bool bad = false;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const int32_t a = src[i], b = dst[i];
+    if (a < 0 || a >= n || b < 0 || b >= n) bad = true;
+    const long long x = t[i];
+    lo = x < lo ? x : lo;
+    hi = x > hi ? x : hi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    long long l2 = __shfl_down_sync(0xffffffffu, lo, o), h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&tminmax[0], lo);
+    atomicMax(&tminmax[1], hi);
+  }
+  if (bad) atomicOr(err, kErrBadId);
+}
+
+// keys = low or high 32 bits of (t - tmin), values = input index
+__global__ void k_time_keys(const int64_t* __restrict__ t, uint64_t m, int64_t tmin, int high, uint32_t* keys,
+                            uint32_t* vals) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t d = (uint64_t)t[i] - (uint64_t)tmin;
+    keys[i] = high ? (uint32_t)(d >> 32) : (uint32_t)d;
+    if (vals) vals[i] = (uint32_t)i;
+  }
+}
+
+__global__ void k_high_time_keys(const int64_t* __restrict__ t, const uint32_t* __restrict__ perm, uint64_t m,
+                                 int64_t tmin, uint32_t* keys) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    keys[i] = (uint32_t)(((uint64_t)t[perm[i]] - (uint64_t)tmin) >> 32);
+}
+
+__global__ void k_gather_key(const int32_t* __restrict__ col, const uint32_t* __restrict__ perm, uint64_t m,
+                             uint32_t* keys) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    keys[i] = (uint32_t)col[perm[i]];
+}
+
+// off[v] = first position whose (sorted) key is >= v, for v in [0, n]
+__global__ void k_offsets(const uint32_t* __restrict__ sorted, uint64_t len, int64_t n, uint32_t* off) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= len; i += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t prev = i == 0 ? -1 : (int64_t)sorted[i - 1];
+    const int64_t cur = i == len ? n : (int64_t)sorted[i];
+    for (int64_t v = prev + 1; v <= cur; v++) off[v] = (uint32_t)i;
+  }
+}
+
+__global__ void k_fill_out(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                           const int64_t* __restrict__ t, const uint32_t* __restrict__ perm, uint64_t m,
+                           OutEdge* out_e, uint32_t* canon) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = perm[i];
+    OutEdge r;
+    r.src = src[e];
+    r.dst = dst[e];
+    r.t = t[e];
+    out_e[i] = r;
+    canon[e] = (uint32_t)i;
+  }
+}
+
+__global__ void k_fill_in(const int32_t* __restrict__ src, const int64_t* __restrict__ t,
+                          const uint32_t* __restrict__ perm, const uint32_t* __restrict__ canon, uint64_t m,
+                          InEdge* in_e) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = perm[i];
+    InEdge r;
+    r.src = src[e];
+    r.eid = canon[e];
+    r.t = t[e];
+    in_e[i] = r;
+  }
+}
+
+// pair flags: 1 where (src, dst) differs from the previous pair-order position
+__global__ void k_pair_flags(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                             const uint32_t* __restrict__ perm, uint64_t m, uint32_t* flags) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = perm[i];
+    uint32_t f = 1;
+    if (i > 0) {
+      const uint32_t p = perm[i - 1];
+      f = (src[p] != src[e] || dst[p] != dst[e]) ? 1u : 0u;
+    }
+    flags[i] = f;
+  }
+}
+
+__global__ void k_fill_pairs(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                             const int64_t* __restrict__ t, const uint32_t* __restrict__ perm,
+                             const uint32_t* __restrict__ canon, const uint32_t* __restrict__ flags,
+                             const uint32_t* __restrict__ pidx, uint64_t m, int32_t* pair_dst, uint32_t* pair_eoff,
+                             uint32_t* pair_src, int64_t* pair_t, uint32_t* pair_eid) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = perm[i];
+    pair_t[i] = t[e];
+    pair_eid[i] = canon[e];
+    if (flags[i]) {
+      const uint32_t p = pidx[i];
+      pair_dst[p] = dst[e];
+      pair_src[p] = (uint32_t)src[e];
+      pair_eoff[p] = (uint32_t)i;
+    }
+  }
+}
+
+__global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
+
+static unsigned grid_for(uint64_t n, int threads = 256) {
+  uint64_t b = (n + threads - 1) / threads;
+  const uint64_t cap = (uint64_t)num_sms() * 16;
+  if (b > cap) b = cap;
+  if (b == 0) b = 1;
+  return (unsigned)b;
+}
+
+template <class T>
+static tc_status dmalloc(T** p, uint64_t count, cudaStream_t st) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMallocAsync((void**)p, sizeof(T) * count, st);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(TC_ERR_OOM, "device allocation failed");
+  }
+  if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync");
+  return TC_OK;
+}
+
+tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t,
+                      cudaStream_t st, tc_graph* g) {
+  const uint64_t M = (uint64_t)m;
+  g->n = n;
+  g->m = m;
+  // graph arrays
+  TC_TRY(dmalloc(&g->out_off, n + 1, st));
+  TC_TRY(dmalloc(&g->out_e, M, st));
+  TC_TRY(dmalloc(&g->perm, M, st));
+  TC_TRY(dmalloc(&g->in_off, n + 1, st));
+  TC_TRY(dmalloc(&g->in_e, M, st));
+  TC_TRY(dmalloc(&g->pair_off, n + 1, st));
+  TC_TRY(dmalloc(&g->pair_t, M, st));
+  TC_TRY(dmalloc(&g->pair_eid, M, st));
+
+  // scratch
+  uint32_t *err = nullptr, *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr, *permT = nullptr,
+           *canon = nullptr, *flags = nullptr, *pidx = nullptr, *pair_src = nullptr;
+  long long* tmm = nullptr;
+  tc_status s = TC_OK;
+  auto done = [&](tc_status r) {
+    for (void* p : {(void*)err, (void*)ka, (void*)va, (void*)kb, (void*)vb, (void*)permT, (void*)canon,
+                    (void*)flags, (void*)pidx, (void*)pair_src, (void*)tmm})
+      if (p) cudaFreeAsync(p, st);
+    return r;
+  };
+#define TRY_S(x)                 \
+  do {                           \
+    s = (x);                     \
+    if (s != TC_OK) return done(s); \
+  } while (0)
+#define TRY_C(x, what)                                    \
+  do {                                                    \
+    cudaError_t _e = (x);                                 \
+    if (_e != cudaSuccess) return done(cuda_status(_e, what)); \
+  } while (0)
+
+  TRY_S(dmalloc(&err, 1, st));
+  TRY_S(dmalloc(&tmm, 2, st));
+  TRY_C(cudaMemsetAsync(err, 0, sizeof(uint32_t), st), "memset");
+  long long init[2] = {INT64_MAX, INT64_MIN};
+  TRY_C(cudaMemcpyAsync(tmm, init, sizeof(init), cudaMemcpyHostToDevice, st), "memcpy");
+  if (M) {
+    k_check_ids<<<grid_for(M), 256, 0, st>>>(d_src, d_dst, d_t, M, n, err, tmm);
+    TC_LAUNCHED(1);
+    TRY_C(cudaGetLastError(), "k_check_ids");
+  }
+  uint32_t h_err = 0;
+  long long h_tmm[2];
+  TRY_C(cudaMemcpyAsync(&h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, st), "memcpy");
+  TRY_C(cudaMemcpyAsync(h_tmm, tmm, sizeof(h_tmm), cudaMemcpyDeviceToHost, st), "memcpy");
+  TRY_C(cudaStreamSynchronize(st), "sync");
+  if (h_err & kErrBadId) return done(set_error(TC_ERR_INVALID_ARG, "vertex id outside [0, n)"));
+  g->tmin = M ? h_tmm[0] : 0;
+  g->tmax = M ? h_tmm[1] : 0;
+
+  TRY_S(dmalloc(&ka, M, st));
+  TRY_S(dmalloc(&va, M, st));
+  TRY_S(dmalloc(&kb, M, st));
+  TRY_S(dmalloc(&vb, M, st));
+  TRY_S(dmalloc(&permT, M, st));
+  TRY_S(dmalloc(&canon, M, st));
+  const unsigned gr = grid_for(M);
+  const uint64_t span = (uint64_t)g->tmax - (uint64_t)g->tmin;
+  const int tbits = bitlen64(span);
+  const int vbits = bitlen64((uint64_t)(n > 0 ? n - 1 : 0));
+
+  // 1. by time (stable in input index): low word, then high word
+  if (M) {
+    k_time_keys<<<gr, 256, 0, st>>>(d_t, M, g->tmin, 0, ka, va);
+    TC_LAUNCHED(1);
+    TRY_C(cudaGetLastError(), "k_time_keys");
+    TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, std::min(tbits, 32), st));
+    if (tbits > 32) {
+      k_high_time_keys<<<gr, 256, 0, st>>>(d_t, va, M, g->tmin, ka);
+      TC_LAUNCHED(1);
+      TRY_C(cudaGetLastError(), "k_high_time_keys");
+      TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, tbits - 32, st));
+    }
+    TRY_C(cudaMemcpyAsync(permT, va, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
+  }
+
+  // 2. out-lists: stable by src of the time order -> (src, t, index)
+  if (M) {
+    k_gather_key<<<gr, 256, 0, st>>>(d_src, permT, M, ka);
+    TC_LAUNCHED(1);
+    TRY_C(cudaMemcpyAsync(va, permT, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
+    TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
+    k_fill_out<<<gr, 256, 0, st>>>(d_src, d_dst, d_t, va, M, g->out_e, canon);
+    TC_LAUNCHED(1);
+    TRY_C(cudaGetLastError(), "k_fill_out");
+    TRY_C(cudaMemcpyAsync(g->perm, va, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
+  }
+  k_offsets<<<grid_for(M + 1), 256, 0, st>>>(ka, M, n, g->out_off);
+  TC_LAUNCHED(1);
+  TRY_C(cudaGetLastError(), "k_offsets");
+
+  // 3. in-lists: stable by dst of the time order -> (dst, t, index)
+  if (M) {
+    k_gather_key<<<gr, 256, 0, st>>>(d_dst, permT, M, ka);
+    TC_LAUNCHED(1);
+    TRY_C(cudaMemcpyAsync(va, permT, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
+    TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
+    k_fill_in<<<gr, 256, 0, st>>>(d_src, d_t, va, canon, M, g->in_e);
+    TC_LAUNCHED(1);
+    TRY_C(cudaGetLastError(), "k_fill_in");
+  }
+  k_offsets<<<grid_for(M + 1), 256, 0, st>>>(ka, M, n, g->in_off);
+  TC_LAUNCHED(1);
+  TRY_C(cudaGetLastError(), "k_offsets");
+
+  // 4. pair lists: stable by src of the in-list order -> (src, dst, t, index)
+  uint32_t P = 0;
+  if (M) {
+    k_gather_key<<<gr, 256, 0, st>>>(d_src, va, M, ka);
+    TC_LAUNCHED(1);
+    TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
+    TRY_S(dmalloc(&flags, M, st));
+    TRY_S(dmalloc(&pidx, M + 1, st));
+    k_pair_flags<<<gr, 256, 0, st>>>(d_src, d_dst, va, M, flags);
+    TC_LAUNCHED(1);
+    TRY_C(cudaGetLastError(), "k_pair_flags");
+    TRY_S(scan_u32(flags, pidx, M, st));
+    TRY_C(cudaMemcpyAsync(&P, pidx + M, sizeof(uint32_t), cudaMemcpyDeviceToHost, st), "memcpy");
+    TRY_C(cudaStreamSynchronize(st), "sync");
+  }
+  g->P = P;
+  TRY_S(dmalloc(&g->pair_dst, P, st));
+  TRY_S(dmalloc(&g->pair_eoff, (uint64_t)P + 1, st));
+  TRY_S(dmalloc(&pair_src, P, st));
+  if (M) {
+    k_fill_pairs<<<gr, 256, 0, st>>>(d_src, d_dst, d_t, va, canon, flags, pidx, M, g->pair_dst, g->pair_eoff,
+                                     pair_src, g->pair_t, g->pair_eid);
+    TC_LAUNCHED(1);
+    TRY_C(cudaGetLastError(), "k_fill_pairs");
+  }
+  k_set_u32<<<1, 1, 0, st>>>(g->pair_eoff + P, (uint32_t)M);
+  TC_LAUNCHED(1);
+  TRY_C(cudaGetLastError(), "k_set_u32");
+  k_offsets<<<grid_for((uint64_t)P + 1), 256, 0, st>>>(pair_src, P, n, g->pair_off);
+  TC_LAUNCHED(1);
+  TRY_C(cudaGetLastError(), "k_offsets");
+  TRY_C(cudaStreamSynchronize(st), "sync");
+#undef TRY_S
+#undef TRY_C
+  return done(TC_OK);
+}
+
+}  // namespace tc

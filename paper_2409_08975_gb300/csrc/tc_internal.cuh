@@ -1,0 +1,267 @@
+// Internal declarations of the tc library (device layouts, launch helpers).
+// Not part of the ABI; include/tc.h is.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+// ---------------------------------------------------------------------------
+// Device layouts.  Edge positions are uint32 (m < 2^32 - 1), vertex ids int32.
+
+struct __align__(16) OutEdge {  // canonical order = out-lists sorted by (src, t, input index)
+  int32_t src;
+  int32_t dst;
+  int64_t t;
+};
+
+struct __align__(16) InEdge {  // in-lists sorted by (dst, t, input index)
+  int32_t src;
+  uint32_t eid;  // canonical position of the same edge
+  int64_t t;
+};
+
+// One sampler record per canonical edge: the edge and both window ranges of
+// Alg. 2, so that drawing the middle edge costs one 32-byte sector.
+struct __align__(32) EdgeRec {
+  int32_t u;
+  int32_t v;
+  int64_t t;
+  uint32_t lo1, d1;  // window of e1: positions [lo1, lo1 + d1) of u's alpha1 list
+  uint32_t lo3, d3;  // window of e3: positions [lo3, lo3 + d3) of v's alpha3 list
+};
+
+constexpr uint64_t kIndexMagic = 0x7463696e64657831ull;  // "tcindex1"
+constexpr size_t kIndexHeaderBytes = 256;
+
+// Header at the start of a sampling index; written on the device by the guide
+// kernel so that sampling needs no host round trip.
+struct IndexHeader {
+  uint64_t magic;
+  uint64_t W;
+  uint64_t m;
+  uint32_t shift;    // guide bucket b covers [b << shift, (b + 1) << shift)
+  uint32_t nb;       // buckets; guide has nb + 1 entries
+  int32_t cls[4];    // alpha1, alpha3, beta1, beta3 (+-1)
+  int32_t closed;
+  int32_t anchor[3];
+  int64_t delta;
+  uint64_t graph_id;
+  uint32_t status;   // device error bits of the weights and prefix pass
+};
+
+// Device error bits, reduced into a status at the next synchronisation.
+enum : uint32_t {
+  kErrOverflow = 1u << 0,
+  kErrRng = 1u << 1,
+  kErrBounds = 1u << 2,
+  kErrBadId = 1u << 3,
+  kErrIndexMismatch = 1u << 4,
+};
+
+// ---------------------------------------------------------------------------
+// Compiled motif: anchor, class and the non-anchor edges grouped by gap.
+
+struct Plan {
+  int32_t r;                 // motif edges
+  int32_t e1, mid, e3;       // anchor motif edge indices (= time ranks)
+  int32_t alpha1, alpha3;    // -1 in-list, +1 out-list
+  int32_t beta1, beta3;      // -1 before the middle edge, +1 after
+  int32_t closed;            // 1: closed windows
+  int32_t lab[4];            // motif labels of u', u, v, v'
+  int32_t rk[3];             // anchor ranks sorted ascending (rk[0] = 0)
+  int32_t ngap[3];           // non-anchor lists per gap
+  int8_t gx[3][16], gy[3][16];  // label pairs of those lists in rank order
+};
+
+tc_status compile_plan(const tc_motif* motif, Plan* plan, std::string* why);
+
+// ---------------------------------------------------------------------------
+// Graph object.
+
+}  // namespace tc
+
+struct tc_graph {
+  int64_t n, m, P;
+  int64_t tmin, tmax;
+  int device;
+  uint64_t id;
+  uint32_t* out_off;
+  tc::OutEdge* out_e;
+  uint32_t* perm;
+  uint32_t* in_off;
+  tc::InEdge* in_e;
+  uint32_t* pair_off;
+  int32_t* pair_dst;
+  uint32_t* pair_eoff;
+  int64_t* pair_t;
+  uint32_t* pair_eid;
+};
+
+namespace tc {
+
+// ---------------------------------------------------------------------------
+// Errors (thread-local message, see tc_last_error).
+
+tc_status set_error(tc_status st, const std::string& msg);
+tc_status cuda_status(cudaError_t e, const char* what);
+tc_status device_status(uint32_t bits, const char* what);
+
+#define TC_CUDA(call)                                         \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ::tc::cuda_status(_e, #call); \
+  } while (0)
+
+#define TC_TRY(call)                    \
+  do {                                  \
+    tc_status _s = (call);              \
+    if (_s != TC_OK) return _s;         \
+  } while (0)
+
+inline int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// Launch counter behind tc_kernel_launches(); every launch site bumps it.
+void note_launches(unsigned count);
+#define TC_LAUNCHED(n) ::tc::note_launches(n)
+
+inline int bitlen64(uint64_t x) { return x ? 64 - __builtin_clzll(x) : 0; }
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products with multipliers 0xD2511F53, 0xCD9E8D57 and Weyl
+// key increments 0x9E3779B9, 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    const uint32_t p0hi = __umulhi(0xD2511F53u, c.x), p0lo = 0xD2511F53u * c.x;
+    const uint32_t p1hi = __umulhi(0xCD9E8D57u, c.z), p1lo = 0xCD9E8D57u * c.z;
+    c = make_uint4(p1hi ^ c.y ^ k.x, p1lo, p0hi ^ c.w ^ k.y, p0lo);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform integer in [0, range), range >= 1 (Lemire, "Fast random integer
+// generation in an interval", ACM TOMACS 2019): x * range = hi:lo, accept
+// when lo >= 2^64 mod range, answer hi.  Attempt a draws Philox with counter
+// (s_lo, s_hi, draw, a).  Returns false after 64 rejected attempts.
+__device__ __forceinline__ bool bounded_draw(uint64_t seed, uint64_t s, uint32_t draw, uint64_t range,
+                                             uint64_t* out) {
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  uint64_t reject_below = 0;
+  bool have_threshold = false;
+  for (uint32_t a = 0; a < 64; a++) {
+    const uint4 o = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)(s >> 32), draw, a), key);
+    const uint64_t x = (uint64_t)o.x | ((uint64_t)o.y << 32);
+    const uint64_t lo = x * range;
+    const uint64_t hi = __umul64hi(x, range);
+    if (lo >= range) { *out = hi; return true; }  // 2^64 mod range < range
+    if (!have_threshold) { reject_below = (0ull - range) % range; have_threshold = true; }
+    if (lo >= reject_below) { *out = hi; return true; }
+  }
+  return false;
+}
+
+__device__ __forceinline__ int64_t sat_add(int64_t a, int64_t d) {
+  return (a > INT64_MAX - d) ? INT64_MAX : a + d;
+}
+__device__ __forceinline__ int64_t sat_sub(int64_t a, int64_t d) {
+  return (a < INT64_MIN + d) ? INT64_MIN : a - d;
+}
+
+// First position p in [lo, hi) with time(p) >= x (Ge) or > x (!Ge).
+template <bool Ge, class TimeAt>
+__device__ __forceinline__ uint32_t search_time(uint32_t lo, uint32_t hi, int64_t x, TimeAt time_at) {
+  while (lo < hi) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    const int64_t tm = time_at(mid);
+    if (Ge ? (tm < x) : (tm <= x)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Window of x's list (alpha < 0: in-list, else out-list) around time t
+// (beta < 0: before, else after; strict or closed at t) as positions [lo, hi).
+__device__ __forceinline__ void window_range(const OutEdge* __restrict__ out_e,
+                                             const uint32_t* __restrict__ out_off,
+                                             const InEdge* __restrict__ in_e,
+                                             const uint32_t* __restrict__ in_off, int alpha, int beta,
+                                             int closed, int32_t x, int64_t t, int64_t delta,
+                                             uint32_t* lo, uint32_t* hi) {
+  if (alpha < 0) {
+    const uint32_t a = __ldg(in_off + x), b = __ldg(in_off + x + 1);
+    auto tt = [&](uint32_t p) { return in_e[p].t; };
+    if (beta < 0) {
+      *lo = search_time<true>(a, b, sat_sub(t, delta), tt);
+      *hi = closed ? search_time<false>(*lo, b, t, tt) : search_time<true>(*lo, b, t, tt);
+    } else {
+      *lo = closed ? search_time<true>(a, b, t, tt) : search_time<false>(a, b, t, tt);
+      *hi = search_time<false>(*lo, b, sat_add(t, delta), tt);
+    }
+  } else {
+    const uint32_t a = __ldg(out_off + x), b = __ldg(out_off + x + 1);
+    auto tt = [&](uint32_t p) { return out_e[p].t; };
+    if (beta < 0) {
+      *lo = search_time<true>(a, b, sat_sub(t, delta), tt);
+      *hi = closed ? search_time<false>(*lo, b, t, tt) : search_time<true>(*lo, b, t, tt);
+    } else {
+      *lo = closed ? search_time<true>(a, b, t, tt) : search_time<false>(a, b, t, tt);
+      *hi = search_time<false>(*lo, b, sat_add(t, delta), tt);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files).
+
+// Exclusive scans.  scan_u64 writes out[0..n] (out[n] = total) and sets
+// kErrOverflow in *d_err when the total exceeds 64 bits.  in and out must
+// not overlap unless in == out.
+tc_status scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint32_t* d_err, cudaStream_t st);
+tc_status scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t st);
+
+// Stable LSD radix sort of (key, val) pairs on key bits [bit0, bit1).  The
+// sorted data ends in (k0, v0); k1, v1 are scratch of the same size.
+tc_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint64_t n, int bit0,
+                           int bit1, cudaStream_t st);
+
+tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t,
+                      cudaStream_t st, tc_graph* g);
+
+tc_status launch_weights(const tc_graph* g, const Plan& plan, int64_t delta, EdgeRec* rec, uint64_t* w,
+                         cudaStream_t st);
+tc_status launch_guide(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
+                       void* index, uint32_t* d_err, cudaStream_t st);
+
+size_t index_bytes(uint64_t m);
+int guide_bits(uint64_t m);
+
+struct SampleSums {  // per-call device accumulator
+  unsigned long long sum_x, sum_x2_lo, sum_x2_hi, hits, checked, W;
+  unsigned int err;
+  unsigned int pad;
+};
+
+tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
+                         const void* index, uint64_t k, uint64_t seed, uint64_t offset, uint64_t* trace,
+                         SampleSums* d_sums, cudaStream_t st);
+
+}  // namespace tc

@@ -1,0 +1,171 @@
+"""Seeded synthetic temporal multigraphs shaped like the paper's workloads.
+
+Input generation only: nothing in this module computes any part of the
+estimator.  The paper's datasets (Table II: WT, SO, BI, RE) are not
+available, so these generators stand in for them:
+
+  * ``tiny``       n=2,000, m=20,000, uniform pairs, ~10% of pairs repeated
+                   2-5 times, times uniform in [0, 1e6)
+  * ``dense_tiny`` few vertices and the same edge count, so that delta windows
+                   hold many edges and the exact count is large
+  * ``chung_lu``   directed power-law (Chung-Lu weighted) multigraph whose
+                   edges arrive in bursts: Poisson burst starts over the
+                   span, Pareto(alpha = 1.5, x_m = 1 s) gaps inside a burst,
+                   and a share of repeated pairs (multi-edges)
+"""
+import numpy as np
+
+C4 = [(0, 1), (1, 2), (2, 3), (3, 0)]         # M4-0, directed temporal 4-cycle
+PATH_CHORD = [(0, 1), (1, 2), (2, 3), (0, 3)]  # a->b, b->c, c->d, then a->d last
+
+
+def _pairs_with_multiplicity(rng, n, m, repeat_prob, rep_lo=2, rep_hi=5):
+    """Unique ordered pairs (src != dst) drawn uniformly; each pair gets
+    multiplicity 1 or U{rep_lo..rep_hi} with probability repeat_prob; stop at
+    m edges, trimming the last pair's multiplicity."""
+    src_l, dst_l, total = [], [], 0
+    seen = set()
+    while total < m:
+        need = max(1024, int((m - total) * 0.8))
+        a = rng.integers(0, n, need)
+        b = rng.integers(0, n, need)
+        mult = np.where(rng.random(need) < repeat_prob, rng.integers(rep_lo, rep_hi + 1, need), 1)
+        for x, y, k in zip(a.tolist(), b.tolist(), mult.tolist()):
+            if x == y or (x, y) in seen:
+                continue
+            seen.add((x, y))
+            k = min(k, m - total)
+            src_l.extend([x] * k)
+            dst_l.extend([y] * k)
+            total += k
+            if total >= m:
+                break
+    return np.array(src_l, np.int32), np.array(dst_l, np.int32)
+
+
+def tiny(seed=1001):
+    rng = np.random.default_rng(seed)
+    src, dst = _pairs_with_multiplicity(rng, 2000, 20000, 0.10)
+    t = rng.integers(0, 1_000_000, len(src)).astype(np.int64)
+    return {"name": "tiny", "n": 2000, "src": src, "dst": dst, "t": t, "motif": C4, "delta": 10_000,
+            "k": 100_000}
+
+
+def dense_tiny(seed=1011, n=24, m=20000, span=1_000_000, bursty=False):
+    """Companion graphs whose exact count is large (the tiny config's is ~0)."""
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, n, 2 * m)
+    dst = rng.integers(0, n, 2 * m)
+    keep = src != dst
+    src, dst = src[keep][:m], dst[keep][:m]
+    rep = rng.random(m) < 0.10
+    idx = np.flatnonzero(rep)
+    if len(idx) > 1:  # repeat some earlier pairs
+        j = rng.integers(0, len(src), len(idx))
+        src[idx], dst[idx] = src[j], dst[j]
+    if bursty:
+        starts = rng.integers(0, span, m)
+        gaps = np.floor(rng.pareto(1.5, m) + 1.0) * 60
+        t = np.minimum(starts + gaps.astype(np.int64), span - 1)
+    else:
+        t = rng.integers(0, span, m)
+    return {"name": "dense_tiny_n%d%s" % (n, "_bursty" if bursty else ""), "n": n,
+            "src": src.astype(np.int32), "dst": dst.astype(np.int32), "t": t.astype(np.int64), "motif": C4,
+            "delta": 10_000, "k": 100_000}
+
+
+def _power_weights(n, gamma, i0):
+    return (np.arange(n, dtype=np.float64) + i0) ** (-1.0 / (gamma - 1.0))
+
+
+def _solve_i0(n, pairs, gamma, max_deg):
+    lo, hi = 1e-3, float(n)
+    for _ in range(80):
+        mid = np.sqrt(lo * hi)
+        w = _power_weights(n, gamma, mid)
+        top = pairs * w[0] / w.sum()
+        if top > max_deg:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+def chung_lu(n, m, gamma=2.1, max_deg=1e5, multi_frac=0.30, span=100_000_000, pareto_alpha=1.5, seed=1002,
+             mean_burst_edges=200, burst_degree=4, daily=False):
+    """Directed power-law multigraph whose edges arrive in bursts.
+
+    Bursts start at uniform times over the span (a Poisson process
+    conditioned on its count); a burst of B ~ Geometric(mean_burst_edges)
+    edges draws max(4, B / burst_degree) vertex slots with Chung-Lu weights
+    w_i ~ (i + i0)^(-1/(gamma-1)) (i0 set so the top vertex's expected
+    out-degree is max_deg) and joins uniform slot pairs (no self-loops); its
+    edges follow one another after Pareto(alpha, x_m = 1 s) gaps.  A vertex's
+    degree is then proportional to its weight, and edges close in time share
+    vertices, as in transaction and communication networks.  A share
+    multi_frac of all edges repeat an earlier edge's pair a Pareto gap later.
+    ``daily`` modulates burst starts by 1 + 0.5 sin(2 pi t / 86400)."""
+    rng = np.random.default_rng(seed)
+    base_m = int(round(m * (1.0 - multi_frac)))
+    sizes = rng.geometric(1.0 / mean_burst_edges, int(base_m / mean_burst_edges * 1.2) + 100)
+    cs = np.cumsum(sizes)
+    S = int(np.searchsorted(cs, base_m)) + 1
+    sizes = sizes[:S].copy()
+    sizes[-1] -= cs[S - 1] - base_m
+    nv = np.maximum(4, np.round(sizes / burst_degree)).astype(np.int64)
+    slots_total = int(nv.sum())
+    i0 = _solve_i0(n, slots_total * burst_degree, gamma, max_deg)
+    w = _power_weights(n, gamma, i0)
+    cdf = np.cumsum(w / w.sum())
+    cdf[-1] = 1.0
+    perm = rng.permutation(n)
+    slots = perm[np.searchsorted(cdf, rng.random(slots_total), side="right").clip(0, n - 1)]
+    soff = np.concatenate([[0], np.cumsum(nv)])
+    burst = np.repeat(np.arange(S), sizes)
+    src = slots[soff[burst] + rng.integers(0, nv[burst])]
+    dst = slots[soff[burst] + rng.integers(0, nv[burst])]
+    bad = src == dst
+    while bad.any():
+        idx = np.flatnonzero(bad)
+        src[idx] = slots[soff[burst[idx]] + rng.integers(0, nv[burst[idx]])]
+        dst[idx] = slots[soff[burst[idx]] + rng.integers(0, nv[burst[idx]])]
+        bad = src == dst
+    start = rng.integers(0, span, S)
+    if daily:  # accept a start with probability (1 + 0.5 sin(2 pi t / 86400)) / 1.5
+        bad = np.ones(S, bool)
+        while bad.any():
+            idx = np.flatnonzero(bad)
+            c = rng.integers(0, span, len(idx))
+            acc = rng.random(len(idx)) * 1.5 < 1.0 + 0.5 * np.sin(2 * np.pi * c / 86400.0)
+            start[idx[acc]] = c[acc]
+            bad[idx[acc]] = False
+    gaps = np.floor(rng.pareto(pareto_alpha, base_m) + 1.0).astype(np.int64)
+    first = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    gaps[first] = 0
+    cum = np.cumsum(gaps)
+    cum = cum - cum[first][burst]
+    t = np.minimum(start[burst] + cum, span - 1)
+    extra = m - base_m
+    pick = rng.integers(0, base_m, extra)
+    rt = np.minimum(t[pick] + np.floor(rng.pareto(pareto_alpha, extra) + 1.0).astype(np.int64), span - 1)
+    src = np.concatenate([src, src[pick]]).astype(np.int32)
+    dst = np.concatenate([dst, dst[pick]]).astype(np.int32)
+    t = np.concatenate([t, rt]).astype(np.int64)
+    shuffle = rng.permutation(m)
+    return {"n": n, "src": src[shuffle], "dst": dst[shuffle], "t": t[shuffle]}
+
+
+def mid(seed=1002):
+    g = chung_lu(1_000_000, 20_000_000, gamma=2.1, max_deg=1e5, multi_frac=0.30, seed=seed)
+    g.update({"name": "mid", "motif": PATH_CHORD, "delta": 3600, "k": 100_000_000})
+    return g
+
+
+def scaled_mid(n, m, seed=1002, k=1_000_000):
+    """The mid generator at another size (parity tests, profiling)."""
+    g = chung_lu(n, m, gamma=2.1, max_deg=max(10.0, 1e5 * m / 20_000_000), multi_frac=0.30, seed=seed)
+    g.update({"name": "mid_n%d_m%d" % (n, m), "motif": PATH_CHORD, "delta": 3600, "k": k})
+    return g
+
+
+CONFIGS = {"tiny": tiny, "mid": mid}

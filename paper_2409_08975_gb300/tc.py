@@ -1,0 +1,267 @@
+"""Python binding of the tc C ABI (include/tc.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libtc.so``.  Device buffers are torch CUDA tensors; torch provides memory
+and streams, nothing else.  If the library is missing the import fails loudly;
+there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+TC_OK = 0
+STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_OOM", 3: "TC_ERR_OVERFLOW", 4: "TC_ERR_CUDA",
+                5: "TC_ERR_UNSUPPORTED_MOTIF", 6: "TC_ERR_RNG_EXHAUSTED", 7: "TC_ERR_TIMEOUT",
+                8: "TC_ERR_BOUNDS"}
+WINDOW_STRICT, WINDOW_CLOSED = 0, 1
+
+ARRAYS = {"out_off": 0, "out_edges": 1, "edge_perm": 2, "in_off": 3, "in_edges": 4, "pair_off": 5,
+          "pair_dst": 6, "pair_eoff": 7, "pair_t": 8, "pair_eid": 9}
+
+
+class TcError(RuntimeError):
+    def __init__(self, status, what, msg):
+        super().__init__("%s: %s (%s)" % (what, STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class tc_motif(ctypes.Structure):
+    _fields_ = [("num_edges", ctypes.c_int32), ("src", ctypes.c_int8 * 16), ("dst", ctypes.c_int8 * 16),
+                ("anchor", ctypes.c_int32 * 3), ("window", ctypes.c_int32)]
+
+
+class tc_estimate(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_uint64), ("k", ctypes.c_uint64), ("sum_x", ctypes.c_uint64),
+                ("sum_x2_lo", ctypes.c_uint64), ("sum_x2_hi", ctypes.c_uint64), ("hits", ctypes.c_uint64),
+                ("checked", ctypes.c_uint64), ("estimate", ctypes.c_double), ("std_err", ctypes.c_double)]
+
+
+class tc_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("num_pairs", ctypes.c_int64),
+                ("t_min", ctypes.c_int64), ("t_max", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libtc.so is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, u64, i32, st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int
+        sz = ctypes.c_size_t
+        sig = {
+            "tc_build_temporal_csr": [i64, i64, vp, vp, vp, vp, ctypes.POINTER(vp)],
+            "tc_graph_destroy": [vp],
+            "tc_graph_info_get": [vp, ctypes.POINTER(tc_graph_info)],
+            "tc_graph_copy": [vp, i32, vp, vp],
+            "tc_sample_index_bytes": [vp, ctypes.POINTER(sz)],
+            "tc_path_weights": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, ctypes.POINTER(u64), vp],
+            "tc_sample_estimate": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, u64, u64, u64,
+                                   ctypes.POINTER(tc_estimate), vp],
+            "tc_sample_trace": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, u64, u64, u64, vp, vp],
+            "tc_estimate_from_host": [i64, i64, vp, vp, vp, ctypes.POINTER(tc_motif), i64, u64, u64,
+                                      ctypes.POINTER(tc_estimate), vp],
+            "tc_motif_plan": [ctypes.POINTER(tc_motif), vp, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = st
+        L.tc_kernel_launches.argtypes = []
+        L.tc_kernel_launches.restype = ctypes.c_uint64
+        L.tc_last_error.argtypes = []
+        L.tc_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status, what):
+    if status != TC_OK:
+        raise TcError(status, what, lib().tc_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def tc_kernel_launches():
+    return int(lib().tc_kernel_launches())
+
+
+def make_motif(edges, anchor=None, window=WINDOW_STRICT):
+    """Motif M = (H, pi) from a list of (src_label, dst_label); edge i has
+    time rank i (Def. 1)."""
+    m = tc_motif()
+    m.num_edges = len(edges)
+    for i, (a, b) in enumerate(edges):
+        m.src[i] = int(a)
+        m.dst[i] = int(b)
+    a = anchor if anchor is not None else (-1, -1, -1)
+    for i in range(3):
+        m.anchor[i] = int(a[i])
+    m.window = int(window)
+    return m
+
+
+def tc_motif_plan(motif):
+    anchor = (ctypes.c_int32 * 3)()
+    cls = (ctypes.c_int32 * 4)()
+    _check(lib().tc_motif_plan(ctypes.byref(motif), ctypes.cast(anchor, ctypes.c_void_p),
+                               ctypes.cast(cls, ctypes.c_void_p)), "tc_motif_plan")
+    return tuple(anchor), tuple(cls)
+
+
+class Graph:
+    """Owner of a device-resident tc_graph."""
+
+    def __init__(self, handle):
+        self._h = handle
+        info = tc_graph_info()
+        _check(lib().tc_graph_info_get(handle, ctypes.byref(info)), "tc_graph_info_get")
+        self.n, self.m, self.num_pairs = info.n, info.m, info.num_pairs
+        self.t_min, self.t_max = info.t_min, info.t_max
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("graph destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h is not None:
+            lib().tc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def array(self, name, stream=None):
+        """Copy an internal array to a new CUDA tensor (layouts in tc.h)."""
+        n1, m, P = self.n + 1, self.m, self.num_pairs
+        shapes = {"out_off": (n1, torch.int32), "out_edges": (4 * m, torch.int32), "edge_perm": (m, torch.int32),
+                  "in_off": (n1, torch.int32), "in_edges": (4 * m, torch.int32), "pair_off": (n1, torch.int32),
+                  "pair_dst": (P, torch.int32), "pair_eoff": (P + 1, torch.int32), "pair_t": (m, torch.int64),
+                  "pair_eid": (m, torch.int32)}
+        size, dt = shapes[name]
+        out = torch.empty(max(size, 1), dtype=dt, device="cuda")
+        _check(lib().tc_graph_copy(self.handle, ARRAYS[name], _ptr(out), _stream(stream)), "tc_graph_copy")
+        return out[:size]
+
+
+def tc_build_temporal_csr(n, src, dst, t, stream=None):
+    """src, dst: int32 CUDA tensors, t: int64 CUDA tensor, input order."""
+    assert src.is_cuda and dst.is_cuda and t.is_cuda
+    assert src.dtype == torch.int32 and dst.dtype == torch.int32 and t.dtype == torch.int64
+    src, dst, t = src.contiguous(), dst.contiguous(), t.contiguous()
+    h = ctypes.c_void_p()
+    _check(lib().tc_build_temporal_csr(int(n), int(src.numel()), _ptr(src), _ptr(dst), _ptr(t), _stream(stream),
+                                       ctypes.byref(h)), "tc_build_temporal_csr")
+    return Graph(h)
+
+
+def tc_sample_index_bytes(g):
+    b = ctypes.c_size_t()
+    _check(lib().tc_sample_index_bytes(g.handle, ctypes.byref(b)), "tc_sample_index_bytes")
+    return b.value
+
+
+class Weights:
+    """Prefix sums and sampling index of one (graph, motif, delta)."""
+
+    def __init__(self, prefix, index, w, W):
+        self.prefix, self.index, self.w, self.W = prefix, index, w, W
+
+
+def alloc_weights(g, want_w=False):
+    m = g.m
+    prefix = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    index = torch.empty(tc_sample_index_bytes(g), dtype=torch.uint8, device="cuda")
+    w = torch.empty(max(m, 1), dtype=torch.int64, device="cuda") if want_w else None
+    return Weights(prefix, index, w, None)
+
+
+def tc_path_weights(g, motif, delta, out=None, want_W=True, want_w=False, stream=None):
+    """Claim 1 / Alg. 1 on the device; returns a Weights with W (host) when
+    want_W (which synchronises)."""
+    if out is None:
+        out = alloc_weights(g, want_w)
+    W = ctypes.c_uint64(0)
+    _check(lib().tc_path_weights(g.handle, ctypes.byref(motif), int(delta), _ptr(out.w), _ptr(out.prefix),
+                                 _ptr(out.index), ctypes.byref(W) if want_W else None, _stream(stream)),
+           "tc_path_weights")
+    if want_W:
+        out.W = W.value
+    return out
+
+
+def _est_dict(e):
+    return {"W": e.W, "k": e.k, "sum_x": e.sum_x, "sum_x2": e.sum_x2_lo | (e.sum_x2_hi << 64), "hits": e.hits,
+            "checked": e.checked, "estimate": e.estimate, "std_err": e.std_err}
+
+
+def tc_sample_estimate(g, motif, delta, weights, k, seed=0, offset=0, stream=None):
+    e = tc_estimate()
+    _check(lib().tc_sample_estimate(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix),
+                                    _ptr(weights.index), None, int(k), int(seed), int(offset), ctypes.byref(e),
+                                    _stream(stream)), "tc_sample_estimate")
+    return _est_dict(e)
+
+
+def tc_sample_trace(g, motif, delta, weights, count, seed=0, offset=0, stream=None):
+    """(count, 4) int64 tensor of (middle edge, e1 position, e3 position, X)."""
+    tr = torch.empty((max(count, 1), 4), dtype=torch.int64, device="cuda")
+    _check(lib().tc_sample_trace(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix),
+                                 _ptr(weights.index), int(count), int(seed), int(offset), _ptr(tr), _stream(stream)),
+           "tc_sample_trace")
+    return tr[:count]
+
+
+def tc_estimate_from_host(n, src, dst, t, motif, delta, k, seed=0, stream=None):
+    """Whole method from host arrays (numpy or CPU tensors, ideally pinned)."""
+    def hp(a, dt):
+        if isinstance(a, torch.Tensor):
+            assert not a.is_cuda and a.dtype == dt and a.is_contiguous()
+            return a, ctypes.c_void_p(a.data_ptr())
+        a = np.ascontiguousarray(a, dtype={torch.int32: np.int32, torch.int64: np.int64}[dt])
+        return a, a.ctypes.data_as(ctypes.c_void_p)
+    ks, ps = hp(src, torch.int32)
+    kd, pd = hp(dst, torch.int32)
+    kt, pt = hp(t, torch.int64)
+    e = tc_estimate()
+    _check(lib().tc_estimate_from_host(int(n), int(len(ks)), ps, pd, pt, ctypes.byref(motif), int(delta), int(k),
+                                       int(seed), ctypes.byref(e), _stream(stream)), "tc_estimate_from_host")
+    return _est_dict(e)
+
+
+def estimate_from_sums(sum_x, sum_x2, k, W):
+    """Merge helper for partial runs over disjoint sample ranges: the same
+    host formula as the library (Alg. 5), applied to summed integers."""
+    import math
+    if k == 0 or W == 0:
+        return 0.0, 0.0
+    q, r = divmod(int(sum_x) * int(W), int(k))
+    est = float(q) + float(r) / float(k)
+    if k < 2:
+        return est, float("nan")
+    sx, sx2, kf = float(sum_x), float(sum_x2), float(k)
+    s2 = max((sx2 - sx * sx / kf) / (kf - 1.0), 0.0)
+    return est, float(W) * math.sqrt(s2 / kf)

@@ -106,6 +106,10 @@ def test_csr_orders_match_lexsort():
     assert (g.out_perm == np.lexsort((idx, t, src))).all()
     assert (g.in_perm == np.lexsort((idx, t, dst))).all()
     assert (g.pair_perm == np.lexsort((idx, t, dst, src))).all()
+    g2 = oracle.build_csr(n, src, dst, t, sort="lexsort")
+    for name in ("out_perm", "out_off", "in_perm", "in_off", "in_eid", "pair_perm", "pair_off", "pair_dst",
+                 "pair_eoff"):
+        assert (getattr(g, name) == getattr(g2, name)).all(), name
     assert (g.out_off == np.concatenate([[0], np.cumsum(np.bincount(src, minlength=n))])).all()
     assert (g.in_off == np.concatenate([[0], np.cumsum(np.bincount(dst, minlength=n))])).all()
     canon = np.empty(m, np.int64)
