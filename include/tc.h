@@ -211,6 +211,31 @@ tc_status tc_estimate_from_host(int64_t n, int64_t m, const int32_t* h_src, cons
                                 const int64_t* h_t, const tc_motif* motif, int64_t delta, uint64_t k,
                                 uint64_t seed, tc_estimate* h_out, void* stream);
 
+/*
+ * Exact uint64 prefix sum of d_w (the same result as the d_prefix of
+ * tc_path_weights for the same weights) that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc or cudaMallocAsync, for example code whose device
+ * memory is owned by another allocator that reserved all of it up front, or
+ * a process that runs under a hard memory budget in which a new allocation
+ * may fail at any time.  The caller passes the weights and the output:
+ *   d_w       uint64[m] device input
+ *   d_prefix  uint64[m+1] device output, prefix[0] = 0, prefix[m] = W
+ *   h_W       optional; receives W and reports overflow (synchronises)
+ * Scratch (per-tile sums and an error word) lives in one static device array
+ * of about 1 MiB that every GPU loading this library holds until the process
+ * exits.  m may be at most TC_NOALLOC_MAX_EDGES; larger m returns
+ * TC_ERR_INVALID_ARG.  Every call shares that array: calls whose work
+ * overlaps on the GPU (different streams, or several host threads) race and
+ * must be serialised by the caller.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Overflow of W is detected on the device and reported
+ * only when h_W is requested.
+ */
+#define TC_NOALLOC_MAX_EDGES (1ull << 28)
+tc_status tc_prefix_sum_noalloc(const uint64_t* d_w, uint64_t m, uint64_t* d_prefix, uint64_t* h_W,
+                                void* stream);
+
 /* Fill in the automatic anchor and report its class: h_anchor[3] = (e1,
  * middle, e3), h_class[4] = (alpha1, alpha3, beta1, beta3) with -1 for '-' /
  * '<' and +1 for '+' / '>'.  Host only. */

@@ -237,6 +237,9 @@ __device__ __forceinline__ void window_range(const OutEdge* __restrict__ out_e,
 // not overlap unless in == out.
 tc_status scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint32_t* d_err, cudaStream_t st);
 tc_status scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t st);
+uint64_t scan_u64_scratch_words(uint64_t n);
+tc_status scan_u64_in_scratch(const uint64_t* in, uint64_t* out, uint64_t n, bool write_total, uint32_t* d_err,
+                              uint64_t* scratch, uint64_t scratch_words, cudaStream_t st);
 
 // Stable LSD radix sort of (key, val) pairs on key bits [bit0, bit1).  The
 // sorted data ends in (k0, v0); k1, v1 are scratch of the same size.

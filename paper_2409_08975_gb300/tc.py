@@ -70,6 +70,7 @@ def lib():
             "tc_estimate_from_host": [i64, i64, vp, vp, vp, ctypes.POINTER(tc_motif), i64, u64, u64,
                                       ctypes.POINTER(tc_estimate), vp],
             "tc_motif_plan": [ctypes.POINTER(tc_motif), vp, vp],
+            "tc_prefix_sum_noalloc": [vp, u64, vp, ctypes.POINTER(u64), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -250,6 +251,18 @@ def tc_estimate_from_host(n, src, dst, t, motif, delta, k, seed=0, stream=None):
     _check(lib().tc_estimate_from_host(int(n), int(len(ks)), ps, pd, pt, ctypes.byref(motif), int(delta), int(k),
                                        int(seed), ctypes.byref(e), _stream(stream)), "tc_estimate_from_host")
     return _est_dict(e)
+
+
+NOALLOC_MAX_EDGES = 1 << 28
+
+
+def tc_prefix_sum_noalloc(w, m, prefix, want_W=True, stream=None):
+    """Prefix sum of w[:m] into prefix[:m+1] without device allocation (for
+    callers that cannot allocate device memory).  Returns W when want_W."""
+    W = ctypes.c_uint64(0)
+    _check(lib().tc_prefix_sum_noalloc(_ptr(w), int(m), _ptr(prefix), ctypes.byref(W) if want_W else None,
+                                       _stream(stream)), "tc_prefix_sum_noalloc")
+    return W.value if want_W else None
 
 
 def estimate_from_sums(sum_x, sum_x2, k, W):
