@@ -108,12 +108,13 @@ typedef enum {
   TC_ARRAY_OUT_EDGES = 1, /* {int32 src, int32 dst, int64 t}[m], canonical order  */
   TC_ARRAY_EDGE_PERM = 2, /* uint32[m]     canonical position -> input index      */
   TC_ARRAY_IN_OFF = 3,    /* uint32[n+1]   in-list offsets per vertex             */
-  TC_ARRAY_IN_EDGES = 4,  /* {int32 src, uint32 canonical, int64 t}[m], in order   */
+  TC_ARRAY_IN_EDGES = 4,  /* {int32 src, int32 dst, int64 t}[m], in-list order      */
   TC_ARRAY_PAIR_OFF = 5,  /* uint32[n+1]   first pair index per source vertex      */
   TC_ARRAY_PAIR_DST = 6,  /* int32[P]      destination of each pair, by (src, dst) */
   TC_ARRAY_PAIR_EOFF = 7, /* uint32[P+1]   first pair-list position per pair       */
   TC_ARRAY_PAIR_T = 8,    /* int64[m]      times in pair order                     */
-  TC_ARRAY_PAIR_EID = 9   /* uint32[m]     pair position -> canonical position     */
+  TC_ARRAY_PAIR_EID = 9,  /* uint32[m]     pair position -> canonical position     */
+  TC_ARRAY_IN_EID = 10    /* uint32[m]     in-list position -> canonical position  */
 } tc_array;
 
 /*

@@ -120,11 +120,13 @@ tc_status compile_plan(const tc_motif* M, Plan* P, std::string* why) {
     for (int b = a + 1; b < 3; b++)
       if (rk[b] < rk[a]) { int x = rk[a]; rk[a] = rk[b]; rk[b] = x; }
   for (int a = 0; a < 3; a++) P->rk[a] = rk[a];
+  int role[4];  // label -> position in (u', u, v, v')
+  for (int i = 0; i < 4; i++) role[best_lab[i]] = i;
   for (int gp = 0; gp < 3; gp++) {
     const int lo = rk[gp], hi = gp < 2 ? rk[gp + 1] : r;
     for (int f = lo + 1; f < hi; f++) {
-      P->gx[gp][P->ngap[gp]] = M->src[f];
-      P->gy[gp][P->ngap[gp]] = M->dst[f];
+      P->gx[gp][P->ngap[gp]] = (int8_t)role[M->src[f]];
+      P->gy[gp][P->ngap[gp]] = (int8_t)role[M->dst[f]];
       P->ngap[gp]++;
     }
   }
@@ -149,8 +151,8 @@ static tc_status plan_of(const tc_motif* motif, Plan* p) {
 }
 
 static void free_graph_arrays(tc_graph* g) {
-  void* ps[] = {g->out_off, g->out_e, g->perm, g->in_off, g->in_e, g->pair_off,
-                g->pair_dst, g->pair_eoff, g->pair_t, g->pair_eid};
+  void* ps[] = {g->out_off, g->out_e, g->perm, g->in_off, g->in_e, g->in_eid, g->pair_off,
+                g->pair_dst, g->pair_eoff, g->pair_t, g->pair_eid, g->pair_hash};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -255,6 +257,7 @@ tc_status tc_graph_copy(const tc_graph* g, int32_t which, void* d_dst, void* str
     case TC_ARRAY_EDGE_PERM: src = g->perm; bytes = 4 * m; break;
     case TC_ARRAY_IN_OFF: src = g->in_off; bytes = 4 * n1; break;
     case TC_ARRAY_IN_EDGES: src = g->in_e; bytes = 16 * m; break;
+    case TC_ARRAY_IN_EID: src = g->in_eid; bytes = 4 * m; break;
     case TC_ARRAY_PAIR_OFF: src = g->pair_off; bytes = 4 * n1; break;
     case TC_ARRAY_PAIR_DST: src = g->pair_dst; bytes = 4 * P; break;
     case TC_ARRAY_PAIR_EOFF: src = g->pair_eoff; bytes = 4 * (P + 1); break;

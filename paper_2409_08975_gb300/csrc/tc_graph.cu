@@ -411,16 +411,17 @@ __global__ void k_fill_out(const int32_t* __restrict__ src, const int32_t* __res
   }
 }
 
-__global__ void k_fill_in(const int32_t* __restrict__ src, const int64_t* __restrict__ t,
-                          const uint32_t* __restrict__ perm, const uint32_t* __restrict__ canon, uint64_t m,
-                          InEdge* in_e) {
+__global__ void k_fill_in(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                          const int64_t* __restrict__ t, const uint32_t* __restrict__ perm,
+                          const uint32_t* __restrict__ canon, uint64_t m, InEdge* in_e, uint32_t* in_eid) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t e = perm[i];
     InEdge r;
     r.src = src[e];
-    r.eid = canon[e];
+    r.dst = dst[e];
     r.t = t[e];
     in_e[i] = r;
+    in_eid[i] = canon[e];
   }
 }
 
@@ -458,6 +459,27 @@ __global__ void k_fill_pairs(const int32_t* __restrict__ src, const int32_t* __r
 
 __global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
 
+// Insert every distinct pair (x, y) with its list range into the hash table.
+// Each pair is inserted once; a probe sequence ends at the first empty slot,
+// which exists because the load factor is at most 1/2.
+__global__ void k_pair_hash(const uint32_t* __restrict__ pair_src, const int32_t* __restrict__ pair_dst,
+                            const uint32_t* __restrict__ pair_eoff, uint32_t P, PairSlot* table, uint64_t mask) {
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = pair_src[p], y = (uint32_t)pair_dst[p];
+    const unsigned long long key = pair_key(x, y);
+    uint64_t h = mix64(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+      unsigned long long* word = reinterpret_cast<unsigned long long*>(&table[h]);
+      if (atomicCAS(word, kEmptyPairKey, key) == kEmptyPairKey) {
+        table[h].begin = pair_eoff[p];
+        table[h].end = pair_eoff[p + 1];
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+  }
+}
+
 static unsigned grid_for(uint64_t n, int threads = 256) {
   uint64_t b = (n + threads - 1) / threads;
   const uint64_t cap = (uint64_t)num_sms() * 16;
@@ -490,6 +512,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   TC_TRY(dmalloc(&g->perm, M, st));
   TC_TRY(dmalloc(&g->in_off, n + 1, st));
   TC_TRY(dmalloc(&g->in_e, M, st));
+  TC_TRY(dmalloc(&g->in_eid, M, st));
   TC_TRY(dmalloc(&g->pair_off, n + 1, st));
   TC_TRY(dmalloc(&g->pair_t, M, st));
   TC_TRY(dmalloc(&g->pair_eid, M, st));
@@ -582,7 +605,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
     TC_LAUNCHED(1);
     TRY_C(cudaMemcpyAsync(va, permT, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
-    k_fill_in<<<gr, 256, 0, st>>>(d_src, d_t, va, canon, M, g->in_e);
+    k_fill_in<<<gr, 256, 0, st>>>(d_src, d_dst, d_t, va, canon, M, g->in_e, g->in_eid);
     TC_LAUNCHED(1);
     TRY_C(cudaGetLastError(), "k_fill_in");
   }
@@ -621,6 +644,17 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   k_offsets<<<grid_for((uint64_t)P + 1), 256, 0, st>>>(pair_src, P, n, g->pair_off);
   TC_LAUNCHED(1);
   TRY_C(cudaGetLastError(), "k_offsets");
+  // pair hash table, capacity the power of two >= max(2, 2P)
+  uint64_t cap = 2;
+  while (cap < 2ull * P) cap <<= 1;
+  g->hash_mask = cap - 1;
+  TRY_S(dmalloc(&g->pair_hash, cap, st));
+  TRY_C(cudaMemsetAsync(g->pair_hash, 0xFF, sizeof(PairSlot) * cap, st), "memset");
+  if (P) {
+    k_pair_hash<<<grid_for(P), 256, 0, st>>>(pair_src, g->pair_dst, g->pair_eoff, P, g->pair_hash, g->hash_mask);
+    TC_LAUNCHED(1);
+    TRY_C(cudaGetLastError(), "k_pair_hash");
+  }
   TRY_C(cudaStreamSynchronize(st), "sync");
 #undef TRY_S
 #undef TRY_C

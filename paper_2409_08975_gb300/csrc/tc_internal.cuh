@@ -22,7 +22,7 @@ struct __align__(16) OutEdge {  // canonical order = out-lists sorted by (src, t
 
 struct __align__(16) InEdge {  // in-lists sorted by (dst, t, input index)
   int32_t src;
-  uint32_t eid;  // canonical position of the same edge
+  int32_t dst;
   int64_t t;
 };
 
@@ -35,6 +35,24 @@ struct __align__(32) EdgeRec {
   uint32_t lo1, d1;  // window of e1: positions [lo1, lo1 + d1) of u's alpha1 list
   uint32_t lo3, d3;  // window of e3: positions [lo3, lo3 + d3) of v's alpha3 list
 };
+
+// Slot of the pair hash table: the pair list L_{x,y} occupies positions
+// [begin, end) of pair_t.  Empty slots have x = y = 0xFFFFFFFF.
+struct __align__(16) PairSlot {
+  uint32_t x, y;
+  uint32_t begin, end;
+};
+constexpr unsigned long long kEmptyPairKey = 0xFFFFFFFFFFFFFFFFull;
+
+// 64-bit finaliser of SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t pair_key(uint32_t x, uint32_t y) {
+  return (uint64_t)x | ((uint64_t)y << 32);  // little-endian image of {x, y}
+}
 
 constexpr uint64_t kIndexMagic = 0x7463696e64657831ull;  // "tcindex1"
 constexpr size_t kIndexHeaderBytes = 256;
@@ -76,7 +94,8 @@ struct Plan {
   int32_t lab[4];            // motif labels of u', u, v, v'
   int32_t rk[3];             // anchor ranks sorted ascending (rk[0] = 0)
   int32_t ngap[3];           // non-anchor lists per gap
-  int8_t gx[3][16], gy[3][16];  // label pairs of those lists in rank order
+  int8_t gx[3][16], gy[3][16];  // path roles (0 u', 1 u, 2 v, 3 v') of the
+                                // endpoints of those lists, in rank order
 };
 
 tc_status compile_plan(const tc_motif* motif, Plan* plan, std::string* why);
@@ -96,11 +115,14 @@ struct tc_graph {
   uint32_t* perm;
   uint32_t* in_off;
   tc::InEdge* in_e;
+  uint32_t* in_eid;  // in-list position -> canonical position
   uint32_t* pair_off;
   int32_t* pair_dst;
   uint32_t* pair_eoff;
   int64_t* pair_t;
   uint32_t* pair_eid;
+  tc::PairSlot* pair_hash;  // open addressing, linear probing, load <= 1/2
+  uint64_t hash_mask;       // capacity - 1 (capacity a power of two)
 };
 
 namespace tc {

@@ -7,32 +7,53 @@
 namespace tc {
 
 // ---------------------------------------------------------------------------
-// Weights: one thread per canonical edge e = (u, v, t).  The window of u's
-// alpha1 list and of v's alpha3 list are found by binary search on time
-// (Alg. 1: four searches per edge); w_e = d1 * d3 (Claim 1).
+// Weights (Claim 1, Alg. 1): w_e = d1 * d3 for every canonical edge
+// e = (u, v, t), the sizes of the window of u's alpha1 list and of v's alpha3
+// list, found by binary search on time (four searches per edge).  Two passes
+// so that the lanes of a warp search the same list in lockstep and share the
+// probes of their searches:
+//   pass 1 runs over the in-lists (edges grouped by v) and finds v's window;
+//          its (lo3, d3) is parked in w at the edge's canonical position;
+//   pass 2 runs over the canonical order (edges grouped by u), finds u's
+//          window, writes the sampler record and w_e.
 
-__global__ void __launch_bounds__(256) k_weights(const OutEdge* __restrict__ out_e,
-                                                 const uint32_t* __restrict__ out_off,
-                                                 const InEdge* __restrict__ in_e,
-                                                 const uint32_t* __restrict__ in_off, uint32_t m, Plan plan,
-                                                 int64_t delta, EdgeRec* __restrict__ rec,
-                                                 uint64_t* __restrict__ w) {
+__global__ void __launch_bounds__(256) k_weights_dst(const OutEdge* __restrict__ out_e,
+                                                     const uint32_t* __restrict__ out_off,
+                                                     const InEdge* __restrict__ in_e,
+                                                     const uint32_t* __restrict__ in_off,
+                                                     const uint32_t* __restrict__ in_eid, uint64_t m, Plan plan,
+                                                     int64_t delta, uint64_t* __restrict__ w) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += stride) {
+    const InEdge e = in_e[p];
+    uint32_t lo3, hi3;
+    window_range(out_e, out_off, in_e, in_off, plan.alpha3, plan.beta3, plan.closed, e.dst, e.t, delta, &lo3,
+                 &hi3);
+    w[in_eid[p]] = (uint64_t)lo3 | ((uint64_t)(hi3 - lo3) << 32);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_weights_src(const OutEdge* __restrict__ out_e,
+                                                     const uint32_t* __restrict__ out_off,
+                                                     const InEdge* __restrict__ in_e,
+                                                     const uint32_t* __restrict__ in_off, uint64_t m, Plan plan,
+                                                     int64_t delta, EdgeRec* __restrict__ rec,
+                                                     uint64_t* __restrict__ w) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
     const OutEdge e = out_e[i];
-    uint32_t lo1, hi1, lo3, hi3;
+    uint32_t lo1, hi1;
     window_range(out_e, out_off, in_e, in_off, plan.alpha1, plan.beta1, plan.closed, e.src, e.t, delta, &lo1,
                  &hi1);
-    window_range(out_e, out_off, in_e, in_off, plan.alpha3, plan.beta3, plan.closed, e.dst, e.t, delta, &lo3,
-                 &hi3);
+    const uint64_t parked = w[i];
     EdgeRec r;
     r.u = e.src;
     r.v = e.dst;
     r.t = e.t;
     r.lo1 = lo1;
     r.d1 = hi1 - lo1;
-    r.lo3 = lo3;
-    r.d3 = hi3 - lo3;
+    r.lo3 = (uint32_t)parked;
+    r.d3 = (uint32_t)(parked >> 32);
     rec[i] = r;
     w[i] = (uint64_t)r.d1 * (uint64_t)r.d3;
   }
@@ -40,10 +61,13 @@ __global__ void __launch_bounds__(256) k_weights(const OutEdge* __restrict__ out
 
 tc_status launch_weights(const tc_graph* g, const Plan& plan, int64_t delta, EdgeRec* rec, uint64_t* w,
                          cudaStream_t st) {
-  const uint32_t m = (uint32_t)g->m;
+  const uint64_t m = (uint64_t)g->m;
   if (m == 0) return TC_OK;
-  unsigned blocks = (m + 255) / 256;
-  k_weights<<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, m, plan, delta, rec, w);
+  const unsigned blocks = (unsigned)((m + 255) / 256);
+  k_weights_dst<<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->in_eid, m, plan, delta, w);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  k_weights_src<<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, m, plan, delta, rec, w);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
@@ -80,9 +104,11 @@ static IndexView index_view(void* index, uint64_t m) {
 }
 
 // Guide table: bucket b covers r in [b << shift, (b + 1) << shift); guide[b]
-// is the largest i < m with prefix[i] <= b << shift, the first candidate of
-// the CDF search for any r in the bucket; guide[nb] = m - 1.  Each block
-// first bounds its buckets' answers, then each thread searches that range.
+// is the edge whose range [prefix[i], prefix[i+1]) holds b << shift (the
+// largest i with prefix[i] <= b << shift), the first candidate of the CDF
+// search for any r in the bucket; guide[nb] = m - 1.  Filled edge-parallel:
+// edge i owns the buckets b with b << shift in its range; a warp shares the
+// writes of its 32 edges evenly, so that heavy edges do not serialise.
 __global__ void __launch_bounds__(256) k_guide(const uint64_t* __restrict__ prefix, uint32_t m, int gbits,
                                                uint32_t* __restrict__ guide, IndexHeader* hdr, Plan plan,
                                                int64_t delta, uint64_t graph_id, const uint32_t* err) {
@@ -90,29 +116,42 @@ __global__ void __launch_bounds__(256) k_guide(const uint64_t* __restrict__ pref
   const int wbits = W ? 64 - __clzll(W - 1) : 0;
   const uint32_t shift = wbits > gbits ? (uint32_t)(wbits - gbits) : 0u;
   const uint32_t nb = W ? (uint32_t)(((W - 1) >> shift) + 1) : 0u;
-  auto largest_le = [&](uint64_t x, uint32_t lo, uint32_t hi) {  // in [lo, hi], prefix[lo] <= x
-    while (lo < hi) {
-      const uint32_t mid = lo + ((hi - lo + 1) >> 1);
-      if (prefix[mid] <= x) lo = mid; else hi = mid - 1;
+  const uint64_t low = (1ull << shift) - 1ull;
+  auto first_bucket = [&](uint64_t x) { return (uint32_t)((x >> shift) + ((x & low) != 0)); };  // ceil(x / 2^shift)
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t wb = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wb * 32 < m; wb += warps) {
+    const uint64_t i = wb * 32 + lane;
+    uint32_t b0 = 0, n = 0;
+    if (i < m) {
+      b0 = first_bucket(prefix[i]);
+      n = first_bucket(prefix[i + 1]) - b0;
     }
-    return lo;
-  };
-  __shared__ uint32_t s_lo, s_hi;
-  const uint64_t b0 = (uint64_t)blockIdx.x * blockDim.x;
-  if (b0 >= nb) {
-    if (b0 == nb && threadIdx.x == 0 && m) guide[nb] = m - 1;
-  } else {
-    if (threadIdx.x == 0) {
-      const uint64_t blast = min((uint64_t)nb - 1, b0 + blockDim.x - 1);
-      s_lo = largest_le(b0 << shift, 0, m - 1);
-      s_hi = largest_le(blast << shift, s_lo, m - 1);
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    __syncthreads();
-    const uint64_t b = b0 + threadIdx.x;
-    if (b < nb) guide[b] = largest_le(b << shift, s_lo, s_hi);
-    if (b == nb && m) guide[nb] = m - 1;
+    const uint32_t excl = incl - n;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+      const uint32_t q = q0 + lane;
+      // owner: the last lane whose exclusive offset is <= q
+      int lo = 0, hi = 31;
+#pragma unroll
+      for (int step = 0; step < 5; step++) {
+        const int mid = (lo + hi + 1) >> 1;
+        const uint32_t ex = __shfl_sync(0xffffffffu, excl, mid);
+        if (ex <= q) lo = mid; else hi = mid - 1;
+      }
+      const uint32_t ob0 = __shfl_sync(0xffffffffu, b0, lo);
+      const uint32_t oex = __shfl_sync(0xffffffffu, excl, lo);
+      if (q < total) guide[ob0 + (q - oex)] = (uint32_t)(wb * 32 + lo);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (m) guide[nb] = m - 1;
     IndexHeader h;
     h.magic = kIndexMagic;
     h.W = W;
@@ -139,9 +178,11 @@ tc_status launch_guide(const tc_graph* g, const Plan& plan, int64_t delta, const
   const uint64_t m = (uint64_t)g->m;
   IndexView v = index_view(index, m);
   const int gb = guide_bits(m);
-  const uint64_t slots = (1ull << gb) + 1;  // nb <= 2^gb, plus guide[nb]
-  const unsigned blocks = (unsigned)((slots + 255) / 256);
-  k_guide<<<blocks, 256, 0, st>>>(prefix, (uint32_t)m, gb, v.guide, v.hdr, plan, delta, g->id, d_err);
+  uint64_t blocks = (m + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  k_guide<<<(unsigned)blocks, 256, 0, st>>>(prefix, (uint32_t)m, gb, v.guide, v.hdr, plan, delta, g->id, d_err);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
@@ -153,15 +194,17 @@ tc_status launch_guide(const tc_graph* g, const Plan& plan, int64_t delta, const
 struct SamplerArgs {
   const OutEdge* out_e;
   const InEdge* in_e;
-  const uint32_t* pair_off;
-  const int32_t* pair_dst;
-  const uint32_t* pair_eoff;
+  const PairSlot* pair_hash;
+  uint64_t hash_mask;
   const int64_t* pair_t;
   const uint64_t* prefix;
   const IndexHeader* hdr;
   const EdgeRec* rec;
   const uint32_t* guide;
   uint64_t k, seed, offset;
+  const uint32_t* order;  // processing order of the chunk's samples (NULL: in id order)
+  uint64_t chunk_base;    // index of the chunk's first sample within the call
+  uint64_t count;         // samples in the chunk
   uint32_t m;
   int64_t delta;
   uint64_t graph_id;
@@ -170,16 +213,26 @@ struct SamplerArgs {
 };
 
 // Positions [a, b) of the pair list L_{x,y} with time in (tlo, thi) or
-// (tlo, thi] (hi_incl).  Returns false when x never sends to y.
+// (tlo, thi] (hi_incl).  The list's range comes from the pair hash table (one
+// 16-byte slot per probe).  Returns false when x never sends to y.
 __device__ __forceinline__ bool pair_window(const SamplerArgs& A, int32_t x, int32_t y, int64_t tlo, int64_t thi,
                                             bool hi_incl, uint32_t* a, uint32_t* b) {
-  uint32_t lo = __ldg(A.pair_off + x), hi = __ldg(A.pair_off + x + 1);
-  while (lo < hi) {
-    const uint32_t mid = lo + ((hi - lo) >> 1);
-    if (__ldg(A.pair_dst + mid) < y) lo = mid + 1; else hi = mid;
+  const uint64_t key = pair_key((uint32_t)x, (uint32_t)y);
+  uint64_t h = mix64(key) & A.hash_mask;
+  uint32_t s = 0, e = 0;
+  bool found = false;
+  for (uint64_t probe = 0; probe <= A.hash_mask; probe++) {
+    const uint4 slot = __ldg(reinterpret_cast<const uint4*>(A.pair_hash + h));
+    if (slot.x == (uint32_t)x && slot.y == (uint32_t)y) {
+      s = slot.z;
+      e = slot.w;
+      found = true;
+      break;
+    }
+    if (slot.x == 0xFFFFFFFFu) break;
+    h = (h + 1) & A.hash_mask;
   }
-  if (lo >= __ldg(A.pair_off + x + 1) || __ldg(A.pair_dst + lo) != y) return false;
-  const uint32_t s = __ldg(A.pair_eoff + lo), e = __ldg(A.pair_eoff + lo + 1);
+  if (!found) return false;
   auto tt = [&](uint32_t p) { return __ldg(A.pair_t + p); };
   *a = search_time<false>(s, e, tlo, tt);
   *b = hi_incl ? search_time<false>(*a, e, thi, tt) : search_time<true>(*a, e, thi, tt);
@@ -221,6 +274,21 @@ __device__ uint64_t list_count_merge(const int64_t* __restrict__ pt, const uint3
   return acc[l];
 }
 
+// ListCount of a gap with two or more lists (kept out of line so that its
+// arrays do not weigh on the single-list path).
+__device__ __noinline__ uint64_t gap_count_multi(const SamplerArgs& A, const Plan& P, int gp, int32_t up, int32_t u,
+                                                int32_t v, int32_t vp, int64_t tlo, int64_t thi, bool incl,
+                                                uint32_t* err) {
+  auto phi = [&](int role) { return role == 0 ? up : (role == 1 ? u : (role == 2 ? v : vp)); };
+  const int l = P.ngap[gp];
+  uint32_t a[16], b[16];
+  for (int j = 0; j < l; j++) {
+    if (!pair_window(A, phi(P.gx[gp][j]), phi(P.gy[gp][j]), tlo, thi, incl, &a[j], &b[j])) return 0;
+    if (a[j] == b[j]) return 0;
+  }
+  return list_count_merge(A.pair_t, a, b, l, err);
+}
+
 // CheckMotif (Alg. 3) of the path (u' -e1- u -e2- v -e3- v').
 __device__ __forceinline__ uint64_t check_motif(const SamplerArgs& A, const Plan& P, int32_t up, int32_t u,
                                                 int32_t v, int32_t vp, int64_t t1, int64_t t2, int64_t t3,
@@ -236,11 +304,8 @@ __device__ __forceinline__ uint64_t check_motif(const SamplerArgs& A, const Plan
   if (!(ta[0] < ta[1] && ta[1] < ta[2])) return 0;
   if ((uint64_t)ta[2] - (uint64_t)ta[0] > (uint64_t)A.delta) return 0;
   ++*checked;
-  int32_t phi[4];
-  phi[P.lab[0]] = up;
-  phi[P.lab[1]] = u;
-  phi[P.lab[2]] = v;
-  phi[P.lab[3]] = vp;
+  // phi of a motif vertex, by its role on the path (u', u, v, v')
+  auto phi = [&](int role) { return role == 0 ? up : (role == 1 ? u : (role == 2 ? v : vp)); };
   uint64_t X = 1;
   for (int gp = 0; gp < 3; gp++) {
     const int l = P.ngap[gp];
@@ -248,14 +313,14 @@ __device__ __forceinline__ uint64_t check_motif(const SamplerArgs& A, const Plan
     const int64_t tlo = ta[gp];
     const int64_t thi = gp < 2 ? ta[gp + 1] : sat_add(ta[0], A.delta);
     const bool incl = gp == 2;
-    uint32_t a[16], b[16];
-    for (int j = 0; j < l; j++) {
-      if (!pair_window(A, phi[P.gx[gp][j]], phi[P.gy[gp][j]], tlo, thi, incl, &a[j], &b[j])) return 0;
-      if (a[j] == b[j]) return 0;
-    }
     uint64_t c;
-    if (l == 1) c = b[0] - a[0];
-    else c = list_count_merge(A.pair_t, a, b, l, err);
+    if (l == 1) {  // one list: its length in the window
+      uint32_t a0, b0;
+      if (!pair_window(A, phi(P.gx[gp][0]), phi(P.gy[gp][0]), tlo, thi, incl, &a0, &b0)) return 0;
+      c = b0 - a0;
+    } else {
+      c = gap_count_multi(A, P, gp, up, u, v, vp, tlo, thi, incl, err);
+    }
     if (c == 0) return 0;
     const uint64_t hi = __umul64hi(X, c);
     if (hi) atomicOr(err, kErrOverflow);
@@ -264,8 +329,14 @@ __device__ __forceinline__ uint64_t check_motif(const SamplerArgs& A, const Plan
   return X;
 }
 
+// Resident blocks per SM the sampler is compiled for (caps its registers).
+#ifndef TC_SAMPLE_MIN_BLOCKS
+#define TC_SAMPLE_MIN_BLOCKS 4
+#endif
+
 template <bool Trace>
-__global__ void __launch_bounds__(256) k_sample(SamplerArgs A, Plan P) {
+__global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __grid_constant__ SamplerArgs A,
+                                                const __grid_constant__ Plan P) {
   const IndexHeader* H = A.hdr;
   const uint64_t W = H->W;
   const uint32_t shift = H->shift;
@@ -292,7 +363,8 @@ __global__ void __launch_bounds__(256) k_sample(SamplerArgs A, Plan P) {
   unsigned __int128 sx2 = 0;
   uint32_t err = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.k && W; i += stride) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < A.count && W; j += stride) {
+    const uint64_t i = A.chunk_base + (A.order ? __ldg(A.order + j) : j);  // sample index within the call
     const uint64_t s = A.offset + i;
     uint64_t r2, r1, r3;
     if (!bounded_draw(A.seed, s, 0, W, &r2)) { err |= kErrRng; continue; }
@@ -387,6 +459,196 @@ __global__ void __launch_bounds__(256) k_sample(SamplerArgs A, Plan P) {
   }
 }
 
+// Processing order of the samples.  Samples whose middle-edge draws r are
+// close share records, windows and pair lists, so each chunk of samples is
+// put in order of the top 16 bits of r by a two-pass most-significant-digit
+// counting sort: pass A partitions the samples by the high byte of the key
+// into 256 segments, pass B orders each segment by the low byte.  The order
+// of samples with equal keys is free, so ranks inside a tile come from
+// shared-memory atomics; tiles are staged in shared memory in digit order so
+// that global writes form contiguous runs.  The first pass draws r once per
+// sample and stores its 16-bit key.  Integer sums do not depend on the order.
+constexpr int kBuckets = 256;
+constexpr int kBucketItems = 16;
+constexpr int kBucketTile = 256 * kBucketItems;
+
+struct SegInfo {          // pass-B tiling of the 256 segments of pass A
+  uint32_t start[kBuckets + 1];      // first element of each segment
+  uint32_t ntiles[kBuckets];         // tiles of each segment
+  uint32_t tile_base[kBuckets + 1];  // first tile of each segment
+};
+
+// Pass A histogram: draws the keys (writing them in id order) and counts
+// their high bytes; hist[d * tiles + tile].
+__global__ void __launch_bounds__(256) k_key_hist(const IndexHeader* __restrict__ H, uint64_t seed, uint64_t first,
+                                                  uint64_t count, uint16_t* __restrict__ keys,
+                                                  uint32_t* __restrict__ hist, uint32_t tiles) {
+  __shared__ uint32_t cnt[kBuckets];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t W = H->W;
+  const int wbits = W > 1 ? 64 - __clzll(W - 1) : 0;
+  const int drop = wbits > 16 ? wbits - 16 : 0;
+  const uint64_t base = (uint64_t)blockIdx.x * kBucketTile;
+#pragma unroll 4
+  for (int it = 0; it < kBucketItems; it++) {
+    const uint64_t j = base + (uint64_t)it * 256 + threadIdx.x;
+    if (j < count) {
+      uint64_t r = 0;
+      if (W) bounded_draw(seed, first + j, 0, W, &r);  // a failed draw is flagged by the sampler
+      const uint32_t key = (uint32_t)(r >> drop);
+      keys[j] = (uint16_t)key;
+      atomicAdd(&cnt[key >> 8], 1u);
+    }
+  }
+  __syncthreads();
+  hist[(uint64_t)threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Scatter the elements [lo, hi) of one tile by digit (key >> shift) & 255 to
+// out_base[d] + rank, staging the tile in shared memory in digit order.
+// ids_in == NULL means the element's own position.
+__device__ __forceinline__ void tile_scatter(uint32_t lo, uint32_t hi, const uint16_t* __restrict__ keys_in,
+                                             const uint32_t* __restrict__ ids_in, int shift,
+                                             const uint32_t* s_out_base, uint16_t* __restrict__ keys_out,
+                                             uint32_t* __restrict__ ids_out, uint32_t* cnt, uint32_t* start,
+                                             uint32_t* warp_tot, uint32_t* stage, uint16_t* stage_k) {
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t key[kBucketItems], rank[kBucketItems];
+#pragma unroll
+  for (int it = 0; it < kBucketItems; it++) {
+    const uint32_t j = lo + (uint32_t)it * 256 + threadIdx.x;
+    key[it] = 0xFFFFFFFFu;
+    if (j < hi) {
+      key[it] = __ldg(keys_in + j);
+      rank[it] = atomicAdd(&cnt[(key[it] >> shift) & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  {  // exclusive scan of the tile's digit counts
+    const uint32_t v = cnt[threadIdx.x];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < wid; w++) before += warp_tot[w];
+    start[threadIdx.x] = before + inc - v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kBucketItems; it++) {
+    if (key[it] != 0xFFFFFFFFu) {
+      const uint32_t j = lo + (uint32_t)it * 256 + threadIdx.x;
+      const uint32_t p = start[(key[it] >> shift) & 255u] + rank[it];
+      stage[p] = ids_in ? __ldg(ids_in + j) : j;
+      stage_k[p] = (uint16_t)key[it];
+    }
+  }
+  __syncthreads();
+  const uint32_t n = hi - lo;
+  for (uint32_t i = threadIdx.x; i < n; i += 256) {
+    const uint32_t kk = stage_k[i];
+    const uint32_t d = (kk >> shift) & 255u;
+    const uint32_t g = s_out_base[d] + (i - start[d]);
+    ids_out[g] = stage[i];
+    if (keys_out) keys_out[g] = (uint16_t)kk;
+  }
+}
+
+// Pass A scatter: tile t of the chunk, by the high byte.
+__global__ void __launch_bounds__(256) k_key_scatter_a(uint64_t count, const uint16_t* __restrict__ keys,
+                                                       const uint32_t* __restrict__ offs, uint32_t tiles,
+                                                       uint16_t* __restrict__ keys_out,
+                                                       uint32_t* __restrict__ ids_out) {
+  __shared__ uint32_t cnt[kBuckets], start[kBuckets], base_s[kBuckets], warp_tot[8];
+  __shared__ uint32_t stage[kBucketTile];
+  __shared__ uint16_t stage_k[kBucketTile];
+  base_s[threadIdx.x] = offs[(uint64_t)threadIdx.x * tiles + blockIdx.x];
+  const uint64_t lo = (uint64_t)blockIdx.x * kBucketTile;
+  const uint64_t hi = lo + kBucketTile < count ? lo + kBucketTile : count;
+  tile_scatter((uint32_t)lo, (uint32_t)hi, keys, nullptr, 8, base_s, keys_out, ids_out, cnt, start, warp_tot, stage,
+               stage_k);
+}
+
+// Segment sizes from the scanned pass-A histogram and the pass-B tiling.
+__global__ void k_seg_info(const uint32_t* __restrict__ offs, uint32_t tiles, uint64_t count, SegInfo* info) {
+  __shared__ uint32_t nt[kBuckets + 1];
+  const int d = threadIdx.x;
+  const uint32_t s0 = offs[(uint64_t)d * tiles];
+  const uint32_t s1 = d + 1 < kBuckets ? offs[(uint64_t)(d + 1) * tiles] : (uint32_t)count;
+  info->start[d] = s0;
+  if (d == kBuckets - 1) info->start[kBuckets] = (uint32_t)count;
+  nt[d] = (s1 - s0 + kBucketTile - 1) / kBucketTile;
+  info->ntiles[d] = nt[d];
+  __syncthreads();
+  if (d == 0) {
+    uint32_t run = 0;
+    for (int i = 0; i < kBuckets; i++) {
+      info->tile_base[i] = run;
+      run += nt[i];
+    }
+    info->tile_base[kBuckets] = run;
+  }
+}
+
+// Segment and tile of pass-B block b (false past the last tile).
+__device__ __forceinline__ bool seg_tile(const SegInfo* info, uint32_t b, uint32_t* seg, uint32_t* t) {
+  if (b >= info->tile_base[kBuckets]) return false;
+  uint32_t lo = 0, hi = kBuckets - 1;  // last segment with tile_base <= b
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (info->tile_base[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  *seg = lo;
+  *t = b - info->tile_base[lo];
+  return true;
+}
+
+// Pass B: histogram of the low byte per (segment, digit, tile) at
+// tile_base[s] * 256 + d * ntiles[s] + t, so that one flat exclusive scan
+// gives every element's final position.
+__global__ void __launch_bounds__(256) k_key_hist_b(const uint16_t* __restrict__ keys, const SegInfo* __restrict__ info,
+                                                    uint32_t* __restrict__ hist) {
+  __shared__ uint32_t cnt[kBuckets];
+  uint32_t seg, t;
+  if (!seg_tile(info, blockIdx.x, &seg, &t)) return;
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t lo = info->start[seg] + t * kBucketTile;
+  const uint32_t end = info->start[seg + 1];
+  const uint32_t hi = lo + kBucketTile < end ? lo + kBucketTile : end;
+  for (uint32_t j = lo + threadIdx.x; j < hi; j += 256) atomicAdd(&cnt[__ldg(keys + j) & 255u], 1u);
+  __syncthreads();
+  hist[(uint64_t)info->tile_base[seg] * kBuckets + (uint64_t)threadIdx.x * info->ntiles[seg] + t] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_key_scatter_b(const uint16_t* __restrict__ keys,
+                                                       const uint32_t* __restrict__ ids,
+                                                       const SegInfo* __restrict__ info,
+                                                       const uint32_t* __restrict__ offs,
+                                                       uint32_t* __restrict__ ids_out) {
+  __shared__ uint32_t cnt[kBuckets], start[kBuckets], base_s[kBuckets], warp_tot[8];
+  __shared__ uint32_t stage[kBucketTile];
+  __shared__ uint16_t stage_k[kBucketTile];
+  uint32_t seg, t;
+  if (!seg_tile(info, blockIdx.x, &seg, &t)) return;
+  base_s[threadIdx.x] = offs[(uint64_t)info->tile_base[seg] * kBuckets + (uint64_t)threadIdx.x * info->ntiles[seg] + t];
+  const uint32_t lo = info->start[seg] + t * kBucketTile;
+  const uint32_t end = info->start[seg + 1];
+  const uint32_t hi = lo + kBucketTile < end ? lo + kBucketTile : end;
+  tile_scatter(lo, hi, keys, ids, 0, base_s, nullptr, ids_out, cnt, start, warp_tot, stage, stage_k);
+}
+
+constexpr uint64_t kSortedMinSamples = 1ull << 16;  // below this, samples run in id order
+constexpr uint64_t kChunkSamples = 1ull << 28;
+
 tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
                          const void* index, uint64_t k, uint64_t seed, uint64_t offset, uint64_t* trace,
                          SampleSums* d_sums, cudaStream_t st) {
@@ -395,15 +657,17 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   SamplerArgs A;
   A.out_e = g->out_e;
   A.in_e = g->in_e;
-  A.pair_off = g->pair_off;
-  A.pair_dst = g->pair_dst;
-  A.pair_eoff = g->pair_eoff;
+  A.pair_hash = g->pair_hash;
+  A.hash_mask = g->hash_mask;
   A.pair_t = g->pair_t;
   A.prefix = prefix;
   A.hdr = v.hdr;
   A.rec = v.rec;
   A.guide = v.guide;
   A.k = k;
+  A.order = nullptr;
+  A.chunk_base = 0;
+  A.count = k;
   A.m = (uint32_t)m;
   A.seed = seed;
   A.offset = offset;
@@ -421,16 +685,72 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample<false>, 256, 0);
     blocks_per_sm[ti] = b > 0 ? b : 1;
   }
-  uint64_t blocks = (uint64_t)num_sms() * blocks_per_sm[ti];
-  const uint64_t need = (k + 255) / 256;
-  if (need < blocks) blocks = need ? need : 1;
-  if (trace)
-    k_sample<true><<<(unsigned)blocks, 256, 0, st>>>(A, plan);
-  else
-    k_sample<false><<<(unsigned)blocks, 256, 0, st>>>(A, plan);
-  TC_LAUNCHED(1);
-  TC_CUDA(cudaGetLastError());
-  return TC_OK;
+  const uint64_t max_blocks = (uint64_t)num_sms() * blocks_per_sm[ti];
+  auto run = [&](const uint32_t* order, uint64_t base, uint64_t count) -> tc_status {
+    A.order = order;
+    A.chunk_base = base;
+    A.count = count;
+    uint64_t blocks = max_blocks;
+    const uint64_t need = (count + 255) / 256;
+    if (need < blocks) blocks = need ? need : 1;
+    if (trace)
+      k_sample<true><<<(unsigned)blocks, 256, 0, st>>>(A, plan);
+    else
+      k_sample<false><<<(unsigned)blocks, 256, 0, st>>>(A, plan);
+    TC_LAUNCHED(1);
+    TC_CUDA(cudaGetLastError());
+    return TC_OK;
+  };
+  if (k < kSortedMinSamples) return run(nullptr, 0, k);
+  // samples in chunks; each chunk is put in key order first
+  const uint64_t chunk = k < kChunkSamples ? k : kChunkSamples;
+  const uint64_t tiles_max = (chunk + kBucketTile - 1) / kBucketTile;
+  const uint64_t tiles_b_max = tiles_max + kBuckets;
+  const size_t hist_words = (size_t)kBuckets * tiles_b_max + 1;
+  char* buf = nullptr;
+  const size_t bytes = 12 * chunk + 4 * hist_words + sizeof(SegInfo) + 256;
+  TC_CUDA(cudaMallocAsync(&buf, bytes, st));
+  uint32_t* ids_a = (uint32_t*)buf;                  // after pass A
+  uint32_t* ids_b = (uint32_t*)(buf + 4 * chunk);    // after pass B
+  uint16_t* keys_0 = (uint16_t*)(buf + 8 * chunk);   // id order
+  uint16_t* keys_a = (uint16_t*)(buf + 10 * chunk);  // after pass A
+  uint32_t* hist = (uint32_t*)(buf + 12 * chunk);
+  SegInfo* info = (SegInfo*)(((uintptr_t)(hist + hist_words) + 255) & ~(uintptr_t)255);
+  tc_status s = TC_OK;
+  auto ok = [&](const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_status(e, what);
+    return s == TC_OK;
+  };
+  for (uint64_t base = 0; base < k && s == TC_OK; base += chunk) {
+    const uint64_t count = (k - base) < chunk ? (k - base) : chunk;
+    const uint32_t tiles = (uint32_t)((count + kBucketTile - 1) / kBucketTile);
+    const uint32_t tiles_b = tiles + kBuckets;
+    k_key_hist<<<tiles, 256, 0, st>>>(v.hdr, seed, offset + base, count, keys_0, hist, tiles);
+    TC_LAUNCHED(1);
+    if (!ok("k_key_hist")) break;
+    if ((s = scan_u32(hist, hist, (uint64_t)kBuckets * tiles, st)) != TC_OK) break;
+    k_key_scatter_a<<<tiles, 256, 0, st>>>(count, keys_0, hist, tiles, keys_a, ids_a);
+    TC_LAUNCHED(1);
+    if (!ok("k_key_scatter_a")) break;
+    k_seg_info<<<1, kBuckets, 0, st>>>(hist, tiles, count, info);
+    TC_LAUNCHED(1);
+    if (!ok("k_seg_info")) break;
+    if (cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)kBuckets * tiles_b, st) != cudaSuccess) {
+      s = cuda_status(cudaGetLastError(), "memset");
+      break;
+    }
+    k_key_hist_b<<<tiles_b, 256, 0, st>>>(keys_a, info, hist);
+    TC_LAUNCHED(1);
+    if (!ok("k_key_hist_b")) break;
+    if ((s = scan_u32(hist, hist, (uint64_t)kBuckets * tiles_b, st)) != TC_OK) break;
+    k_key_scatter_b<<<tiles_b, 256, 0, st>>>(keys_a, ids_a, info, hist, ids_b);
+    TC_LAUNCHED(1);
+    if (!ok("k_key_scatter_b")) break;
+    s = run(ids_b, base, count);
+  }
+  cudaFreeAsync(buf, st);
+  return s;
 }
 
 }  // namespace tc

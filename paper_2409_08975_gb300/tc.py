@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_OOM", 3: "TC_ERR
 WINDOW_STRICT, WINDOW_CLOSED = 0, 1
 
 ARRAYS = {"out_off": 0, "out_edges": 1, "edge_perm": 2, "in_off": 3, "in_edges": 4, "pair_off": 5,
-          "pair_dst": 6, "pair_eoff": 7, "pair_t": 8, "pair_eid": 9}
+          "pair_dst": 6, "pair_eoff": 7, "pair_t": 8, "pair_eid": 9, "in_eid": 10}
 
 
 class TcError(RuntimeError):
@@ -161,7 +161,7 @@ class Graph:
         shapes = {"out_off": (n1, torch.int32), "out_edges": (4 * m, torch.int32), "edge_perm": (m, torch.int32),
                   "in_off": (n1, torch.int32), "in_edges": (4 * m, torch.int32), "pair_off": (n1, torch.int32),
                   "pair_dst": (P, torch.int32), "pair_eoff": (P + 1, torch.int32), "pair_t": (m, torch.int64),
-                  "pair_eid": (m, torch.int32)}
+                  "pair_eid": (m, torch.int32), "in_eid": (m, torch.int32)}
         size, dt = shapes[name]
         out = torch.empty(max(size, 1), dtype=dt, device="cuda")
         _check(lib().tc_graph_copy(self.handle, ARRAYS[name], _ptr(out), _stream(stream)), "tc_graph_copy")

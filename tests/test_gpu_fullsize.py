@@ -41,7 +41,8 @@ def test_lists_full_size(setup):
     assert (oe[:, 0] == og.src[og.out_perm]).all() and (oe[:, 1] == og.dst[og.out_perm]).all()
     assert (g.array("out_off").cpu().numpy() == og.out_off).all()
     ie = g.array("in_edges").view(-1, 4).cpu().numpy()
-    assert (ie[:, 1].astype(np.int64) == og.in_eid).all()
+    assert (ie[:, 1] == og.dst[og.in_perm]).all()
+    assert (g.array("in_eid").cpu().numpy().astype(np.int64) == og.in_eid).all()
     assert (g.array("in_off").cpu().numpy() == og.in_off).all()
     assert g.num_pairs == og.P
     assert (g.array("pair_off").cpu().numpy() == og.pair_off).all()

@@ -76,7 +76,8 @@ def _check_csr(tc, g, og):
     assert (g.array("out_off").cpu().numpy() == og.out_off).all()
     ie = g.array("in_edges").view(-1, 4).cpu().numpy()
     assert (ie[:, 0] == src[og.in_perm]).all()
-    assert (ie[:, 1].astype(np.int64) == og.in_eid).all()
+    assert (ie[:, 1] == og.dst[og.in_perm]).all()
+    assert (g.array("in_eid").cpu().numpy().astype(np.int64) == og.in_eid).all()
     assert (ie[:, 2:].copy().view(np.int64)[:, 0] == t[og.in_perm]).all()
     assert (g.array("in_off").cpu().numpy() == og.in_off).all()
     assert g.num_pairs == og.P
@@ -148,6 +149,26 @@ def test_sampler_trace_and_sums_bit_exact(tc, case):
             c_hat, se = oracle.estimate(osums["sum_x"], osums["sum_x2"], k, int(opre[-1]))
             assert est["estimate"] == pytest.approx(c_hat, rel=REL_TOL, abs=0)
             assert est["std_err"] == pytest.approx(se, rel=REL_TOL, abs=0)
+
+
+@pytest.mark.parametrize("case", GRAPHS[2:], ids=lambda c: c[0])
+def test_key_sorted_sampling_bit_exact(tc, case):
+    # from 2^16 samples on, the library processes each chunk's samples sorted
+    # by middle-edge key; ids, indices and X must still match the oracle
+    name, n, src, dst, t = case
+    g, og = _build_both(tc, n, src, dst, t)
+    for edges in (CHORD, MULTI):
+        plan = oracle.compile_motif(edges)
+        mot = tc.make_motif(edges)
+        w = tc.tc_path_weights(g, mot, 10_000)
+        opre = oracle.prefix_sum(oracle.path_weights(og, plan, 10_000)["w"])
+        k, seed, off = 70_001, 99, 1 << 40
+        tr = _u64(tc.tc_sample_trace(g, mot, 10_000, w, k, seed, off))
+        osums, otr = oracle.sample_run(og, plan, 10_000, opre, k, seed, off, trace=True)
+        assert (tr == otr).all()
+        est = tc.tc_sample_estimate(g, mot, 10_000, w, k, seed, off)
+        for key in ("sum_x", "sum_x2", "hits"):
+            assert est[key] == osums[key]
 
 
 def test_tiny_config_estimate(tc):
