@@ -19,9 +19,10 @@ Contents (each function names the passage it follows):
   * ``exact_count``       -- chronological backtracking count of M-matches (Def. 2)
   * ``brute_force_count`` -- literal Def. 2 over all edge tuples (tiny graphs)
   * ``estimate``          -- C_hat = (sum X / k) * W (Alg. 5) and its standard error
-  * ``mlp``               -- FP64 reference of the learned proposal's network
+  * ``learned``           -- features, FP64 network, proposal sampler (learned proposal)
 
 Parity of every function here is pinned by the ``-m "not gpu"`` tests against
 closed forms, brute force and published known answers; see the test files.
 """
 from .core import *  # noqa: F401,F403
+from . import learned  # noqa: F401

@@ -601,3 +601,147 @@ int or_exact_count(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
   free(tperm);
   return S.ovf ? OR_OVERFLOW : OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned proposal (not in the paper; the estimator stays that of Alg. 5    */
+/* with the middle edge drawn proportional to w_e * h_e instead of w_e).     */
+
+/* Edge features, all log1p of counts, per canonical edge (row-major [m][12]):
+ *  0 d1 and 1 d3 (the anchor's windows, Claim 1), 2 w = d1 * d3,
+ *  3..6 in- and out-degree of u, then of v, over [t - delta, t + delta],
+ *  7 multiplicity sigma_{u,v}[t - delta, t + delta] (Def. 3),
+ *  8 sigma_{v,u}[t - delta, t + delta],
+ *  9 total out-degree of u, 10 total in-degree of v, 11 total in-degree of u.
+ * Counts are taken from the plain definitions on the lists. */
+int or_edge_features(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const int64_t *t,
+                     const int64_t *out_perm, const int64_t *out_off, const int64_t *in_perm,
+                     const int64_t *in_off, const int64_t *pair_perm, const int64_t *pair_off,
+                     const int32_t *pair_dst, const int64_t *pair_eoff, const int32_t *plan_arr,
+                     int64_t delta, double *feat) {
+  or_graph g = {n, m, src, dst, t, out_perm, out_off, in_perm, in_off,
+                pair_perm, pair_off, pair_eoff, pair_dst};
+  or_plan pl;
+  read_plan(plan_arr, &pl);
+  for (int64_t i = 0; i < m; i++) {
+    int64_t e = out_perm[i];
+    int64_t u = src[e], v = dst[e], te = t[e];
+    int64_t a, b, c, d;
+    window_list(&g, pl.alpha1, pl.beta1, pl.closed, u, te, delta, &a, &b);
+    window_list(&g, pl.alpha3, pl.beta3, pl.closed, v, te, delta, &c, &d);
+    double *f = feat + 12 * i;
+    int64_t lo = sat_sub(te, delta), hi = sat_add(te, delta);
+    f[0] = (double)(b - a);
+    f[1] = (double)(d - c);
+    f[2] = (double)((uint64_t)(b - a) * (uint64_t)(d - c));
+    f[3] = (double)(first_gt(in_perm, t, in_off[u], in_off[u + 1], hi) - first_ge(in_perm, t, in_off[u], in_off[u + 1], lo));
+    f[4] = (double)(first_gt(out_perm, t, out_off[u], out_off[u + 1], hi) - first_ge(out_perm, t, out_off[u], out_off[u + 1], lo));
+    f[5] = (double)(first_gt(in_perm, t, in_off[v], in_off[v + 1], hi) - first_ge(in_perm, t, in_off[v], in_off[v + 1], lo));
+    f[6] = (double)(first_gt(out_perm, t, out_off[v], out_off[v + 1], hi) - first_ge(out_perm, t, out_off[v], out_off[v + 1], lo));
+    int64_t pa, pb;
+    pair_window(&g, u, v, lo == INT64_MIN ? INT64_MIN : lo - 1, hi, 1, &pa, &pb);
+    f[7] = (double)(pb - pa);
+    pair_window(&g, v, u, lo == INT64_MIN ? INT64_MIN : lo - 1, hi, 1, &pa, &pb);
+    f[8] = (double)(pb - pa);
+    f[9] = (double)(out_off[u + 1] - out_off[u]);
+    f[10] = (double)(in_off[v + 1] - in_off[v]);
+    f[11] = (double)(in_off[u + 1] - in_off[u]);
+  }
+  return OR_OK;
+}
+
+/*
+ * Sampling with the proposal q_e = w_e * h_e: the middle edge is the unique
+ * e with qprefix[e] <= r < qprefix[e+1] for r uniform in [0, Q); e1 and e3
+ * uniform in their windows as in Alg. 2.  Per sample Y = X * Q / h_e is
+ * unbiased; it is accumulated exactly per value of h:
+ *   bins[3*(h - h_lo) + 0] = sum of X, + 1 = sum of X^2 (low), + 2 = (high)
+ * for h in [h_lo, h_hi].  trace (optional) as in or_sample_run.
+ * sums[0..2] = (hits, checked-free count of samples, k).
+ */
+int or_sample_run_q(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const int64_t *t,
+                    const int64_t *out_perm, const int64_t *out_off, const int64_t *in_perm,
+                    const int64_t *in_off, const int64_t *pair_perm, const int64_t *pair_off,
+                    const int32_t *pair_dst, const int64_t *pair_eoff, const int32_t *plan_arr,
+                    int64_t delta, const uint64_t *qprefix, const uint16_t *h, uint32_t h_lo, uint32_t h_hi,
+                    uint64_t k, uint64_t seed, uint64_t offset, uint64_t *trace, uint64_t *bins,
+                    uint64_t *sums) {
+  or_graph g = {n, m, src, dst, t, out_perm, out_off, in_perm, in_off,
+                pair_perm, pair_off, pair_eoff, pair_dst};
+  or_plan pl;
+  read_plan(plan_arr, &pl);
+  uint64_t Q = qprefix[m], hits = 0;
+  int ovf = 0;
+  for (uint64_t b = 0; b < 3ull * (h_hi - h_lo + 1); b++) bins[b] = 0;
+  sums[0] = sums[1] = 0; sums[2] = k;
+  if (Q == 0) return OR_OK;
+  for (uint64_t i = 0; i < k; i++) {
+    uint64_t s = offset + i, r2, r1, r3;
+    int st = or_bounded(seed, s, 0, Q, &r2);
+    if (st) return st;
+    int64_t lo = 0, hi = m; /* qprefix[lo] <= r2 < qprefix[hi] */
+    while (hi - lo > 1) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (qprefix[mid] <= r2) lo = mid; else hi = mid;
+    }
+    int64_t i2 = lo, e2 = out_perm[i2];
+    int64_t a, b, c, d;
+    window_list(&g, pl.alpha1, pl.beta1, pl.closed, src[e2], t[e2], delta, &a, &b);
+    window_list(&g, pl.alpha3, pl.beta3, pl.closed, dst[e2], t[e2], delta, &c, &d);
+    st = or_bounded(seed, s, 1, (uint64_t)(b - a), &r1);
+    if (st) return st;
+    st = or_bounded(seed, s, 2, (uint64_t)(d - c), &r3);
+    if (st) return st;
+    int64_t p1 = a + (int64_t)r1, p3 = c + (int64_t)r3;
+    uint64_t X = check_motif(&g, &pl, delta, i2, p1, p3, &ovf);
+    if (trace) {
+      trace[4 * i + 0] = (uint64_t)i2; trace[4 * i + 1] = (uint64_t)p1;
+      trace[4 * i + 2] = (uint64_t)p3; trace[4 * i + 3] = X;
+    }
+    uint32_t hv = h[i2];
+    if (hv < h_lo || hv > h_hi) return OR_INVALID;
+    uint64_t *bin = bins + 3 * (hv - h_lo);
+    uint64_t s1 = bin[0] + X;
+    if (s1 < bin[0]) ovf = 1;
+    bin[0] = s1;
+    u128 x2 = ((u128)bin[2] << 64 | bin[1]) + (u128)X * X;
+    bin[1] = (uint64_t)x2; bin[2] = (uint64_t)(x2 >> 64);
+    hits += X > 0;
+  }
+  sums[0] = hits;
+  return ovf ? OR_OVERFLOW : OR_OK;
+}
+
+/* Exhaustive sums for the proposal: out[0..1] = sum over all class paths P
+ * of C_P^2 / h_{e(P)} as a fraction num / den is not exact in integers, so
+ * the per-h sums are returned instead: acc[3*(h - h_lo) + 0] = sum of C_P,
+ * + 1 / + 2 = sum of C_P^2 (low, high), over paths whose middle edge has h. */
+int or_path_sum_q(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const int64_t *t,
+                  const int64_t *out_perm, const int64_t *out_off, const int64_t *in_perm,
+                  const int64_t *in_off, const int64_t *pair_perm, const int64_t *pair_off,
+                  const int32_t *pair_dst, const int64_t *pair_eoff, const int32_t *plan_arr,
+                  int64_t delta, const uint16_t *h, uint32_t h_lo, uint32_t h_hi, uint64_t *acc) {
+  or_graph g = {n, m, src, dst, t, out_perm, out_off, in_perm, in_off,
+                pair_perm, pair_off, pair_eoff, pair_dst};
+  or_plan pl;
+  read_plan(plan_arr, &pl);
+  int ovf = 0;
+  for (uint64_t b = 0; b < 3ull * (h_hi - h_lo + 1); b++) acc[b] = 0;
+  for (int64_t i2 = 0; i2 < m; i2++) {
+    int64_t e2 = out_perm[i2];
+    int64_t a, b, c, d;
+    window_list(&g, pl.alpha1, pl.beta1, pl.closed, src[e2], t[e2], delta, &a, &b);
+    window_list(&g, pl.alpha3, pl.beta3, pl.closed, dst[e2], t[e2], delta, &c, &d);
+    if (a == b || c == d) continue;
+    uint32_t hv = h[i2];
+    if (hv < h_lo || hv > h_hi) return OR_INVALID;
+    uint64_t *bin = acc + 3 * (hv - h_lo);
+    for (int64_t p1 = a; p1 < b; p1++)
+      for (int64_t p3 = c; p3 < d; p3++) {
+        uint64_t X = check_motif(&g, &pl, delta, i2, p1, p3, &ovf);
+        bin[0] += X;
+        u128 x2 = ((u128)bin[2] << 64 | bin[1]) + (u128)X * X;
+        bin[1] = (uint64_t)x2; bin[2] = (uint64_t)(x2 >> 64);
+      }
+  }
+  return ovf ? OR_OVERFLOW : OR_OK;
+}

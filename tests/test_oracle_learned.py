@@ -1,0 +1,138 @@
+"""Pins of the learned-proposal oracle (no GPU): bf16 rounding against
+torch's conversion, features against literal counting, the FP64 backward
+against central finite differences, and the proposal sampler against the
+plain sampler (h = 1) and the unbiasedness of Claim 2 with the exact variance
+Q sum_P C_P^2 / h_P - C^2."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import learned as L
+from _graphs import small_random_graph
+
+CHORD = [(0, 1), (1, 2), (2, 3), (0, 3)]
+C4 = [(0, 1), (1, 2), (2, 3), (3, 0)]
+
+
+def test_bf16_matches_torch_conversion():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-6, 6, 20000),
+                        np.array([0.0, 1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.5, 65504.0])]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert (L.bf16(x) == ref).all()
+    assert L.bf16(np.float32(1.0 + 2 ** -8)) == 1.0            # tie goes to even
+    assert L.bf16(np.float32(1.0 + 3 * 2 ** -9)) == 1.0 + 2 ** -7
+
+
+def test_features_literal_counts():
+    src, dst, t = small_random_graph(31, 7, 90, 70, dup_frac=0.3)
+    g = oracle.build_csr(7, src, dst, t)
+    plan = oracle.compile_motif(CHORD)
+    delta = 9
+    f = L.edge_features(g, plan, delta)
+    pw = oracle.path_weights(g, plan, delta)
+    for i, e in enumerate(g.out_perm):
+        u, v, te = int(src[e]), int(dst[e]), int(t[e])
+        win = (t >= te - delta) & (t <= te + delta)
+        exp = [pw["d1"][i], pw["d3"][i], int(pw["w"][i]),
+               int(((dst == u) & win).sum()), int(((src == u) & win).sum()),
+               int(((dst == v) & win).sum()), int(((src == v) & win).sum()),
+               int(((src == u) & (dst == v) & win).sum()), int(((src == v) & (dst == u) & win).sum()),
+               int((src == u).sum()), int((dst == v).sum()), int((dst == u).sum())]
+        assert list(f[i]) == exp, i
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    params = L.init_params(rng)
+    x = np.zeros((40, 16))
+    x[:, :12] = rng.uniform(0, 3, (40, 12))
+    y = (rng.random(40) < 0.3).astype(np.float64)
+    grads, _ = L.mlp_backward(params, x, y, round_acts=False, quantized=False)
+    h = 1e-6
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        p = params[name]
+        flat = p.reshape(-1)
+        idx = rng.choice(flat.size, size=min(12, flat.size), replace=False)
+        if name == "W1":
+            idx = [i for i in idx if i % 16 < 12] or [0]
+        for j in idx:
+            old = flat[j]
+            flat[j] = old + h
+            lp = L.bce_loss(L.mlp_forward(params, x, False, False)[0], y)
+            flat[j] = old - h
+            lm = L.bce_loss(L.mlp_forward(params, x, False, False)[0], y)
+            flat[j] = old
+            fd = (lp - lm) / (2 * h)
+            an = grads[name].reshape(-1)[j]
+            assert abs(fd - an) <= 1e-6 + 1e-5 * abs(fd), (name, j, fd, an)
+
+
+def test_pack_roundtrip_and_size():
+    params = L.init_params(np.random.default_rng(1))
+    flat = L.pack(params)
+    assert flat.size == L.N_PARAMS == 5313
+    back = L.unpack(flat)
+    for k in params:
+        assert np.array_equal(back[k], np.asarray(params[k]).reshape(back[k].shape))
+
+
+def test_proposal_h_closed_forms():
+    h = L.proposal_h([0.0, 1.0, 0.5], 0.05, 1024)
+    assert h.tolist() == [51, 1075, 563]          # floor(1024 * 0.05 + .5) = 51, etc.
+    assert L.proposal_h([0.0], 0.0, 1024).tolist() == [1]
+
+
+def _graph():
+    src, dst, t = small_random_graph(77, 6, 60, 60, dup_frac=0.3)
+    return src, dst, t, oracle.build_csr(6, src, dst, t)
+
+
+def test_unit_proposal_is_the_plain_sampler():
+    src, dst, t, g = _graph()
+    plan = oracle.compile_motif(C4)
+    w = oracle.path_weights(g, plan, 20)["w"]
+    pre = oracle.prefix_sum(w)
+    h = np.ones(g.m, np.uint16)
+    qs, qtr = L.sample_run_q(g, plan, 20, L.qprefix(w, h), h, 3000, 4, 10, trace=True)
+    ps, ptr = oracle.sample_run(g, plan, 20, pre, 3000, 4, 10, trace=True)
+    assert (qtr == ptr).all()
+    assert qs["B"] == [ps["sum_x"]] and qs["B2"] == [ps["sum_x2"]] and qs["hits"] == ps["hits"]
+    est_q, se_q = L.estimate_q(qs["B"], qs["B2"], 1, qs["Q"], 3000)
+    est_p, se_p = oracle.estimate(ps["sum_x"], ps["sum_x2"], 3000, int(pre[-1]))
+    assert est_q == pytest.approx(est_p, rel=1e-12) and se_q == pytest.approx(se_p, rel=1e-9)
+
+
+def test_proposal_unbiased_over_1000_seeds_and_exact_variance():
+    src, dst, t, g = _graph()
+    plan = oracle.compile_motif(C4)
+    delta = 20
+    w = oracle.path_weights(g, plan, delta)["w"]
+    rng = np.random.default_rng(3)
+    h = rng.integers(1, 40, g.m).astype(np.uint16)
+    qpre = L.qprefix(w, h)
+    Q = int(qpre[-1])
+    h_lo, S1, S2 = L.path_sum_q(g, plan, delta, h)
+    C = oracle.brute_force_count(src, dst, t, C4, delta)
+    assert sum(S1) == C > 0                         # every match has one anchor path
+    var = L.exact_variance_q(Q, C, h_lo, S2)
+    assert var >= 0
+    # with h = 1 the formula is the plain variance W sum C_P^2 - C^2
+    ps = oracle.path_sum(g, plan, delta)
+    W = int(oracle.prefix_sum(w)[-1])
+    one = np.ones(g.m, np.uint16)
+    lo1, T1, T2 = L.path_sum_q(g, plan, delta, one)
+    assert L.exact_variance_q(W, C, lo1, T2) == Fraction(W) * ps["sum_x2"] - C * C
+    k, seeds = 200, 1000
+    ests = []
+    for seed in range(seeds):
+        s, _ = L.sample_run_q(g, plan, delta, qpre, h, k, seed)
+        ests.append(L.estimate_q(s["B"], s["B2"], s["h_lo"], Q, k)[0])
+    sd_mean = math.sqrt(float(var) / k / seeds)
+    assert abs(np.mean(ests) - C) <= 2.576 * sd_mean
+    sd_run = math.sqrt(float(var) / k)
+    assert 0.8 * sd_run < np.std(ests) < 1.2 * sd_run
