@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--samples", type=int, default=None, help="samples per step (default: the config's k)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
+    ap.add_argument("--train-samples", type=int, default=10_000_000)
     return ap.parse_args()
 
 
@@ -181,6 +183,52 @@ def run_reference(args, rank, world):
     }))
 
 
+def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weights_ms, n_train, stream):
+    """Learned proposal q ~ w (eps + g) against the plain q ~ w on the same
+    graph: features, training on n_train plain samples and the proposal are
+    timed once; then k samples with the proposal.  Relative error at a fixed
+    GPU time follows from the per-sample variance (k SE^2) and the GPU time
+    per sample of each sampler."""
+    import torch
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    feat, feat_ms = timed(lambda: tc.tc_edge_features(g, mot, delta, wts))
+    mlp = tc.MLP(seed=1)
+    losses, train_ms = timed(lambda: tc.tc_mlp_train(mlp, g, mot, delta, wts, feat, n_train, seed=12345,
+                                                     batch=16384, lr=3e-3))
+    prop, prop_ms = timed(lambda: tc.tc_proposal_weights(mlp, g, mot, delta, wts, feat))
+    runs = []
+    for i in range(4):
+        r, ms = timed(lambda: tc.tc_sample_estimate_q(g, mot, delta, wts, prop, k, seed=0, offset=(50 + i) * k))
+        runs.append((r, ms))
+    q_ms = statistics.median(ms for _, ms in runs[1:])
+    rq = runs[-1][0]
+    var_plain = plain["std_err"] ** 2 * k
+    var_learned = rq["std_err"] ** 2 * k
+    c = rq["estimate"]
+
+    def t_1pct(var, ms_per_sample):  # sampling time for a 1% relative standard error
+        return var / (0.01 * c) ** 2 * ms_per_sample
+
+    tp = t_1pct(var_plain, plain_sampler_ms / k)
+    tl = t_1pct(var_learned, q_ms / k)
+    mlp.destroy()
+    return {"train_samples": n_train, "train_ms": train_ms, "features_ms": feat_ms, "proposal_ms": prop_ms,
+            "loss_first_batch": losses[0], "loss_last_batch": losses[1],
+            "sampler_ms": q_ms, "samples_per_s": k / (q_ms / 1e3), "estimate": c, "std_err": rq["std_err"],
+            "plain_estimate": plain["estimate"], "plain_std_err": plain["std_err"],
+            "variance_ratio_learned_over_plain": var_learned / var_plain,
+            "time_to_1pct_ms_plain": tp, "time_to_1pct_ms_learned": tl, "time_ratio_learned_over_plain": tl / tp,
+            "time_ratio_with_setup": (tl + feat_ms + train_ms + prop_ms) / (tp + weights_ms)}
+
+
 def config_dict(cfg, k, world):
     return {"workload": "mid: Chung-Lu n=1M m=20M gamma=2.1 max_deg~1e5 30% multi-edges, bursty times over 1e8 s; "
                         "motif a->b,b->c,c->d,a->d (path+chord), delta=3600, k=1e8 samples per step",
@@ -313,6 +361,9 @@ def main():
         e2e = {"value": world * k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * m, "d2h_bytes_per_step": 92,
                "ms_per_step": e2e_s * 1e3}
 
+    learned = None if args.no_learned else learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
+                                                              args.train_samples, stream)
+
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(cfg, k)[0]
@@ -325,7 +376,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_dict(cfg, k, world),
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-            "cpu_baseline": base, "csr_build_ms": csr_ms, "weights": weights,
+            "cpu_baseline": base, "csr_build_ms": csr_ms, "weights": weights, "learned": learned,
             "estimate": {"W": r0["W"], "estimate": r0["estimate"], "std_err": r0["std_err"], "hits": r0["hits"],
                          "checked": r0["checked"]},
         }))

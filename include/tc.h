@@ -180,16 +180,14 @@ tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delt
  * X = prod over gaps of ListCount (Alg. 3, 4).
  *   d_prefix, d_index  as filled by tc_path_weights for the same graph,
  *                      motif and delta (checked on the device)
- *   d_h       reserved for a learned proposal; pass NULL
  *   h_out     receives the sums and the estimate (synchronises the stream)
  * Ranges [offset, offset + k) of one seed can be merged by adding the sums.
  * Errors: TC_ERR_INVALID_ARG, TC_ERR_OVERFLOW, TC_ERR_RNG_EXHAUSTED,
  * TC_ERR_CUDA.
  */
 tc_status tc_sample_estimate(const tc_graph* g, const tc_motif* motif, int64_t delta,
-                             const uint64_t* d_prefix, const void* d_index, const uint16_t* d_h,
-                             uint64_t k, uint64_t seed, uint64_t sample_offset, tc_estimate* h_out,
-                             void* stream);
+                             const uint64_t* d_prefix, const void* d_index, uint64_t k, uint64_t seed,
+                             uint64_t sample_offset, tc_estimate* h_out, void* stream);
 
 /*
  * Same sampling as tc_sample_estimate for `count` samples, writing per sample
@@ -241,6 +239,98 @@ tc_status tc_prefix_sum_noalloc(const uint64_t* d_w, uint64_t m, uint64_t* d_pre
  * middle, e3), h_class[4] = (alpha1, alpha3, beta1, beta3) with -1 for '-' /
  * '<' and +1 for '+' / '>'.  Host only. */
 tc_status tc_motif_plan(const tc_motif* motif, int32_t* h_anchor, int32_t* h_class);
+
+/* ------------------------------------------------------------------------
+ * Learned proposal.  The paper's estimator draws the middle edge with
+ * probability w_e / W (Alg. 2).  Any proposal q_e = w_e h_e with integer
+ * h_e >= 1 keeps it unbiased when each path is weighted by Q / h_e, with
+ * Q = sum_e q_e (Claim 2's argument path by path).  Here h_e comes from a
+ * small network g(e) in (0, 1) trained to predict whether a path through e
+ * completes the motif: h_e = max(1, floor(scale (eps + g_e) + 1/2)).
+ * The network: 12 features -> 64 -> 64 -> 1 with ReLU and a sigmoid output,
+ * bf16 operands and FP32 accumulation; TC_MLP_PARAMS FP32 parameters laid out
+ * as W1[64][16] (columns 12..15 unused, kept 0), b1[64], W2[64][64], b2[64],
+ * W3[64], b3.
+ * ------------------------------------------------------------------------ */
+typedef struct tc_mlp tc_mlp;
+#define TC_MLP_PARAMS 5313
+#define TC_FEATURE_STRIDE 16 /* bf16 values per feature row (12 used) */
+#define TC_PROPOSAL_MAX_H 4095
+
+/* New network with weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)) drawn from
+ * Philox keyed by seed; device memory on the current device. */
+tc_status tc_mlp_create(uint64_t seed, tc_mlp** out);
+tc_status tc_mlp_destroy(tc_mlp* mlp);
+/* Copy the FP32 parameters to / from host memory (TC_MLP_PARAMS floats);
+ * setting them resets the optimizer state. */
+tc_status tc_mlp_get_params(const tc_mlp* mlp, float* h_params);
+tc_status tc_mlp_set_params(tc_mlp* mlp, const float* h_params);
+
+/*
+ * Per canonical edge e = (u, v, t), bf16 features (row stride 16, last 4 zero),
+ * each log1p of a count: 0 d1, 1 d3, 2 w_e (the anchor's windows, Claim 1),
+ * 3..6 in- and out-degree of u, then of v, over [t - delta, t + delta],
+ * 7 sigma_{u,v}[t - delta, t + delta], 8 sigma_{v,u}[t - delta, t + delta]
+ * (Def. 3), 9 out-degree of u, 10 in-degree of v, 11 in-degree of u.
+ *   d_index  as filled by tc_path_weights for the same graph, motif, delta
+ *   d_feat   uint16 (bf16 bits) [m][16] output
+ */
+tc_status tc_edge_features(const tc_graph* g, const tc_motif* motif, int64_t delta, const void* d_index,
+                           uint16_t* d_feat, void* stream);
+
+/* Logits z of rows d_rows[i] (or i when d_rows is NULL) of d_feat into
+ * d_logits[n] (FP32); g = sigmoid(z). */
+tc_status tc_mlp_forward(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, uint64_t n,
+                         float* d_logits, void* stream);
+
+/* Gradient of the mean binary cross-entropy of sigmoid(z) against d_labels
+ * (0 or 1) over n rows into d_grad[TC_MLP_PARAMS] (FP32, overwritten);
+ * h_loss (optional) receives the mean loss.  Synchronises the stream. */
+tc_status tc_mlp_grad(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, const float* d_labels,
+                      uint64_t n, float* d_grad, float* h_loss, void* stream);
+
+/*
+ * Train on n_samples paths drawn by the plain sampler (tc_sample_trace with
+ * seed, ids 0..n_samples-1): input the features of the middle edge, label
+ * [X > 0].  One pass of Adam (lr, betas 0.9 / 0.999) in batches of `batch`.
+ * h_losses (optional) receives the mean loss of the first and last batch.
+ * Synchronises the stream.
+ */
+tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, int64_t delta,
+                       const uint64_t* d_prefix, const void* d_index, const uint16_t* d_feat,
+                       uint64_t n_samples, uint64_t seed, uint32_t batch, float lr, float* h_losses,
+                       void* stream);
+
+/* Bytes of a proposal index (header and guide table) for graph g. */
+tc_status tc_proposal_index_bytes(const tc_graph* g, size_t* h_bytes);
+
+/*
+ * Proposal weights: d_h[m] (uint16) = max(1, floor(scale (eps + g_e) + 1/2)),
+ * d_qprefix[m+1] the exact prefix sum of w_e h_e (w_e from d_prefix), and the
+ * proposal's sampling index d_qindex (tc_proposal_index_bytes, 256-byte
+ * aligned).  scale >= 1, eps >= 0, scale (1 + eps) + 1 <= TC_PROPOSAL_MAX_H.
+ * h_Q (optional) receives Q = d_qprefix[m] and reports overflow.
+ */
+tc_status tc_proposal_weights(const tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, int64_t delta,
+                              const uint64_t* d_prefix, const uint16_t* d_feat, float eps, uint32_t scale,
+                              uint16_t* d_h, uint64_t* d_qprefix, void* d_qindex, uint64_t* h_Q,
+                              void* stream);
+
+/*
+ * Sampling with the proposal: sample s draws r uniform in [0, Q) (draw 0)
+ * and the middle edge e with qprefix[e] <= r < qprefix[e+1]; e1, e3 and X as
+ * in tc_sample_estimate.  The exact per-h sums B_h = sum X and B2_h = sum X^2
+ * give C_hat = Q / k * sum over ascending h of B_h / h (FP64 on the host).
+ *   d_index   the plain index of the same graph, motif and delta (records)
+ *   h_bins    optional host array [3 * (TC_PROPOSAL_MAX_H + 1)]: per h,
+ *             B_h, B2_h low 64 bits, B2_h high 64 bits
+ *   d_trace   optional [4 * k] as in tc_sample_trace
+ * h_out->W receives Q.  Synchronises the stream.
+ */
+tc_status tc_sample_estimate_q(const tc_graph* g, const tc_motif* motif, int64_t delta, const void* d_index,
+                               const uint16_t* d_h, const uint64_t* d_qprefix, const void* d_qindex,
+                               uint64_t k, uint64_t seed, uint64_t sample_offset, tc_estimate* h_out,
+                               uint64_t* h_bins, uint64_t* d_trace, void* stream);
 
 /* Number of kernels this library has launched in this process so far
  * (a diagnostic for counting launches around a region). */

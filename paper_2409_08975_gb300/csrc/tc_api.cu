@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "tc_internal.cuh"
 
@@ -356,9 +357,8 @@ static tc_status sample_common(const tc_graph* g, const tc_motif* motif, int64_t
 }
 
 tc_status tc_sample_estimate(const tc_graph* g, const tc_motif* motif, int64_t delta, const uint64_t* d_prefix,
-                             const void* d_index, const uint16_t* d_h, uint64_t k, uint64_t seed,
-                             uint64_t sample_offset, tc_estimate* h_out, void* stream) {
-  if (d_h) return set_error(TC_ERR_INVALID_ARG, "d_h is reserved; pass NULL");
+                             const void* d_index, uint64_t k, uint64_t seed, uint64_t sample_offset,
+                             tc_estimate* h_out, void* stream) {
   if (!h_out) return set_error(TC_ERR_INVALID_ARG, "out is NULL");
   return sample_common(g, motif, delta, d_prefix, d_index, k, seed, sample_offset, nullptr, h_out, stream,
                        "tc_sample_estimate");
@@ -408,12 +408,263 @@ tc_status tc_estimate_from_host(int64_t n, int64_t m, const int32_t* h_src, cons
   }
   uint64_t W = 0;
   if (s == TC_OK) s = tc_path_weights(g, motif, delta, nullptr, d_prefix, d_index, &W, stream);
-  if (s == TC_OK) s = tc_sample_estimate(g, motif, delta, d_prefix, d_index, nullptr, k, seed, 0, h_out, stream);
+  if (s == TC_OK) s = tc_sample_estimate(g, motif, delta, d_prefix, d_index, k, seed, 0, h_out, stream);
   if (d_prefix) cudaFreeAsync(d_prefix, st);
   if (d_index) cudaFreeAsync(d_index, st);
   cudaStreamSynchronize(st);
   if (g) tc_graph_destroy(g);
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// Learned proposal.
+
+static tc_status check_index_header(const tc_graph* g, const Plan& plan, int64_t delta, const void* d_index,
+                                    cudaStream_t st) {
+  IndexHeader h;
+  TC_CUDA(cudaMemcpyAsync(&h, d_index, sizeof(h), cudaMemcpyDeviceToHost, st));
+  TC_CUDA(cudaStreamSynchronize(st));
+  const bool ok = h.magic == kIndexMagic && h.graph_id == g->id && h.delta == delta && h.cls[0] == plan.alpha1 &&
+                  h.cls[1] == plan.alpha3 && h.cls[2] == plan.beta1 && h.cls[3] == plan.beta3 &&
+                  h.closed == plan.closed && h.anchor[0] == plan.e1 && h.anchor[1] == plan.mid &&
+                  h.anchor[2] == plan.e3;
+  if (!ok) return set_error(TC_ERR_INVALID_ARG, "index was built for another graph, motif or delta");
+  if (h.status) return device_status(h.status, "index");
+  return TC_OK;
+}
+
+tc_status tc_mlp_create(uint64_t seed, tc_mlp** out) {
+  if (!out) return set_error(TC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  return mlp_create(seed, out);
+}
+
+tc_status tc_mlp_destroy(tc_mlp* mlp) {
+  if (mlp) mlp_destroy(mlp);
+  return TC_OK;
+}
+
+tc_status tc_mlp_get_params(const tc_mlp* mlp, float* h_params) {
+  if (!mlp || !h_params) return set_error(TC_ERR_INVALID_ARG, "mlp or params is NULL");
+  return mlp_get_params(mlp, h_params);
+}
+
+tc_status tc_mlp_set_params(tc_mlp* mlp, const float* h_params) {
+  if (!mlp || !h_params) return set_error(TC_ERR_INVALID_ARG, "mlp or params is NULL");
+  return mlp_set_params(mlp, h_params);
+}
+
+tc_status tc_edge_features(const tc_graph* g, const tc_motif* motif, int64_t delta, const void* d_index,
+                           uint16_t* d_feat, void* stream) {
+  TC_TRY(check_graph(g));
+  Plan plan;
+  TC_TRY(plan_of(motif, &plan));
+  if (delta < 0) return set_error(TC_ERR_INVALID_ARG, "delta must be >= 0");
+  if (!d_index || !d_feat) return set_error(TC_ERR_INVALID_ARG, "index or features is NULL");
+  cudaStream_t st = S(stream);
+  TC_TRY(check_index_header(g, plan, delta, d_index, st));
+  const EdgeRec* rec = (const EdgeRec*)((const char*)d_index + kIndexHeaderBytes);
+  return launch_features(g, rec, delta, d_feat, st);
+}
+
+tc_status tc_mlp_forward(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, uint64_t n,
+                         float* d_logits, void* stream) {
+  if (!mlp || (n && (!d_feat || !d_logits))) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
+  return launch_mlp_forward(mlp, d_feat, d_rows, n, d_logits, S(stream));
+}
+
+tc_status tc_mlp_grad(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, const float* d_labels,
+                      uint64_t n, float* d_grad, float* h_loss, void* stream) {
+  if (!mlp || !d_grad || (n && (!d_feat || !d_labels))) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = S(stream);
+  float* loss = nullptr;
+  TC_CUDA(cudaMallocAsync(&loss, sizeof(float), st));
+  tc_status s = TC_OK;
+  cudaError_t e = cudaMemsetAsync(d_grad, 0, sizeof(float) * TC_MLP_PARAMS, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+  if (e != cudaSuccess) s = cuda_status(e, "memset");
+  if (s == TC_OK) s = launch_mlp_grad(mlp, d_feat, d_rows, d_labels, n, d_grad, loss, st);
+  float hl = 0.f;
+  if (s == TC_OK) {
+    e = cudaMemcpyAsync(&hl, loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_status(e, "tc_mlp_grad");
+  }
+  cudaFreeAsync(loss, st);
+  if (s == TC_OK && h_loss) *h_loss = n ? hl / (float)n : 0.f;
+  return s;
+}
+
+tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, int64_t delta,
+                       const uint64_t* d_prefix, const void* d_index, const uint16_t* d_feat,
+                       uint64_t n_samples, uint64_t seed, uint32_t batch, float lr, float* h_losses,
+                       void* stream) {
+  TC_TRY(check_graph(g));
+  Plan plan;
+  TC_TRY(plan_of(motif, &plan));
+  if (!mlp || !d_prefix || !d_index || !d_feat) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
+  if (batch == 0 || !(lr > 0.f)) return set_error(TC_ERR_INVALID_ARG, "batch must be > 0 and lr > 0");
+  if (n_samples == 0) return TC_OK;
+  cudaStream_t st = S(stream);
+  const uint64_t steps = (n_samples + batch - 1) / batch;
+  uint64_t* trace = nullptr;
+  uint32_t* rows = nullptr;
+  float* labels = nullptr;
+  float* losses = nullptr;
+  SampleSums* sums = nullptr;
+  tc_status s = TC_OK;
+  cudaError_t e = cudaMallocAsync(&trace, 32 * n_samples, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&rows, 4 * n_samples, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&labels, 4 * n_samples, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&losses, sizeof(float) * steps, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&sums, sizeof(SampleSums), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(SampleSums), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(losses, 0, sizeof(float) * steps, st);
+  if (e != cudaSuccess) s = cuda_status(e, "tc_mlp_train allocation");
+  // training paths from the plain sampler: rows = middle edges, labels = [X > 0]
+  if (s == TC_OK) s = launch_sampler(g, plan, delta, d_prefix, d_index, n_samples, seed, 0, trace, sums, st);
+  if (s == TC_OK) s = launch_trace_to_rows(trace, n_samples, rows, labels, st);
+  for (uint64_t b = 0; b < steps && s == TC_OK; b++) {
+    const uint64_t lo = b * batch, nb = (n_samples - lo) < batch ? (n_samples - lo) : batch;
+    s = launch_mlp_grad(mlp, d_feat, rows + lo, labels + lo, nb, mlp_grad_buffer(mlp), losses + b, st);
+    if (s == TC_OK) s = mlp_adam(mlp, lr, st);
+  }
+  SampleSums hs;
+  float first = 0.f, last = 0.f;
+  if (s == TC_OK) {
+    e = cudaMemcpyAsync(&hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&first, losses, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last, losses + steps - 1, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_status(e, "tc_mlp_train");
+  }
+  for (void* p : {(void*)trace, (void*)rows, (void*)labels, (void*)losses, (void*)sums})
+    if (p) cudaFreeAsync(p, st);
+  if (s == TC_OK && hs.err) s = device_status(hs.err, "tc_mlp_train");
+  if (s == TC_OK && h_losses) {
+    const uint64_t last_n = n_samples - (steps - 1) * (uint64_t)batch;
+    h_losses[0] = first / (float)(batch < n_samples ? batch : n_samples);
+    h_losses[1] = last / (float)last_n;
+  }
+  return s;
+}
+
+tc_status tc_proposal_index_bytes(const tc_graph* g, size_t* h_bytes) {
+  TC_TRY(check_graph(g));
+  if (!h_bytes) return set_error(TC_ERR_INVALID_ARG, "bytes is NULL");
+  *h_bytes = proposal_index_bytes((uint64_t)g->m);
+  return TC_OK;
+}
+
+tc_status tc_proposal_weights(const tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, int64_t delta,
+                              const uint64_t* d_prefix, const uint16_t* d_feat, float eps, uint32_t scale,
+                              uint16_t* d_h, uint64_t* d_qprefix, void* d_qindex, uint64_t* h_Q,
+                              void* stream) {
+  TC_TRY(check_graph(g));
+  Plan plan;
+  TC_TRY(plan_of(motif, &plan));
+  if (!mlp || !d_prefix || !d_feat || !d_h || !d_qprefix || !d_qindex)
+    return set_error(TC_ERR_INVALID_ARG, "NULL argument");
+  if (((uintptr_t)d_qindex & 255) != 0) return set_error(TC_ERR_INVALID_ARG, "index must be 256-byte aligned");
+  if (scale < 1 || !(eps >= 0.f) || (double)scale * (1.0 + eps) + 1.0 > TC_PROPOSAL_MAX_H)
+    return set_error(TC_ERR_INVALID_ARG, "need scale >= 1, eps >= 0 and scale (1 + eps) + 1 <= 4095");
+  cudaStream_t st = S(stream);
+  const uint64_t m = (uint64_t)g->m;
+  uint64_t* q = nullptr;
+  uint32_t* err = nullptr;
+  tc_status s = TC_OK;
+  cudaError_t e = cudaMallocAsync(&q, 8 * (m ? m : 1), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&err, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) s = cuda_status(e, "tc_proposal_weights allocation");
+  if (s == TC_OK) s = launch_proposal(mlp, d_feat, d_prefix, m, eps, (float)scale, d_h, q, st);
+  if (s == TC_OK) s = scan_u64(q, d_qprefix, m, err, st);
+  if (s == TC_OK)
+    s = launch_guide_at(g, plan, delta, d_qprefix, (IndexHeader*)d_qindex,
+                        (uint32_t*)((char*)d_qindex + kIndexHeaderBytes), err, st);
+  uint32_t h_err = 0;
+  if (s == TC_OK && h_Q) {
+    e = cudaMemcpyAsync(h_Q, d_qprefix + m, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_status(e, "tc_proposal_weights");
+  }
+  if (q) cudaFreeAsync(q, st);
+  if (err) cudaFreeAsync(err, st);
+  if (s == TC_OK && h_err) s = device_status(h_err, "tc_proposal_weights");
+  return s;
+}
+
+tc_status tc_sample_estimate_q(const tc_graph* g, const tc_motif* motif, int64_t delta, const void* d_index,
+                               const uint16_t* d_h, const uint64_t* d_qprefix, const void* d_qindex,
+                               uint64_t k, uint64_t seed, uint64_t sample_offset, tc_estimate* h_out,
+                               uint64_t* h_bins, uint64_t* d_trace, void* stream) {
+  TC_TRY(check_graph(g));
+  Plan plan;
+  TC_TRY(plan_of(motif, &plan));
+  if (!d_index || !d_h || !d_qprefix || !d_qindex || !h_out) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
+  if ((((uintptr_t)d_index) | ((uintptr_t)d_qindex)) & 255)
+    return set_error(TC_ERR_INVALID_ARG, "indexes must be 256-byte aligned");
+  cudaStream_t st = S(stream);
+  const size_t nbins = 3 * (size_t)(TC_PROPOSAL_MAX_H + 1);
+  unsigned long long* bins = nullptr;
+  SampleSums* sums = nullptr;
+  tc_status s = TC_OK;
+  cudaError_t e = cudaMallocAsync(&bins, 8 * nbins, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&sums, sizeof(SampleSums), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bins, 0, 8 * nbins, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(SampleSums), st);
+  if (e != cudaSuccess) s = cuda_status(e, "tc_sample_estimate_q allocation");
+  if (s == TC_OK)
+    s = launch_sampler(g, plan, delta, d_qprefix, d_index, k, seed, sample_offset, d_trace, sums, st, d_qindex, d_h,
+                       bins);
+  std::vector<uint64_t> hb(nbins);
+  SampleSums hs;
+  std::memset(&hs, 0, sizeof(hs));
+  if (s == TC_OK) {
+    e = cudaMemcpyAsync(hb.data(), bins, 8 * nbins, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_status(e, "tc_sample_estimate_q");
+  }
+  if (bins) cudaFreeAsync(bins, st);
+  if (sums) cudaFreeAsync(sums, st);
+  if (s == TC_OK && hs.err) s = device_status(hs.err, "tc_sample_estimate_q");
+  if (s != TC_OK) return s;
+  const uint64_t Q = hs.W;
+  h_out->W = Q;
+  h_out->k = k;
+  h_out->sum_x = hs.sum_x;
+  h_out->sum_x2_lo = hs.sum_x2_lo;
+  h_out->sum_x2_hi = hs.sum_x2_hi;
+  h_out->hits = hs.hits;
+  h_out->checked = hs.checked;
+  // C_hat = Q / k * sum over ascending h of B_h / h; SE from sum Y and sum Y^2
+  double s1 = 0.0, s2 = 0.0;
+  for (int hv = 1; hv <= TC_PROPOSAL_MAX_H; hv++) {
+    const uint64_t b = hb[3 * hv];
+    const unsigned __int128 b2 = ((unsigned __int128)hb[3 * hv + 2] << 64) | hb[3 * hv + 1];
+    if (!b && !b2) continue;
+    const double h = (double)hv;
+    s1 += (double)b / h;
+    s2 += (double)b2 / (h * h);
+  }
+  h_out->estimate = 0.0;
+  h_out->std_err = 0.0;
+  if (k && Q) {
+    const double Qf = (double)Q, kf = (double)k;
+    h_out->estimate = Qf / kf * s1;
+    if (k >= 2) {
+      const double sy = Qf * s1, sy2 = Qf * Qf * s2;
+      double var = (sy2 - sy * sy / kf) / (kf - 1.0);
+      if (var < 0.0) var = 0.0;
+      h_out->std_err = std::sqrt(var / kf);
+    } else {
+      h_out->std_err = NAN;
+    }
+  }
+  if (h_bins) std::memcpy(h_bins, hb.data(), 8 * nbins);
+  return TC_OK;
 }
 
 }  // extern "C"

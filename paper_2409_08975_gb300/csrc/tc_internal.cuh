@@ -275,8 +275,28 @@ tc_status launch_weights(const tc_graph* g, const Plan& plan, int64_t delta, Edg
                          cudaStream_t st);
 tc_status launch_guide(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
                        void* index, uint32_t* d_err, cudaStream_t st);
+tc_status launch_guide_at(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
+                          IndexHeader* hdr, uint32_t* guide, uint32_t* d_err, cudaStream_t st);
+size_t proposal_index_bytes(uint64_t m);  // header + guide of a proposal's CDF
 
 size_t index_bytes(uint64_t m);
+
+// learned proposal (tc_learn.cu)
+tc_status mlp_create(uint64_t seed, tc_mlp** out);
+void mlp_destroy(tc_mlp* M);
+int mlp_num_params();
+tc_status mlp_set_params(tc_mlp* M, const float* h);
+tc_status mlp_get_params(const tc_mlp* M, float* h);
+tc_status launch_features(const tc_graph* g, const EdgeRec* rec, int64_t delta, uint16_t* feat, cudaStream_t st);
+tc_status launch_mlp_forward(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, uint64_t n, float* out,
+                             cudaStream_t st);
+tc_status launch_mlp_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, const float* labels,
+                          uint64_t n, float* grad, float* loss_sum, cudaStream_t st);
+tc_status mlp_adam(tc_mlp* M, float lr, cudaStream_t st);
+float* mlp_grad_buffer(tc_mlp* M);
+tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st);
+tc_status launch_proposal(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
+                          float scale, uint16_t* h, uint64_t* q, cudaStream_t st);
 int guide_bits(uint64_t m);
 
 struct SampleSums {  // per-call device accumulator
@@ -287,6 +307,7 @@ struct SampleSums {  // per-call device accumulator
 
 tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
                          const void* index, uint64_t k, uint64_t seed, uint64_t offset, uint64_t* trace,
-                         SampleSums* d_sums, cudaStream_t st);
+                         SampleSums* d_sums, cudaStream_t st, const void* qindex = nullptr,
+                         const uint16_t* h = nullptr, unsigned long long* bins = nullptr);
 
 }  // namespace tc

@@ -1,0 +1,601 @@
+// Learned proposal: edge features, a 12 -> 64 -> 64 -> 1 network (bf16
+// operands on the tensor cores through mma.sync m16n8k16, FP32 accumulation,
+// FP32 backward and Adam on FP32 master weights) and the proposal
+// h_e = max(1, floor(S (eps + g_e) + 1/2)), q_e = w_e h_e.  Sampling middle
+// edges proportional to q and weighting each path by Q / h_e keeps the
+// estimator of Alg. 5 unbiased (Claim 2 applies path by path).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+
+constexpr int kH = 64;      // hidden width
+constexpr int kF = 16;      // feature row stride (12 used)
+constexpr int kNFeat = 12;
+constexpr int kNParams = kH * kF + kH + kH * kH + kH + kH + 1;  // 5313
+// flat parameter layout: W1[64][16], b1[64], W2[64][64], b2[64], W3[64], b3
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * kF, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH,
+              kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH;
+
+}  // namespace tc
+
+struct tc_mlp {
+  float* params;  // FP32 master weights (flat layout above)
+  float* m1;      // Adam first moments
+  float* m2;      // Adam second moments
+  float* grad;    // gradient accumulator
+  uint64_t steps;
+  int device;
+};
+
+namespace tc {
+
+// ---------------------------------------------------------------------------
+// Features: counts of the 12 quantities below for canonical edge e = (u, v, t)
+// (d1, d3 and w from the sampling index records), log1p in FP32, rounded to
+// bf16 (nearest even); columns 12..15 are zero.
+//   0 d1, 1 d3, 2 w, 3..6 in/out-degree of u then of v over [t-delta, t+delta],
+//   7 sigma_{u,v}[t-delta, t+delta], 8 sigma_{v,u}[t-delta, t+delta] (Def. 3),
+//   9 out-degree of u, 10 in-degree of v, 11 in-degree of u.
+
+__device__ __forceinline__ uint32_t count_window(const OutEdge* __restrict__ out_e, const uint32_t* __restrict__ out_off,
+                                                 const InEdge* __restrict__ in_e, const uint32_t* __restrict__ in_off,
+                                                 bool in_list, int32_t x, int64_t lo, int64_t hi) {
+  if (in_list) {
+    const uint32_t a = __ldg(in_off + x), b = __ldg(in_off + x + 1);
+    auto tt = [&](uint32_t p) { return in_e[p].t; };
+    const uint32_t s = search_time<true>(a, b, lo, tt);
+    return search_time<false>(s, b, hi, tt) - s;
+  }
+  const uint32_t a = __ldg(out_off + x), b = __ldg(out_off + x + 1);
+  auto tt = [&](uint32_t p) { return out_e[p].t; };
+  const uint32_t s = search_time<true>(a, b, lo, tt);
+  return search_time<false>(s, b, hi, tt) - s;
+}
+
+__device__ __forceinline__ uint32_t pair_count(const PairSlot* __restrict__ table, uint64_t mask,
+                                               const int64_t* __restrict__ pair_t, int32_t x, int32_t y, int64_t lo,
+                                               int64_t hi) {
+  const uint64_t key = pair_key((uint32_t)x, (uint32_t)y);
+  uint64_t h = mix64(key) & mask;
+  for (uint64_t probe = 0; probe <= mask; probe++) {
+    const uint4 slot = __ldg(reinterpret_cast<const uint4*>(table + h));
+    if (slot.x == (uint32_t)x && slot.y == (uint32_t)y) {
+      auto tt = [&](uint32_t p) { return __ldg(pair_t + p); };
+      const uint32_t s = search_time<true>(slot.z, slot.w, lo, tt);
+      return search_time<false>(s, slot.w, hi, tt) - s;
+    }
+    if (slot.x == 0xFFFFFFFFu) return 0;
+    h = (h + 1) & mask;
+  }
+  return 0;
+}
+
+__global__ void __launch_bounds__(256) k_features(const OutEdge* __restrict__ out_e,
+                                                  const uint32_t* __restrict__ out_off,
+                                                  const InEdge* __restrict__ in_e, const uint32_t* __restrict__ in_off,
+                                                  const PairSlot* __restrict__ table, uint64_t mask,
+                                                  const int64_t* __restrict__ pair_t, const EdgeRec* __restrict__ rec,
+                                                  uint64_t m, int64_t delta, __nv_bfloat16* __restrict__ feat) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const EdgeRec r = rec[i];
+    const int64_t lo = sat_sub(r.t, delta), hi = sat_add(r.t, delta);
+    float c[kNFeat];
+    c[0] = (float)r.d1;
+    c[1] = (float)r.d3;
+    c[2] = (float)((uint64_t)r.d1 * (uint64_t)r.d3);
+    c[3] = (float)count_window(out_e, out_off, in_e, in_off, true, r.u, lo, hi);
+    c[4] = (float)count_window(out_e, out_off, in_e, in_off, false, r.u, lo, hi);
+    c[5] = (float)count_window(out_e, out_off, in_e, in_off, true, r.v, lo, hi);
+    c[6] = (float)count_window(out_e, out_off, in_e, in_off, false, r.v, lo, hi);
+    c[7] = (float)pair_count(table, mask, pair_t, r.u, r.v, lo, hi);
+    c[8] = (float)pair_count(table, mask, pair_t, r.v, r.u, lo, hi);
+    c[9] = (float)(__ldg(out_off + r.u + 1) - __ldg(out_off + r.u));
+    c[10] = (float)(__ldg(in_off + r.v + 1) - __ldg(in_off + r.v));
+    c[11] = (float)(__ldg(in_off + r.u + 1) - __ldg(in_off + r.u));
+    __align__(16) __nv_bfloat16 row[kF];
+#pragma unroll
+    for (int j = 0; j < kNFeat; j++) row[j] = __float2bfloat16_rn(log1pf(c[j]));
+#pragma unroll
+    for (int j = kNFeat; j < kF; j++) row[j] = __float2bfloat16_rn(0.0f);
+    uint4* dst = reinterpret_cast<uint4*>(feat + i * kF);
+    dst[0] = reinterpret_cast<const uint4*>(row)[0];
+    dst[1] = reinterpret_cast<const uint4*>(row)[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Network on the tensor cores.  One warp computes a tile of 16 rows.
+// Fragment layout of mma.m16n8k16 (g = lane / 4, q = lane % 4):
+//   A (16x16, row-major): regs (g, 2q..2q+1), (g+8, 2q..), (g, 2q+8..), (g+8, 2q+8..)
+//   B (16x8):             regs (k = 2q..2q+1, n = g), (k = 2q+8..2q+9, n = g)
+//   C (16x8):             (g, 2q), (g, 2q+1), (g+8, 2q), (g+8, 2q+1)
+
+struct MlpShared {
+  __nv_bfloat16 W1[kH * kF];   // [n][k]
+  __nv_bfloat16 W2[kH * kH];   // [n][k]
+  __nv_bfloat16 W2T[kH * kH];  // [k][n]
+  float W3[kH];                // bf16 values held as FP32
+  float b1[kH], b2[kH];
+  float b3;
+};
+
+__device__ __forceinline__ void load_mlp_shared(MlpShared& S, const float* __restrict__ p) {
+  for (int i = threadIdx.x; i < kH * kF; i += blockDim.x) S.W1[i] = __float2bfloat16_rn(p[kOffW1 + i]);
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+    const __nv_bfloat16 v = __float2bfloat16_rn(p[kOffW2 + i]);
+    S.W2[i] = v;
+    S.W2T[(i % kH) * kH + i / kH] = v;
+  }
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    S.W3[i] = __bfloat162float(__float2bfloat16_rn(p[kOffW3 + i]));
+    S.b1[i] = p[kOffB1 + i];
+    S.b2[i] = p[kOffB2 + i];
+  }
+  if (threadIdx.x == 0) S.b3 = p[kOffB3];
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// A fragment of 16 feature rows; row index r < 0 means a zero row.
+__device__ __forceinline__ void load_rows(const __nv_bfloat16* __restrict__ feat, int64_t ra, int64_t rb,
+                                          uint32_t (&a)[4]) {
+  const int q = threadIdx.x & 3;
+  const uint32_t* fa = ra >= 0 ? reinterpret_cast<const uint32_t*>(feat + ra * kF) : nullptr;
+  const uint32_t* fb = rb >= 0 ? reinterpret_cast<const uint32_t*>(feat + rb * kF) : nullptr;
+  a[0] = fa ? __ldg(fa + q) : 0u;
+  a[1] = fb ? __ldg(fb + q) : 0u;
+  a[2] = fa ? __ldg(fa + 4 + q) : 0u;
+  a[3] = fb ? __ldg(fb + 4 + q) : 0u;
+}
+
+// Forward of one tile: z1, z2 (pre-activations, FP32) and a2 (bf16 values as
+// FP32) in C-fragment layout, and z3 for rows g and g + 8.
+struct TileAct {
+  float z1[8][4];
+  float z2[8][4];
+  float z3g, z3g8;
+};
+
+__device__ __forceinline__ void tile_forward(const MlpShared& S, const uint32_t (&x)[4], TileAct& T) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  // layer 1: [16 x 16] x [16 x 64]
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int n = j * 8 + g;
+    float c[4] = {S.b1[j * 8 + 2 * q], S.b1[j * 8 + 2 * q + 1], S.b1[j * 8 + 2 * q], S.b1[j * 8 + 2 * q + 1]};
+    mma_bf16(c, x, ld_pair(&S.W1[n * kF + 2 * q]), ld_pair(&S.W1[n * kF + 2 * q + 8]));
+#pragma unroll
+    for (int r = 0; r < 4; r++) T.z1[j][r] = c[r];
+  }
+  // ReLU, bf16, as the A fragments of layer 2
+  uint32_t a1[4][4];
+#pragma unroll
+  for (int kk = 0; kk < 4; kk++) {
+    a1[kk][0] = pack_bf16(fmaxf(T.z1[2 * kk][0], 0.f), fmaxf(T.z1[2 * kk][1], 0.f));
+    a1[kk][1] = pack_bf16(fmaxf(T.z1[2 * kk][2], 0.f), fmaxf(T.z1[2 * kk][3], 0.f));
+    a1[kk][2] = pack_bf16(fmaxf(T.z1[2 * kk + 1][0], 0.f), fmaxf(T.z1[2 * kk + 1][1], 0.f));
+    a1[kk][3] = pack_bf16(fmaxf(T.z1[2 * kk + 1][2], 0.f), fmaxf(T.z1[2 * kk + 1][3], 0.f));
+  }
+  // layer 2: [16 x 64] x [64 x 64]
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int n = j * 8 + g;
+    float c[4] = {S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1], S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1]};
+#pragma unroll
+    for (int kk = 0; kk < 4; kk++)
+      mma_bf16(c, a1[kk], ld_pair(&S.W2[n * kH + kk * 16 + 2 * q]), ld_pair(&S.W2[n * kH + kk * 16 + 2 * q + 8]));
+#pragma unroll
+    for (int r = 0; r < 4; r++) T.z2[j][r] = c[r];
+  }
+  // layer 3 in FP32 on the bf16-rounded activations, reduced over the 4 lanes of a row
+  float sg = 0.f, sg8 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int n0 = j * 8 + 2 * q;
+    sg += __bfloat162float(__float2bfloat16_rn(fmaxf(T.z2[j][0], 0.f))) * S.W3[n0] +
+          __bfloat162float(__float2bfloat16_rn(fmaxf(T.z2[j][1], 0.f))) * S.W3[n0 + 1];
+    sg8 += __bfloat162float(__float2bfloat16_rn(fmaxf(T.z2[j][2], 0.f))) * S.W3[n0] +
+           __bfloat162float(__float2bfloat16_rn(fmaxf(T.z2[j][3], 0.f))) * S.W3[n0 + 1];
+  }
+  sg += __shfl_xor_sync(0xffffffffu, sg, 1);
+  sg += __shfl_xor_sync(0xffffffffu, sg, 2);
+  sg8 += __shfl_xor_sync(0xffffffffu, sg8, 1);
+  sg8 += __shfl_xor_sync(0xffffffffu, sg8, 2);
+  T.z3g = sg + S.b3;
+  T.z3g8 = sg8 + S.b3;
+}
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// Logits of rows (rows[i] or i) -> out[i].
+__global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ params,
+                                                     const __nv_bfloat16* __restrict__ feat,
+                                                     const uint32_t* __restrict__ rows, uint64_t n,
+                                                     float* __restrict__ out) {
+  __shared__ MlpShared S;
+  load_mlp_shared(S, params);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < n; tile += warps) {
+    const uint64_t ia = tile * 16 + g, ib = ia + 8;
+    const int64_t ra = ia < n ? (int64_t)(rows ? rows[ia] : ia) : -1;
+    const int64_t rb = ib < n ? (int64_t)(rows ? rows[ib] : ib) : -1;
+    uint32_t x[4];
+    load_rows(feat, ra, rb, x);
+    TileAct T;
+    tile_forward(S, x, T);
+    if ((lane & 3) == 0) {
+      if (ia < n) out[ia] = T.z3g;
+      if (ib < n) out[ib] = T.z3g8;
+    }
+  }
+}
+
+// Proposal: h_e = max(1, floor(scale (eps + g_e) + 1/2)) and q_e = w_e h_e for
+// every canonical edge, with w_e = prefix[e + 1] - prefix[e].
+__global__ void __launch_bounds__(128) k_proposal(const float* __restrict__ params,
+                                                  const __nv_bfloat16* __restrict__ feat,
+                                                  const uint64_t* __restrict__ prefix, uint64_t m, float eps,
+                                                  float scale, uint16_t* __restrict__ h, uint64_t* __restrict__ q) {
+  __shared__ MlpShared S;
+  load_mlp_shared(S, params);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < m; tile += warps) {
+    const uint64_t ia = tile * 16 + g, ib = ia + 8;
+    uint32_t x[4];
+    load_rows(feat, ia < m ? (int64_t)ia : -1, ib < m ? (int64_t)ib : -1, x);
+    TileAct T;
+    tile_forward(S, x, T);
+    if ((lane & 3) == 0) {
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        const uint64_t i = r ? ib : ia;
+        if (i < m) {
+          const float z = r ? T.z3g8 : T.z3g;
+          const float v = floorf(scale * (eps + sigmoidf_(z)) + 0.5f);
+          const uint32_t hv = v < 1.f ? 1u : (uint32_t)v;
+          h[i] = (uint16_t)hv;
+          q[i] = (prefix[i + 1] - prefix[i]) * (uint64_t)hv;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of the mean binary cross-entropy over a batch.  Each warp runs the
+// forward of a 16-row tile on the tensor cores and back-propagates in FP32:
+//   dz3 = (sigmoid(z3) - y) / B, dz2 = dz3 W3 * [z2 > 0], dz1 = W2^T dz2 * [z1 > 0];
+// the per-row vectors go to shared memory, where the block accumulates the
+// parameter gradients (each thread owns a fixed set of parameters) before one
+// global atomic add per parameter and block.
+
+constexpr int kTrainWarps = 4;
+constexpr int kTrainRows = 16 * kTrainWarps;
+
+struct TrainShared {
+  MlpShared net;
+  float x[kTrainRows][kF];
+  float a1[kTrainRows][kH];
+  float a2[kTrainRows][kH];
+  float dz1[kTrainRows][kH];
+  float dz2[kTrainRows][kH];
+  float dz3[kTrainRows];
+  float loss[kTrainWarps];
+};
+
+__global__ void __launch_bounds__(32 * kTrainWarps) k_mlp_grad(const float* __restrict__ params,
+                                                              const __nv_bfloat16* __restrict__ feat,
+                                                              const uint32_t* __restrict__ rows,
+                                                              const float* __restrict__ labels, uint64_t n,
+                                                              float inv_batch, float* __restrict__ grad,
+                                                              float* __restrict__ loss_sum) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainShared& S = *reinterpret_cast<TrainShared*>(smem_raw);
+  load_mlp_shared(S.net, params);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
+  constexpr int kOwn = (kNParams + 32 * kTrainWarps - 1) / (32 * kTrainWarps);
+  float acc[kOwn];
+#pragma unroll
+  for (int j = 0; j < kOwn; j++) acc[j] = 0.f;
+  float loss_acc = 0.f;
+  __syncthreads();
+  for (uint64_t base = (uint64_t)blockIdx.x * kTrainRows; base < n; base += (uint64_t)gridDim.x * kTrainRows) {
+    // ---- per warp: forward and backward of 16 rows
+    const uint64_t ia = base + warp * 16 + g, ib = ia + 8;
+    const bool va = ia < n, vb = ib < n;
+    uint32_t x[4];
+    load_rows(feat, va ? (int64_t)(rows ? rows[ia] : ia) : -1, vb ? (int64_t)(rows ? rows[ib] : ib) : -1, x);
+    TileAct T;
+    tile_forward(S.net, x, T);
+    const int ra = warp * 16 + g, rb = ra + 8;
+    const float ya = va ? labels[ia] : 0.f, yb = vb ? labels[ib] : 0.f;
+    const float dza = va ? (sigmoidf_(T.z3g) - ya) * inv_batch : 0.f;
+    const float dzb = vb ? (sigmoidf_(T.z3g8) - yb) * inv_batch : 0.f;
+    if (q == 0) {
+      S.dz3[ra] = dza;
+      S.dz3[rb] = dzb;
+      // softplus(z) - y z, stable
+      auto bce = [](float z, float y) { return fmaxf(z, 0.f) - y * z + log1pf(expf(-fabsf(z))); };
+      loss_acc += (va ? bce(T.z3g, ya) : 0.f) + (vb ? bce(T.z3g8, yb) : 0.f);
+    }
+    // inputs and activations of the rows (bf16 values held as FP32)
+    {
+      const __nv_bfloat162* xa = reinterpret_cast<const __nv_bfloat162*>(x);
+      S.x[ra][2 * q] = __low2float(xa[0]);
+      S.x[ra][2 * q + 1] = __high2float(xa[0]);
+      S.x[rb][2 * q] = __low2float(xa[1]);
+      S.x[rb][2 * q + 1] = __high2float(xa[1]);
+      S.x[ra][2 * q + 8] = __low2float(xa[2]);
+      S.x[ra][2 * q + 9] = __high2float(xa[2]);
+      S.x[rb][2 * q + 8] = __low2float(xa[3]);
+      S.x[rb][2 * q + 9] = __high2float(xa[3]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int c0 = j * 8 + 2 * q;
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const int row = r < 2 ? ra : rb, col = c0 + (r & 1);
+        const float z1 = T.z1[j][r], z2 = T.z2[j][r];
+        S.a1[row][col] = __bfloat162float(__float2bfloat16_rn(fmaxf(z1, 0.f)));
+        S.a2[row][col] = __bfloat162float(__float2bfloat16_rn(fmaxf(z2, 0.f)));
+        const float dz3 = r < 2 ? dza : dzb;
+        S.dz2[row][col] = z2 > 0.f ? dz3 * S.net.W3[col] : 0.f;
+        S.dz1[row][col] = z1 > 0.f ? 1.f : 0.f;  // mask; completed below
+      }
+    }
+    __syncwarp();
+    // dz1[row][k] *= sum_n dz2[row][n] W2[n][k]: lane owns columns k = lane, lane + 32
+    for (int rr = 0; rr < 16; rr++) {
+      const int row = warp * 16 + rr;
+#pragma unroll
+      for (int h2 = 0; h2 < 2; h2++) {
+        const int k = lane + 32 * h2;
+        float s = 0.f;
+#pragma unroll 8
+        for (int nn = 0; nn < kH; nn++) s += S.dz2[row][nn] * __bfloat162float(S.net.W2T[k * kH + nn]);
+        S.dz1[row][k] *= s;
+      }
+    }
+    __syncthreads();
+    // ---- block: accumulate the owned parameters over the block's rows
+#pragma unroll
+    for (int j = 0; j < kOwn; j++) {
+      const int p = threadIdx.x + j * 32 * kTrainWarps;
+      if (p >= kNParams) break;
+      float s = 0.f;
+      if (p < kOffB1) {
+        const int nn = p / kF, k = p % kF;
+        for (int r = 0; r < kTrainRows; r++) s += S.dz1[r][nn] * S.x[r][k];
+      } else if (p < kOffW2) {
+        const int nn = p - kOffB1;
+        for (int r = 0; r < kTrainRows; r++) s += S.dz1[r][nn];
+      } else if (p < kOffB2) {
+        const int nn = (p - kOffW2) / kH, k = (p - kOffW2) % kH;
+        for (int r = 0; r < kTrainRows; r++) s += S.dz2[r][nn] * S.a1[r][k];
+      } else if (p < kOffW3) {
+        const int nn = p - kOffB2;
+        for (int r = 0; r < kTrainRows; r++) s += S.dz2[r][nn];
+      } else if (p < kOffB3) {
+        const int k = p - kOffW3;
+        for (int r = 0; r < kTrainRows; r++) s += S.dz3[r] * S.a2[r][k];
+      } else {
+        for (int r = 0; r < kTrainRows; r++) s += S.dz3[r];
+      }
+      acc[j] += s;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < kOwn; j++) {
+    const int p = threadIdx.x + j * 32 * kTrainWarps;
+    if (p < kNParams) atomicAdd(grad + p, acc[j]);
+  }
+  for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+  if (lane == 0) S.loss[warp] = loss_acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < kTrainWarps; w++) t += S.loss[w];
+    atomicAdd(loss_sum, t);
+  }
+}
+
+// Adam (Kingma & Ba, ICLR 2015) on the FP32 master weights; clears grad.
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ m1, float* __restrict__ m2,
+                       float* __restrict__ grad, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNParams) return;
+  if (i >= kOffW1 && i < kOffB1 && (i % kF) >= kNFeat) {  // padding columns stay zero
+    grad[i] = 0.f;
+    return;
+  }
+  const float gr = grad[i];
+  const float a = b1 * m1[i] + (1.f - b1) * gr;
+  const float v = b2 * m2[i] + (1.f - b2) * gr * gr;
+  m1[i] = a;
+  m2[i] = v;
+  p[i] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
+  grad[i] = 0.f;
+}
+
+// Initial weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from Philox keyed by
+// (seed, parameter index); padding columns of W1 are zero.
+__global__ void k_mlp_init(float* __restrict__ p, uint64_t seed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNParams) return;
+  int fan_in = kH;
+  if (i < kOffW2) fan_in = kNFeat;
+  if (i >= kOffW1 && i < kOffB1 && (i % kF) >= kNFeat) {
+    p[i] = 0.f;
+    return;
+  }
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 0x6d6c7000u, 0u),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const float u01 = (float)(r.x >> 8) * (1.0f / 16777216.0f);  // [0, 1)
+  p[i] = (2.f * u01 - 1.f) * rsqrtf((float)fan_in);
+}
+
+// Training rows from a trace of the plain sampler: row = middle edge,
+// label = [X > 0].
+__global__ void k_trace_to_rows(const uint64_t* __restrict__ trace, uint64_t n, uint32_t* __restrict__ rows,
+                                float* __restrict__ labels) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    rows[i] = (uint32_t)trace[4 * i];
+    labels[i] = trace[4 * i + 3] > 0 ? 1.f : 0.f;
+  }
+}
+
+static unsigned grid_cap(uint64_t items, int per_block) {
+  uint64_t b = (items + per_block - 1) / per_block;
+  const uint64_t cap = (uint64_t)num_sms() * 8;
+  if (b > cap) b = cap;
+  return (unsigned)(b ? b : 1);
+}
+
+tc_status mlp_create(uint64_t seed, tc_mlp** out) {
+  tc_mlp* M = new (std::nothrow) tc_mlp;
+  if (!M) return set_error(TC_ERR_OOM, "host allocation failed");
+  std::memset(M, 0, sizeof(*M));
+  cudaGetDevice(&M->device);
+  float* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, sizeof(float) * 4 * kNParams);
+  if (e != cudaSuccess) {
+    delete M;
+    return cuda_status(e, "cudaMalloc(mlp)");
+  }
+  M->params = buf;
+  M->m1 = buf + kNParams;
+  M->m2 = buf + 2 * kNParams;
+  M->grad = buf + 3 * kNParams;
+  e = cudaMemset(buf, 0, sizeof(float) * 4 * kNParams);
+  if (e == cudaSuccess) {
+    k_mlp_init<<<(kNParams + 255) / 256, 256>>>(M->params, seed);
+    TC_LAUNCHED(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(buf);
+    delete M;
+    return cuda_status(e, "tc_mlp_create");
+  }
+  *out = M;
+  return TC_OK;
+}
+
+void mlp_destroy(tc_mlp* M) {
+  if (M->params) cudaFree(M->params);
+  delete M;
+}
+
+int mlp_num_params() { return kNParams; }
+
+tc_status mlp_set_params(tc_mlp* M, const float* h) {
+  TC_CUDA(cudaMemcpy(M->params, h, sizeof(float) * kNParams, cudaMemcpyHostToDevice));
+  TC_CUDA(cudaMemset(M->m1, 0, sizeof(float) * 3 * kNParams));
+  M->steps = 0;
+  return TC_OK;
+}
+
+tc_status mlp_get_params(const tc_mlp* M, float* h) {
+  TC_CUDA(cudaMemcpy(h, M->params, sizeof(float) * kNParams, cudaMemcpyDeviceToHost));
+  return TC_OK;
+}
+
+tc_status launch_features(const tc_graph* g, const EdgeRec* rec, int64_t delta, uint16_t* feat, cudaStream_t st) {
+  const uint64_t m = (uint64_t)g->m;
+  if (!m) return TC_OK;
+  k_features<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->pair_hash,
+                                                          g->hash_mask, g->pair_t, rec, m, delta,
+                                                          reinterpret_cast<__nv_bfloat16*>(feat));
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+tc_status launch_mlp_forward(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, uint64_t n, float* out,
+                             cudaStream_t st) {
+  if (!n) return TC_OK;
+  k_mlp_forward<<<grid_cap((n + 15) / 16, 4), 128, 0, st>>>(M->params, reinterpret_cast<const __nv_bfloat16*>(feat),
+                                                             rows, n, out);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+// grad (device, kNParams) += gradient of the mean BCE over rows; *loss_sum
+// (device) += summed per-row loss.
+tc_status launch_mlp_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, const float* labels,
+                          uint64_t n, float* grad, float* loss_sum, cudaStream_t st) {
+  if (!n) return TC_OK;
+  static bool attr = false;
+  if (!attr) {
+    TC_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainShared)));
+    attr = true;
+  }
+  k_mlp_grad<<<grid_cap(n, kTrainRows * 4), 32 * kTrainWarps, sizeof(TrainShared), st>>>(
+      M->params, reinterpret_cast<const __nv_bfloat16*>(feat), rows, labels, n, 1.0f / (float)n, grad, loss_sum);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+tc_status mlp_adam(tc_mlp* M, float lr, cudaStream_t st) {
+  M->steps++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)M->steps), c2 = 1.f - powf(b2, (float)M->steps);
+  k_adam<<<(kNParams + 255) / 256, 256, 0, st>>>(M->params, M->m1, M->m2, M->grad, lr, b1, b2, 1e-8f, c1, c2);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+float* mlp_grad_buffer(tc_mlp* M) { return M->grad; }
+
+tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st) {
+  if (!n) return TC_OK;
+  k_trace_to_rows<<<grid_cap(n, 256), 256, 0, st>>>(trace, n, rows, labels);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+tc_status launch_proposal(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
+                          float scale, uint16_t* h, uint64_t* q, cudaStream_t st) {
+  if (!m) return TC_OK;
+  k_proposal<<<grid_cap((m + 15) / 16, 4), 128, 0, st>>>(M->params, reinterpret_cast<const __nv_bfloat16*>(feat),
+                                                          prefix, m, eps, scale, h, q);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+}  // namespace tc

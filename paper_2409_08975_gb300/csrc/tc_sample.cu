@@ -175,8 +175,20 @@ __global__ void __launch_bounds__(256) k_guide(const uint64_t* __restrict__ pref
 
 tc_status launch_guide(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix, void* index,
                        uint32_t* d_err, cudaStream_t st) {
+  IndexView v = index_view(index, (uint64_t)g->m);
+  return launch_guide_at(g, plan, delta, prefix, v.hdr, v.guide, d_err, st);
+}
+
+size_t proposal_index_bytes(uint64_t m) {
+  return kIndexHeaderBytes + sizeof(uint32_t) * ((1ull << guide_bits(m)) + 1);
+}
+
+tc_status launch_guide_at(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
+                          IndexHeader* hdr, uint32_t* guide, uint32_t* d_err, cudaStream_t st) {
   const uint64_t m = (uint64_t)g->m;
-  IndexView v = index_view(index, m);
+  IndexView v;
+  v.hdr = hdr;
+  v.guide = guide;
   const int gb = guide_bits(m);
   uint64_t blocks = (m + 255) / 256;
   const uint64_t cap = (uint64_t)num_sms() * 16;
@@ -210,6 +222,12 @@ struct SamplerArgs {
   uint64_t graph_id;
   uint64_t* trace;
   SampleSums* sums;
+  // proposal mode (h != NULL): the middle edge is drawn from the proposal's
+  // prefix and guide (hdr, prefix, guide), the records come from the plain
+  // index (rec, rec_hdr), and each hit adds X and X^2 to bins[3 h + 0..2]
+  const uint16_t* h;
+  unsigned long long* bins;
+  const IndexHeader* rec_hdr;
 };
 
 // Positions [a, b) of the pair list L_{x,y} with time in (tlo, thi) or
@@ -351,10 +369,12 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __gr
     if (threadIdx.x == 0) atomicOr(&A.sums->err, H->status);
     return;
   }
-  bool header_ok = H->magic == kIndexMagic && H->cls[0] == P.alpha1 && H->cls[1] == P.alpha3 &&
-                   H->cls[2] == P.beta1 && H->cls[3] == P.beta3 && H->closed == P.closed &&
-                   H->anchor[0] == P.e1 && H->anchor[1] == P.mid && H->anchor[2] == P.e3 &&
-                   H->delta == A.delta && H->graph_id == A.graph_id;
+  auto matches = [&](const IndexHeader* X) {
+    return X->magic == kIndexMagic && X->cls[0] == P.alpha1 && X->cls[1] == P.alpha3 && X->cls[2] == P.beta1 &&
+           X->cls[3] == P.beta3 && X->closed == P.closed && X->anchor[0] == P.e1 && X->anchor[1] == P.mid &&
+           X->anchor[2] == P.e3 && X->delta == A.delta && X->graph_id == A.graph_id;
+  };
+  bool header_ok = matches(H) && (A.rec_hdr == nullptr || matches(A.rec_hdr));
   if (!header_ok) {
     if (threadIdx.x == 0) atomicOr(&A.sums->err, kErrIndexMismatch);
     return;
@@ -404,6 +424,15 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __gr
       t3 = x.t;
     }
     const uint64_t X = check_motif(A, P, up, e.u, e.v, vp, t1, e.t, t3, &s_err, &checked);
+    if (A.h && X) {  // exact per-h bins of the proposal estimator
+      unsigned long long* bin = A.bins + 3 * (uint64_t)__ldg(A.h + lo);
+      atomicAdd(bin, (unsigned long long)X);
+      const unsigned __int128 x2 = (unsigned __int128)X * X;
+      const unsigned long long l2 = (uint64_t)x2;
+      const unsigned long long old = atomicAdd(bin + 1, l2);
+      const unsigned long long carry = (old + l2 < old) ? 1ull : 0ull;
+      if ((x2 >> 64) || carry) atomicAdd(bin + 2, (unsigned long long)(x2 >> 64) + carry);
+    }
     if (Trace) {
       A.trace[4 * i + 0] = lo;
       A.trace[4 * i + 1] = p1;
@@ -651,9 +680,16 @@ constexpr uint64_t kChunkSamples = 1ull << 28;
 
 tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
                          const void* index, uint64_t k, uint64_t seed, uint64_t offset, uint64_t* trace,
-                         SampleSums* d_sums, cudaStream_t st) {
+                         SampleSums* d_sums, cudaStream_t st, const void* qindex, const uint16_t* h,
+                         unsigned long long* bins) {
   const uint64_t m = (uint64_t)g->m;
   IndexView v = index_view(const_cast<void*>(index), m);
+  const IndexHeader* rec_hdr = nullptr;
+  if (h) {  // the proposal's header and guide replace the plain ones
+    rec_hdr = v.hdr;
+    v.hdr = (IndexHeader*)qindex;
+    v.guide = (uint32_t*)((char*)const_cast<void*>(qindex) + kIndexHeaderBytes);
+  }
   SamplerArgs A;
   A.out_e = g->out_e;
   A.in_e = g->in_e;
@@ -675,6 +711,9 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   A.graph_id = g->id;
   A.trace = trace;
   A.sums = d_sums;
+  A.h = h;
+  A.bins = bins;
+  A.rec_hdr = rec_hdr;
   static int blocks_per_sm[2] = {0, 0};
   const int ti = trace ? 1 : 0;
   if (!blocks_per_sm[ti]) {

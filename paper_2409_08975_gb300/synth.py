@@ -92,17 +92,19 @@ def _solve_i0(n, pairs, gamma, max_deg):
 
 
 def chung_lu(n, m, gamma=2.1, max_deg=1e5, multi_frac=0.30, span=100_000_000, pareto_alpha=1.5, seed=1002,
-             mean_burst_edges=200, burst_degree=4, daily=False):
+             mean_burst_edges=200, burst_degree=(1.5, 24.0), daily=False):
     """Directed power-law multigraph whose edges arrive in bursts.
 
     Bursts start at uniform times over the span (a Poisson process
     conditioned on its count); a burst of B ~ Geometric(mean_burst_edges)
-    edges draws max(4, B / burst_degree) vertex slots with Chung-Lu weights
+    edges draws max(4, B / d) vertex slots with Chung-Lu weights
     w_i ~ (i + i0)^(-1/(gamma-1)) (i0 set so the top vertex's expected
     out-degree is max_deg) and joins uniform slot pairs (no self-loops); its
-    edges follow one another after Pareto(alpha, x_m = 1 s) gaps.  A vertex's
-    degree is then proportional to its weight, and edges close in time share
-    vertices, as in transaction and communication networks.  A share
+    edges follow one another after Pareto(alpha, x_m = 1 s) gaps.  The edges
+    per vertex slot d of a burst is burst_degree, or log-uniform in
+    burst_degree = (lo, hi) per burst, so that dense and sparse bursts mix.
+    A vertex's degree is then proportional to its weight, and edges close in
+    time share vertices, as in transaction and communication networks.  A share
     multi_frac of all edges repeat an earlier edge's pair a Pareto gap later.
     ``daily`` modulates burst starts by 1 + 0.5 sin(2 pi t / 86400)."""
     rng = np.random.default_rng(seed)
@@ -112,9 +114,14 @@ def chung_lu(n, m, gamma=2.1, max_deg=1e5, multi_frac=0.30, span=100_000_000, pa
     S = int(np.searchsorted(cs, base_m)) + 1
     sizes = sizes[:S].copy()
     sizes[-1] -= cs[S - 1] - base_m
-    nv = np.maximum(4, np.round(sizes / burst_degree)).astype(np.int64)
+    if np.isscalar(burst_degree):
+        deg = np.full(S, float(burst_degree))
+    else:
+        lo, hi = burst_degree
+        deg = np.exp(rng.uniform(np.log(lo), np.log(hi), S))
+    nv = np.maximum(4, np.round(sizes / deg)).astype(np.int64)
     slots_total = int(nv.sum())
-    i0 = _solve_i0(n, slots_total * burst_degree, gamma, max_deg)
+    i0 = _solve_i0(n, base_m, gamma, max_deg)
     w = _power_weights(n, gamma, i0)
     cdf = np.cumsum(w / w.sum())
     cdf[-1] = 1.0

@@ -64,13 +64,27 @@ def lib():
             "tc_graph_copy": [vp, i32, vp, vp],
             "tc_sample_index_bytes": [vp, ctypes.POINTER(sz)],
             "tc_path_weights": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, ctypes.POINTER(u64), vp],
-            "tc_sample_estimate": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, u64, u64, u64,
+            "tc_sample_estimate": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, u64, u64, u64,
                                    ctypes.POINTER(tc_estimate), vp],
             "tc_sample_trace": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, u64, u64, u64, vp, vp],
             "tc_estimate_from_host": [i64, i64, vp, vp, vp, ctypes.POINTER(tc_motif), i64, u64, u64,
                                       ctypes.POINTER(tc_estimate), vp],
             "tc_motif_plan": [ctypes.POINTER(tc_motif), vp, vp],
             "tc_prefix_sum_noalloc": [vp, u64, vp, ctypes.POINTER(u64), vp],
+            "tc_mlp_create": [u64, ctypes.POINTER(vp)],
+            "tc_mlp_destroy": [vp],
+            "tc_mlp_get_params": [vp, vp],
+            "tc_mlp_set_params": [vp, vp],
+            "tc_edge_features": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp],
+            "tc_mlp_forward": [vp, vp, vp, u64, vp, vp],
+            "tc_mlp_grad": [vp, vp, vp, vp, u64, vp, ctypes.POINTER(ctypes.c_float), vp],
+            "tc_mlp_train": [vp, vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, u64, u64, ctypes.c_uint32,
+                             ctypes.c_float, vp, vp],
+            "tc_proposal_index_bytes": [vp, ctypes.POINTER(sz)],
+            "tc_proposal_weights": [vp, vp, ctypes.POINTER(tc_motif), i64, vp, vp, ctypes.c_float, ctypes.c_uint32,
+                                    vp, vp, vp, ctypes.POINTER(u64), vp],
+            "tc_sample_estimate_q": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, vp, u64, u64, u64,
+                                     ctypes.POINTER(tc_estimate), vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -222,7 +236,7 @@ def _est_dict(e):
 def tc_sample_estimate(g, motif, delta, weights, k, seed=0, offset=0, stream=None):
     e = tc_estimate()
     _check(lib().tc_sample_estimate(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix),
-                                    _ptr(weights.index), None, int(k), int(seed), int(offset), ctypes.byref(e),
+                                    _ptr(weights.index), int(k), int(seed), int(offset), ctypes.byref(e),
                                     _stream(stream)), "tc_sample_estimate")
     return _est_dict(e)
 
@@ -278,3 +292,119 @@ def estimate_from_sums(sum_x, sum_x2, k, W):
     sx, sx2, kf = float(sum_x), float(sum_x2), float(k)
     s2 = max((sx2 - sx * sx / kf) / (kf - 1.0), 0.0)
     return est, float(W) * math.sqrt(s2 / kf)
+
+
+# ---------------------------------------------------------------------------
+# Learned proposal
+
+MLP_PARAMS = 5313
+FEATURE_STRIDE = 16
+PROPOSAL_MAX_H = 4095
+
+
+class MLP:
+    """Owner of a device-resident tc_mlp (12 -> 64 -> 64 -> 1 network)."""
+
+    def __init__(self, seed=0):
+        h = ctypes.c_void_p()
+        _check(lib().tc_mlp_create(int(seed), ctypes.byref(h)), "tc_mlp_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("mlp destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h is not None:
+            lib().tc_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.empty(MLP_PARAMS, np.float32)
+        _check(lib().tc_mlp_get_params(self.handle, out.ctypes.data_as(ctypes.c_void_p)), "tc_mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        arr = np.ascontiguousarray(params, dtype=np.float32)
+        assert arr.size == MLP_PARAMS
+        _check(lib().tc_mlp_set_params(self.handle, arr.ctypes.data_as(ctypes.c_void_p)), "tc_mlp_set_params")
+
+
+def tc_edge_features(g, motif, delta, weights, stream=None):
+    """bf16 feature rows [m, 16] (returned as a torch.bfloat16 CUDA tensor)."""
+    feat = torch.zeros((max(g.m, 1), FEATURE_STRIDE), dtype=torch.int16, device="cuda")
+    _check(lib().tc_edge_features(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.index), _ptr(feat),
+                                  _stream(stream)), "tc_edge_features")
+    return feat[:g.m].view(torch.bfloat16)
+
+
+def tc_mlp_forward(mlp, feat, rows=None, n=None, stream=None):
+    n = int(n if n is not None else (rows.numel() if rows is not None else feat.shape[0]))
+    out = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+    _check(lib().tc_mlp_forward(mlp.handle, _ptr(feat), _ptr(rows), n, _ptr(out), _stream(stream)),
+           "tc_mlp_forward")
+    return out[:n]
+
+
+def tc_mlp_grad(mlp, feat, rows, labels, stream=None):
+    n = int(labels.numel())
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = ctypes.c_float(0.0)
+    _check(lib().tc_mlp_grad(mlp.handle, _ptr(feat), _ptr(rows), _ptr(labels), n, _ptr(grad), ctypes.byref(loss),
+                             _stream(stream)), "tc_mlp_grad")
+    return grad, loss.value
+
+
+def tc_mlp_train(mlp, g, motif, delta, weights, feat, n_samples, seed=0, batch=16384, lr=2e-3, stream=None):
+    """Returns the mean loss of the first and the last batch."""
+    losses = np.zeros(2, np.float32)
+    _check(lib().tc_mlp_train(mlp.handle, g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix),
+                              _ptr(weights.index), _ptr(feat), int(n_samples), int(seed), int(batch), float(lr),
+                              losses.ctypes.data_as(ctypes.c_void_p), _stream(stream)), "tc_mlp_train")
+    return float(losses[0]), float(losses[1])
+
+
+class Proposal:
+    def __init__(self, h, qprefix, qindex, Q):
+        self.h, self.qprefix, self.qindex, self.Q = h, qprefix, qindex, Q
+
+
+def tc_proposal_weights(mlp, g, motif, delta, weights, feat, eps=0.05, scale=1024, stream=None):
+    m = g.m
+    b = ctypes.c_size_t()
+    _check(lib().tc_proposal_index_bytes(g.handle, ctypes.byref(b)), "tc_proposal_index_bytes")
+    h = torch.empty(max(m, 1), dtype=torch.int16, device="cuda")
+    qprefix = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    qindex = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+    Q = ctypes.c_uint64(0)
+    _check(lib().tc_proposal_weights(mlp.handle, g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix),
+                                     _ptr(feat), float(eps), int(scale), _ptr(h), _ptr(qprefix), _ptr(qindex),
+                                     ctypes.byref(Q), _stream(stream)), "tc_proposal_weights")
+    return Proposal(h[:m], qprefix, qindex, Q.value)
+
+
+def tc_sample_estimate_q(g, motif, delta, weights, proposal, k, seed=0, offset=0, want_bins=False, trace=False,
+                         stream=None):
+    e = tc_estimate()
+    bins = np.zeros(3 * (PROPOSAL_MAX_H + 1), np.uint64) if want_bins else None
+    tr = torch.empty((max(k, 1), 4), dtype=torch.int64, device="cuda") if trace else None
+    _check(lib().tc_sample_estimate_q(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.index),
+                                      _ptr(proposal.h), _ptr(proposal.qprefix), _ptr(proposal.qindex), int(k),
+                                      int(seed), int(offset), ctypes.byref(e),
+                                      bins.ctypes.data_as(ctypes.c_void_p) if want_bins else None, _ptr(tr),
+                                      _stream(stream)), "tc_sample_estimate_q")
+    out = _est_dict(e)
+    if want_bins:
+        b = bins.reshape(-1, 3)
+        out["bins"] = b
+    if trace:
+        out["trace"] = tr[:k]
+    return out

@@ -72,5 +72,4 @@ def test_null_arguments_rejected(libtc):
     m = tc.make_motif([(0, 1), (1, 2), (2, 3), (3, 0)])
     assert libtc.tc_path_weights(None, ctypes.byref(m), 5, None, None, None, None, None) == 1
     est = tc.tc_estimate()
-    assert libtc.tc_sample_estimate(None, ctypes.byref(m), 5, None, None, None, 1, 0, 0, ctypes.byref(est),
-                                    None) == 1
+    assert libtc.tc_sample_estimate(None, ctypes.byref(m), 5, None, None, 1, 0, 0, ctypes.byref(est), None) == 1
