@@ -275,13 +275,13 @@ def main():
     del src_d, dst_d, t_d
 
     wts = tc.alloc_weights(g)
-    offset0 = rank * k * 1000
 
     def step(i, sample_events=None):
+        # step i of rank r draws sample ids [(i * world + r) * k, + k)
         tc.tc_path_weights(g, mot, delta, out=wts, want_W=False)
         if sample_events is not None:
             sample_events[0].record(stream)
-        r = tc.tc_sample_estimate(g, mot, delta, wts, k, seed=0, offset=offset0 + i * k)
+        r = tc.tc_sample_estimate(g, mot, delta, wts, k, seed=0, offset=(i * world + rank) * k)
         if sample_events is not None:
             sample_events[1].record(stream)
         return r
@@ -326,6 +326,10 @@ def main():
     weights_ms = statistics.median(a.elapsed_time(b) for a, b in wev)
 
     r0 = results[-1]
+    merged = None
+    if world > 1:  # the one exchange: exact integer sums of the last step over ranks
+        from paper_2409_08975_gb300 import dist as tcdist
+        merged = tcdist.merge_runs(r0, r0["W"], device="cuda")
     checked_frac = r0["checked"] / max(r0["k"], 1)
     # sampler bytes per sample: guide entry, prefix entry, edge record, e1 and
     # e3 records (5 sectors); a checked path adds the pair list lookup
@@ -361,7 +365,7 @@ def main():
         e2e = {"value": world * k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * m, "d2h_bytes_per_step": 92,
                "ms_per_step": e2e_s * 1e3}
 
-    learned = None if args.no_learned else learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
+    learned = None if (args.no_learned or rank != 0) else learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
                                                               args.train_samples, stream)
 
     base = None
@@ -379,6 +383,7 @@ def main():
             "cpu_baseline": base, "csr_build_ms": csr_ms, "weights": weights, "learned": learned,
             "estimate": {"W": r0["W"], "estimate": r0["estimate"], "std_err": r0["std_err"], "hits": r0["hits"],
                          "checked": r0["checked"]},
+            "merged_over_ranks": merged,
         }))
     g.destroy()
     if world > 1:
