@@ -326,6 +326,14 @@ def main():
     weights_ms = statistics.median(a.elapsed_time(b) for a, b in wev)
 
     r0 = results[-1]
+    # exact count by the exhaustive path sum (all W paths), for the relative error
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev[0].record(stream)
+    ex = tc.tc_exact_count(g, mot, delta, wts)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    exact = {"C": ex["sum_x"], "paths": ex["k"], "ms": ev[0].elapsed_time(ev[1]),
+             "rel_error_plain": abs(r0["estimate"] - ex["sum_x"]) / max(ex["sum_x"], 1)}
     merged = None
     if world > 1:  # the one exchange: exact integer sums of the last step over ranks
         from paper_2409_08975_gb300 import dist as tcdist
@@ -367,6 +375,8 @@ def main():
 
     learned = None if (args.no_learned or rank != 0) else learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
                                                               args.train_samples, stream)
+    if learned:
+        learned["rel_error"] = abs(learned["estimate"] - exact["C"]) / max(exact["C"], 1)
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -383,7 +393,7 @@ def main():
             "cpu_baseline": base, "csr_build_ms": csr_ms, "weights": weights, "learned": learned,
             "estimate": {"W": r0["W"], "estimate": r0["estimate"], "std_err": r0["std_err"], "hits": r0["hits"],
                          "checked": r0["checked"]},
-            "merged_over_ranks": merged,
+            "merged_over_ranks": merged, "exact": exact,
         }))
     g.destroy()
     if world > 1:

@@ -240,6 +240,20 @@ tc_status tc_prefix_sum_noalloc(const uint64_t* d_w, uint64_t m, uint64_t* d_pre
  * '<' and +1 for '+' / '>'.  Host only. */
 tc_status tc_motif_plan(const tc_motif* motif, int32_t* h_anchor, int32_t* h_class);
 
+/*
+ * Exact count by exhaustive path sum (the proof of Claim 2: every M-match
+ * has exactly one anchor path, so the sum over all W delta-centered paths of
+ * the anchor's class of CheckMotif equals C).  Path p in [0, W) is the
+ * (p - prefix[e])-th pair (e1, e3) of its middle edge e, e1 major.  Cost
+ * O(W) CheckMotif calls: exact counting for graphs whose W is at most some
+ * 1e11.  h_out: sum_x = C, sum_x2 = sum of squares of the per-path counts
+ * (so the exact variance of one sample is sum_x2 / W - (C / W)^2),
+ * k = W (paths), hits = paths with a match, estimate = C as FP64, std_err = 0.
+ * Synchronises the stream.
+ */
+tc_status tc_exact_count(const tc_graph* g, const tc_motif* motif, int64_t delta, const uint64_t* d_prefix,
+                         const void* d_index, tc_estimate* h_out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Learned proposal.  The paper's estimator draws the middle edge with
  * probability w_e / W (Alg. 2).  Any proposal q_e = w_e h_e with integer

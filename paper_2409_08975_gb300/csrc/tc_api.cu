@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -17,6 +18,35 @@ static thread_local std::string t_err;
 static std::atomic<uint64_t> g_launches{0};
 
 void note_launches(unsigned count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pools[dev], &props);
+      if (e != cudaSuccess) {
+        pools[dev] = nullptr;
+        return e;
+      }
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
 
 tc_status set_error(tc_status st, const std::string& msg) {
   t_err = msg;
@@ -291,11 +321,11 @@ tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delt
   uint32_t* err = nullptr;
   tc_status s = TC_OK;
   if (!w) {
-    cudaError_t e = cudaMallocAsync(&w, sizeof(uint64_t) * (m ? m : 1), st);
-    if (e != cudaSuccess) return cuda_status(e, "cudaMallocAsync(w)");
+    cudaError_t e = pool_malloc(&w, sizeof(uint64_t) * (m ? m : 1), st);
+    if (e != cudaSuccess) return cuda_status(e, "pool_malloc(w)");
   }
-  cudaError_t e = cudaMallocAsync(&err, sizeof(uint32_t), st);
-  if (e != cudaSuccess) s = cuda_status(e, "cudaMallocAsync(err)");
+  cudaError_t e = pool_malloc(&err, sizeof(uint32_t), st);
+  if (e != cudaSuccess) s = cuda_status(e, "pool_malloc(err)");
   if (s == TC_OK) {
     e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) s = cuda_status(e, "cudaMemsetAsync");
@@ -329,7 +359,7 @@ static tc_status sample_common(const tc_graph* g, const tc_motif* motif, int64_t
   if (((uintptr_t)d_index & 255) != 0) return set_error(TC_ERR_INVALID_ARG, "index must be 256-byte aligned");
   cudaStream_t st = S(stream);
   SampleSums* sums = nullptr;
-  TC_CUDA(cudaMallocAsync(&sums, sizeof(SampleSums), st));
+  TC_CUDA(pool_malloc(&sums, sizeof(SampleSums), st));
   tc_status s = TC_OK;
   cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(SampleSums), st);
   if (e != cudaSuccess) s = cuda_status(e, "cudaMemsetAsync");
@@ -388,9 +418,9 @@ tc_status tc_estimate_from_host(int64_t n, int64_t m, const int32_t* h_src, cons
   void* d_index = nullptr;
   tc_graph* g = nullptr;
   tc_status s = TC_OK;
-  cudaError_t e = cudaMallocAsync(&d_src, 4 * M, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&d_dst, 4 * M, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&d_t, 8 * M, st);
+  cudaError_t e = pool_malloc(&d_src, 4 * M, st);
+  if (e == cudaSuccess) e = pool_malloc(&d_dst, 4 * M, st);
+  if (e == cudaSuccess) e = pool_malloc(&d_t, 8 * M, st);
   if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_src, h_src, 4 * (size_t)m, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_dst, h_dst, 4 * (size_t)m, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && m) e = cudaMemcpyAsync(d_t, h_t, 8 * (size_t)m, cudaMemcpyHostToDevice, st);
@@ -402,8 +432,8 @@ tc_status tc_estimate_from_host(int64_t n, int64_t m, const int32_t* h_src, cons
   size_t ib = 0;
   if (s == TC_OK) s = tc_sample_index_bytes(g, &ib);
   if (s == TC_OK) {
-    e = cudaMallocAsync(&d_prefix, 8 * ((size_t)m + 1), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_index, ib, st);
+    e = pool_malloc(&d_prefix, 8 * ((size_t)m + 1), st);
+    if (e == cudaSuccess) e = pool_malloc(&d_index, ib, st);
     if (e != cudaSuccess) s = cuda_status(e, "cudaMallocAsync");
   }
   uint64_t W = 0;
@@ -414,6 +444,46 @@ tc_status tc_estimate_from_host(int64_t n, int64_t m, const int32_t* h_src, cons
   cudaStreamSynchronize(st);
   if (g) tc_graph_destroy(g);
   return s;
+}
+
+tc_status tc_exact_count(const tc_graph* g, const tc_motif* motif, int64_t delta, const uint64_t* d_prefix,
+                         const void* d_index, tc_estimate* h_out, void* stream) {
+  TC_TRY(check_graph(g));
+  Plan plan;
+  TC_TRY(plan_of(motif, &plan));
+  if (delta < 0) return set_error(TC_ERR_INVALID_ARG, "delta must be >= 0");
+  if (!d_prefix || !d_index || !h_out) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
+  if (((uintptr_t)d_index & 255) != 0) return set_error(TC_ERR_INVALID_ARG, "index must be 256-byte aligned");
+  cudaStream_t st = S(stream);
+  uint64_t W = 0;
+  TC_CUDA(cudaMemcpyAsync(&W, d_prefix + g->m, sizeof(W), cudaMemcpyDeviceToHost, st));
+  TC_CUDA(cudaStreamSynchronize(st));
+  SampleSums* sums = nullptr;
+  TC_CUDA(pool_malloc(&sums, sizeof(SampleSums), st));
+  tc_status s = TC_OK;
+  cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(SampleSums), st);
+  if (e != cudaSuccess) s = cuda_status(e, "memset");
+  if (s == TC_OK && W) s = launch_path_sum(g, plan, delta, d_prefix, d_index, W, sums, st);
+  SampleSums h;
+  std::memset(&h, 0, sizeof(h));
+  if (s == TC_OK) {
+    e = cudaMemcpyAsync(&h, sums, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_status(e, "tc_exact_count");
+  }
+  cudaFreeAsync(sums, st);
+  if (s == TC_OK && h.err) s = device_status(h.err, "tc_exact_count");
+  if (s != TC_OK) return s;
+  h_out->W = W;
+  h_out->k = W;
+  h_out->sum_x = h.sum_x;
+  h_out->sum_x2_lo = h.sum_x2_lo;
+  h_out->sum_x2_hi = h.sum_x2_hi;
+  h_out->hits = h.hits;
+  h_out->checked = h.checked;
+  h_out->estimate = (double)h.sum_x;
+  h_out->std_err = 0.0;
+  return TC_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -478,7 +548,7 @@ tc_status tc_mlp_grad(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t*
   if (!mlp || !d_grad || (n && (!d_feat || !d_labels))) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t st = S(stream);
   float* loss = nullptr;
-  TC_CUDA(cudaMallocAsync(&loss, sizeof(float), st));
+  TC_CUDA(pool_malloc(&loss, sizeof(float), st));
   tc_status s = TC_OK;
   cudaError_t e = cudaMemsetAsync(d_grad, 0, sizeof(float) * TC_MLP_PARAMS, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
@@ -513,11 +583,11 @@ tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, in
   float* losses = nullptr;
   SampleSums* sums = nullptr;
   tc_status s = TC_OK;
-  cudaError_t e = cudaMallocAsync(&trace, 32 * n_samples, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&rows, 4 * n_samples, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&labels, 4 * n_samples, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&losses, sizeof(float) * steps, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&sums, sizeof(SampleSums), st);
+  cudaError_t e = pool_malloc(&trace, 32 * n_samples, st);
+  if (e == cudaSuccess) e = pool_malloc(&rows, 4 * n_samples, st);
+  if (e == cudaSuccess) e = pool_malloc(&labels, 4 * n_samples, st);
+  if (e == cudaSuccess) e = pool_malloc(&losses, sizeof(float) * steps, st);
+  if (e == cudaSuccess) e = pool_malloc(&sums, sizeof(SampleSums), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(SampleSums), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(losses, 0, sizeof(float) * steps, st);
   if (e != cudaSuccess) s = cuda_status(e, "tc_mlp_train allocation");
@@ -573,8 +643,8 @@ tc_status tc_proposal_weights(const tc_mlp* mlp, const tc_graph* g, const tc_mot
   uint64_t* q = nullptr;
   uint32_t* err = nullptr;
   tc_status s = TC_OK;
-  cudaError_t e = cudaMallocAsync(&q, 8 * (m ? m : 1), st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&err, sizeof(uint32_t), st);
+  cudaError_t e = pool_malloc(&q, 8 * (m ? m : 1), st);
+  if (e == cudaSuccess) e = pool_malloc(&err, sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) s = cuda_status(e, "tc_proposal_weights allocation");
   if (s == TC_OK) s = launch_proposal(mlp, d_feat, d_prefix, m, eps, (float)scale, d_h, q, st);
@@ -610,8 +680,8 @@ tc_status tc_sample_estimate_q(const tc_graph* g, const tc_motif* motif, int64_t
   unsigned long long* bins = nullptr;
   SampleSums* sums = nullptr;
   tc_status s = TC_OK;
-  cudaError_t e = cudaMallocAsync(&bins, 8 * nbins, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&sums, sizeof(SampleSums), st);
+  cudaError_t e = pool_malloc(&bins, 8 * nbins, st);
+  if (e == cudaSuccess) e = pool_malloc(&sums, sizeof(SampleSums), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(bins, 0, 8 * nbins, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(SampleSums), st);
   if (e != cudaSuccess) s = cuda_status(e, "tc_sample_estimate_q allocation");

@@ -159,7 +159,7 @@ static tc_status scan_rec(const T* in, T* out, uint64_t n, bool write_total, uin
     return TC_OK;
   }
   T* sums = nullptr;
-  TC_CUDA(cudaMallocAsync(&sums, sizeof(T) * tiles, st));
+  TC_CUDA(pool_malloc(&sums, sizeof(T) * tiles, st));
   k_tile_reduce<T><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums, d_err);
   TC_LAUNCHED(1);
   tc_status s = TC_OK;
@@ -311,7 +311,7 @@ tc_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v
   if (n <= 1 || bit1 <= bit0) return TC_OK;
   const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
   uint32_t* hist = nullptr;
-  TC_CUDA(cudaMallocAsync(&hist, sizeof(uint32_t) * (kRadix * tiles + 1), st));
+  TC_CUDA(pool_malloc(&hist, sizeof(uint32_t) * (kRadix * tiles + 1), st));
   tc_status s = TC_OK;
   uint32_t *ka = k0, *va = v0, *kb = k1, *vb = v1;
   for (int bit = bit0; bit < bit1 && s == TC_OK; bit += 8) {
@@ -340,19 +340,24 @@ tc_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v
 }
 
 // ---------------------------------------------------------------------------
-// Graph build.
+// Graph build.  The input edges are first packed into one 16-byte record
+// {src, dst, t} per input index, so that every later gather by a sorted
+// permutation is one random load.
 
-__global__ void k_check_ids(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                            const int64_t* __restrict__ t, uint64_t m, int64_t n, uint32_t* err,
-                            long long* tminmax) {
+__global__ void k_check_pack(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                             const int64_t* __restrict__ t, uint64_t m, int64_t n, uint32_t* err, long long* tminmax,
+                             OutEdge* __restrict__ pack) {
   long long lo = INT64_MAX, hi = INT64_MIN;
   bool bad = false;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
-    const int32_t a = src[i], b = dst[i];
-    if (a < 0 || a >= n || b < 0 || b >= n) bad = true;
-    const long long x = t[i];
-    lo = x < lo ? x : lo;
-    hi = x > hi ? x : hi;
+    OutEdge r;
+    r.src = src[i];
+    r.dst = dst[i];
+    r.t = t[i];
+    if (r.src < 0 || r.src >= n || r.dst < 0 || r.dst >= n) bad = true;
+    lo = r.t < lo ? r.t : lo;
+    hi = r.t > hi ? r.t : hi;
+    pack[i] = r;
   }
   for (int o = 16; o > 0; o >>= 1) {
     long long l2 = __shfl_down_sync(0xffffffffu, lo, o), h2 = __shfl_down_sync(0xffffffffu, hi, o);
@@ -376,16 +381,19 @@ __global__ void k_time_keys(const int64_t* __restrict__ t, uint64_t m, int64_t t
   }
 }
 
-__global__ void k_high_time_keys(const int64_t* __restrict__ t, const uint32_t* __restrict__ perm, uint64_t m,
+__global__ void k_high_time_keys(const OutEdge* __restrict__ pack, const uint32_t* __restrict__ perm, uint64_t m,
                                  int64_t tmin, uint32_t* keys) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
-    keys[i] = (uint32_t)(((uint64_t)t[perm[i]] - (uint64_t)tmin) >> 32);
+    keys[i] = (uint32_t)(((uint64_t)pack[perm[i]].t - (uint64_t)tmin) >> 32);
 }
 
-__global__ void k_gather_key(const int32_t* __restrict__ col, const uint32_t* __restrict__ perm, uint64_t m,
-                             uint32_t* keys) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
-    keys[i] = (uint32_t)col[perm[i]];
+// keys[i] = src (field 0) or dst (field 1) of edge perm[i]
+__global__ void k_gather_key(const OutEdge* __restrict__ pack, const uint32_t* __restrict__ perm, uint64_t m,
+                             int field, uint32_t* keys) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const OutEdge r = pack[perm[i]];
+    keys[i] = (uint32_t)(field ? r.dst : r.src);
+  }
 }
 
 // off[v] = first position whose (sorted) key is >= v, for v in [0, n]
@@ -397,61 +405,57 @@ __global__ void k_offsets(const uint32_t* __restrict__ sorted, uint64_t len, int
   }
 }
 
-__global__ void k_fill_out(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                           const int64_t* __restrict__ t, const uint32_t* __restrict__ perm, uint64_t m,
+__global__ void k_fill_out(const OutEdge* __restrict__ pack, const uint32_t* __restrict__ perm, uint64_t m,
                            OutEdge* out_e, uint32_t* canon) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t e = perm[i];
-    OutEdge r;
-    r.src = src[e];
-    r.dst = dst[e];
-    r.t = t[e];
-    out_e[i] = r;
+    out_e[i] = pack[e];
     canon[e] = (uint32_t)i;
   }
 }
 
-__global__ void k_fill_in(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                          const int64_t* __restrict__ t, const uint32_t* __restrict__ perm,
+__global__ void k_fill_in(const OutEdge* __restrict__ pack, const uint32_t* __restrict__ perm,
                           const uint32_t* __restrict__ canon, uint64_t m, InEdge* in_e, uint32_t* in_eid) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t e = perm[i];
-    InEdge r;
-    r.src = src[e];
-    r.dst = dst[e];
-    r.t = t[e];
-    in_e[i] = r;
+    const OutEdge r = pack[e];
+    InEdge q;
+    q.src = r.src;
+    q.dst = r.dst;
+    q.t = r.t;
+    in_e[i] = q;
     in_eid[i] = canon[e];
   }
 }
 
-// pair flags: 1 where (src, dst) differs from the previous pair-order position
-__global__ void k_pair_flags(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                             const uint32_t* __restrict__ perm, uint64_t m, uint32_t* flags) {
+// pair order: destination, time and canonical id of each position
+__global__ void k_pair_gather(const OutEdge* __restrict__ pack, const uint32_t* __restrict__ perm,
+                              const uint32_t* __restrict__ canon, uint64_t m, int32_t* __restrict__ pdst,
+                              int64_t* __restrict__ pair_t, uint32_t* __restrict__ pair_eid) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t e = perm[i];
-    uint32_t f = 1;
-    if (i > 0) {
-      const uint32_t p = perm[i - 1];
-      f = (src[p] != src[e] || dst[p] != dst[e]) ? 1u : 0u;
-    }
-    flags[i] = f;
+    const OutEdge r = pack[e];
+    pdst[i] = r.dst;
+    pair_t[i] = r.t;
+    pair_eid[i] = canon[e];
   }
 }
 
-__global__ void k_fill_pairs(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                             const int64_t* __restrict__ t, const uint32_t* __restrict__ perm,
-                             const uint32_t* __restrict__ canon, const uint32_t* __restrict__ flags,
-                             const uint32_t* __restrict__ pidx, uint64_t m, int32_t* pair_dst, uint32_t* pair_eoff,
-                             uint32_t* pair_src, int64_t* pair_t, uint32_t* pair_eid) {
+// pair flags: 1 where (src, dst) differs from the previous position
+__global__ void k_pair_flags(const uint32_t* __restrict__ psrc, const int32_t* __restrict__ pdst, uint64_t m,
+                             uint32_t* flags) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    flags[i] = (i == 0 || psrc[i] != psrc[i - 1] || pdst[i] != pdst[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_fill_pairs(const uint32_t* __restrict__ psrc, const int32_t* __restrict__ pdst,
+                             const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pidx, uint64_t m,
+                             int32_t* pair_dst, uint32_t* pair_eoff, uint32_t* pair_src) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t e = perm[i];
-    pair_t[i] = t[e];
-    pair_eid[i] = canon[e];
     if (flags[i]) {
       const uint32_t p = pidx[i];
-      pair_dst[p] = dst[e];
-      pair_src[p] = (uint32_t)src[e];
+      pair_dst[p] = pdst[i];
+      pair_src[p] = psrc[i];
       pair_eoff[p] = (uint32_t)i;
     }
   }
@@ -492,7 +496,7 @@ template <class T>
 static tc_status dmalloc(T** p, uint64_t count, cudaStream_t st) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMallocAsync((void**)p, sizeof(T) * count, st);
+  cudaError_t e = pool_malloc((void**)p, sizeof(T) * count, st);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return set_error(TC_ERR_OOM, "device allocation failed");
@@ -521,10 +525,12 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   uint32_t *err = nullptr, *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr, *permT = nullptr,
            *canon = nullptr, *flags = nullptr, *pidx = nullptr, *pair_src = nullptr;
   long long* tmm = nullptr;
+  OutEdge* pack = nullptr;
+  int32_t* pdst = nullptr;
   tc_status s = TC_OK;
   auto done = [&](tc_status r) {
     for (void* p : {(void*)err, (void*)ka, (void*)va, (void*)kb, (void*)vb, (void*)permT, (void*)canon,
-                    (void*)flags, (void*)pidx, (void*)pair_src, (void*)tmm})
+                    (void*)flags, (void*)pidx, (void*)pair_src, (void*)tmm, (void*)pack, (void*)pdst})
       if (p) cudaFreeAsync(p, st);
     return r;
   };
@@ -541,13 +547,14 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
 
   TRY_S(dmalloc(&err, 1, st));
   TRY_S(dmalloc(&tmm, 2, st));
+  TRY_S(dmalloc(&pack, M, st));
   TRY_C(cudaMemsetAsync(err, 0, sizeof(uint32_t), st), "memset");
   long long init[2] = {INT64_MAX, INT64_MIN};
   TRY_C(cudaMemcpyAsync(tmm, init, sizeof(init), cudaMemcpyHostToDevice, st), "memcpy");
   if (M) {
-    k_check_ids<<<grid_for(M), 256, 0, st>>>(d_src, d_dst, d_t, M, n, err, tmm);
+    k_check_pack<<<grid_for(M), 256, 0, st>>>(d_src, d_dst, d_t, M, n, err, tmm, pack);
     TC_LAUNCHED(1);
-    TRY_C(cudaGetLastError(), "k_check_ids");
+    TRY_C(cudaGetLastError(), "k_check_pack");
   }
   uint32_t h_err = 0;
   long long h_tmm[2];
@@ -576,7 +583,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
     TRY_C(cudaGetLastError(), "k_time_keys");
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, std::min(tbits, 32), st));
     if (tbits > 32) {
-      k_high_time_keys<<<gr, 256, 0, st>>>(d_t, va, M, g->tmin, ka);
+      k_high_time_keys<<<gr, 256, 0, st>>>(pack, va, M, g->tmin, ka);
       TC_LAUNCHED(1);
       TRY_C(cudaGetLastError(), "k_high_time_keys");
       TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, tbits - 32, st));
@@ -586,11 +593,11 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
 
   // 2. out-lists: stable by src of the time order -> (src, t, index)
   if (M) {
-    k_gather_key<<<gr, 256, 0, st>>>(d_src, permT, M, ka);
+    k_gather_key<<<gr, 256, 0, st>>>(pack, permT, M, 0, ka);
     TC_LAUNCHED(1);
     TRY_C(cudaMemcpyAsync(va, permT, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
-    k_fill_out<<<gr, 256, 0, st>>>(d_src, d_dst, d_t, va, M, g->out_e, canon);
+    k_fill_out<<<gr, 256, 0, st>>>(pack, va, M, g->out_e, canon);
     TC_LAUNCHED(1);
     TRY_C(cudaGetLastError(), "k_fill_out");
     TRY_C(cudaMemcpyAsync(g->perm, va, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
@@ -601,11 +608,11 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
 
   // 3. in-lists: stable by dst of the time order -> (dst, t, index)
   if (M) {
-    k_gather_key<<<gr, 256, 0, st>>>(d_dst, permT, M, ka);
+    k_gather_key<<<gr, 256, 0, st>>>(pack, permT, M, 1, ka);
     TC_LAUNCHED(1);
     TRY_C(cudaMemcpyAsync(va, permT, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
-    k_fill_in<<<gr, 256, 0, st>>>(d_src, d_dst, d_t, va, canon, M, g->in_e, g->in_eid);
+    k_fill_in<<<gr, 256, 0, st>>>(pack, va, canon, M, g->in_e, g->in_eid);
     TC_LAUNCHED(1);
     TRY_C(cudaGetLastError(), "k_fill_in");
   }
@@ -616,12 +623,16 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   // 4. pair lists: stable by src of the in-list order -> (src, dst, t, index)
   uint32_t P = 0;
   if (M) {
-    k_gather_key<<<gr, 256, 0, st>>>(d_src, va, M, ka);
+    k_gather_key<<<gr, 256, 0, st>>>(pack, va, M, 0, ka);
     TC_LAUNCHED(1);
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
     TRY_S(dmalloc(&flags, M, st));
     TRY_S(dmalloc(&pidx, M + 1, st));
-    k_pair_flags<<<gr, 256, 0, st>>>(d_src, d_dst, va, M, flags);
+    TRY_S(dmalloc(&pdst, M, st));
+    k_pair_gather<<<gr, 256, 0, st>>>(pack, va, canon, M, pdst, g->pair_t, g->pair_eid);
+    TC_LAUNCHED(1);
+    TRY_C(cudaGetLastError(), "k_pair_gather");
+    k_pair_flags<<<gr, 256, 0, st>>>(ka, pdst, M, flags);
     TC_LAUNCHED(1);
     TRY_C(cudaGetLastError(), "k_pair_flags");
     TRY_S(scan_u32(flags, pidx, M, st));
@@ -633,8 +644,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   TRY_S(dmalloc(&g->pair_eoff, (uint64_t)P + 1, st));
   TRY_S(dmalloc(&pair_src, P, st));
   if (M) {
-    k_fill_pairs<<<gr, 256, 0, st>>>(d_src, d_dst, d_t, va, canon, flags, pidx, M, g->pair_dst, g->pair_eoff,
-                                     pair_src, g->pair_t, g->pair_eid);
+    k_fill_pairs<<<gr, 256, 0, st>>>(ka, pdst, flags, pidx, M, g->pair_dst, g->pair_eoff, pair_src);
     TC_LAUNCHED(1);
     TRY_C(cudaGetLastError(), "k_fill_pairs");
   }

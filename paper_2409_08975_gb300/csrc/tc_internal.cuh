@@ -131,6 +131,15 @@ namespace tc {
 // Errors (thread-local message, see tc_last_error).
 
 tc_status set_error(tc_status st, const std::string& msg);
+
+// Stream-ordered allocation from a pool owned by the library (one per
+// device) that keeps freed memory for reuse instead of returning it to the
+// system at every synchronisation.
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st);
+template <class T>
+inline cudaError_t pool_malloc(T** p, size_t bytes, cudaStream_t st) {
+  return pool_malloc(reinterpret_cast<void**>(p), bytes, st);
+}
 tc_status cuda_status(cudaError_t e, const char* what);
 tc_status device_status(uint32_t bits, const char* what);
 
@@ -222,6 +231,7 @@ __device__ __forceinline__ uint32_t search_time(uint32_t lo, uint32_t hi, int64_
 
 // Window of x's list (alpha < 0: in-list, else out-list) around time t
 // (beta < 0: before, else after; strict or closed at t) as positions [lo, hi).
+// The two bounds are searched independently so that their loads overlap.
 __device__ __forceinline__ void window_range(const OutEdge* __restrict__ out_e,
                                              const uint32_t* __restrict__ out_off,
                                              const InEdge* __restrict__ in_e,
@@ -233,20 +243,20 @@ __device__ __forceinline__ void window_range(const OutEdge* __restrict__ out_e,
     auto tt = [&](uint32_t p) { return in_e[p].t; };
     if (beta < 0) {
       *lo = search_time<true>(a, b, sat_sub(t, delta), tt);
-      *hi = closed ? search_time<false>(*lo, b, t, tt) : search_time<true>(*lo, b, t, tt);
+      *hi = closed ? search_time<false>(a, b, t, tt) : search_time<true>(a, b, t, tt);
     } else {
       *lo = closed ? search_time<true>(a, b, t, tt) : search_time<false>(a, b, t, tt);
-      *hi = search_time<false>(*lo, b, sat_add(t, delta), tt);
+      *hi = search_time<false>(a, b, sat_add(t, delta), tt);
     }
   } else {
     const uint32_t a = __ldg(out_off + x), b = __ldg(out_off + x + 1);
     auto tt = [&](uint32_t p) { return out_e[p].t; };
     if (beta < 0) {
       *lo = search_time<true>(a, b, sat_sub(t, delta), tt);
-      *hi = closed ? search_time<false>(*lo, b, t, tt) : search_time<true>(*lo, b, t, tt);
+      *hi = closed ? search_time<false>(a, b, t, tt) : search_time<true>(a, b, t, tt);
     } else {
       *lo = closed ? search_time<true>(a, b, t, tt) : search_time<false>(a, b, t, tt);
-      *hi = search_time<false>(*lo, b, sat_add(t, delta), tt);
+      *hi = search_time<false>(a, b, sat_add(t, delta), tt);
     }
   }
 }
@@ -305,6 +315,8 @@ struct SampleSums {  // per-call device accumulator
   unsigned int pad;
 };
 
+tc_status launch_path_sum(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
+                          const void* index, uint64_t W, SampleSums* d_sums, cudaStream_t st);
 tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
                          const void* index, uint64_t k, uint64_t seed, uint64_t offset, uint64_t* trace,
                          SampleSums* d_sums, cudaStream_t st, const void* qindex = nullptr,

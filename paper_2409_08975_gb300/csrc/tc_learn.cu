@@ -50,13 +50,11 @@ __device__ __forceinline__ uint32_t count_window(const OutEdge* __restrict__ out
   if (in_list) {
     const uint32_t a = __ldg(in_off + x), b = __ldg(in_off + x + 1);
     auto tt = [&](uint32_t p) { return in_e[p].t; };
-    const uint32_t s = search_time<true>(a, b, lo, tt);
-    return search_time<false>(s, b, hi, tt) - s;
+    return search_time<false>(a, b, hi, tt) - search_time<true>(a, b, lo, tt);
   }
   const uint32_t a = __ldg(out_off + x), b = __ldg(out_off + x + 1);
   auto tt = [&](uint32_t p) { return out_e[p].t; };
-  const uint32_t s = search_time<true>(a, b, lo, tt);
-  return search_time<false>(s, b, hi, tt) - s;
+  return search_time<false>(a, b, hi, tt) - search_time<true>(a, b, lo, tt);
 }
 
 __device__ __forceinline__ uint32_t pair_count(const PairSlot* __restrict__ table, uint64_t mask,

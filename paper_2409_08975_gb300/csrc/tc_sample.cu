@@ -2,6 +2,8 @@
 // sampler with CheckMotif / ListCount and the reduction of X (Alg. 2-5).
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -351,6 +353,129 @@ __device__ __forceinline__ uint64_t check_motif(const SamplerArgs& A, const Plan
 #ifndef TC_SAMPLE_MIN_BLOCKS
 #define TC_SAMPLE_MIN_BLOCKS 4
 #endif
+#define TC_SAMPLE_MIN_BLOCKS_DECL TC_SAMPLE_MIN_BLOCKS
+
+// Warp-shuffle reduction of the per-thread sums, one shared atomic per warp
+// and one global atomic per block; 128-bit sum of squares with carries,
+// overflow of the 64-bit sum flagged.
+__device__ __forceinline__ void block_commit(SampleSums* G, uint64_t W, uint64_t sx, unsigned __int128 sx2,
+                                             uint64_t hits, uint64_t checked, uint32_t err, uint32_t& s_err,
+                                             unsigned long long& s_x, unsigned long long& s_x2lo,
+                                             unsigned long long& s_x2hi, unsigned long long& s_hits,
+                                             unsigned long long& s_checked) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t ox = __shfl_down_sync(0xffffffffu, sx, o);
+    const uint64_t olo = __shfl_down_sync(0xffffffffu, (uint64_t)sx2, o);
+    const uint64_t ohi = __shfl_down_sync(0xffffffffu, (uint64_t)(sx2 >> 64), o);
+    const uint64_t oh = __shfl_down_sync(0xffffffffu, hits, o);
+    const uint64_t oc = __shfl_down_sync(0xffffffffu, checked, o);
+    const uint32_t oe = __shfl_down_sync(0xffffffffu, err, o);
+    const uint64_t nx = sx + ox;
+    if (nx < sx) err |= kErrOverflow;
+    sx = nx;
+    sx2 += ((unsigned __int128)ohi << 64) | olo;
+    hits += oh;
+    checked += oc;
+    err |= oe;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    const unsigned long long old = atomicAdd(&s_x, (unsigned long long)sx);
+    if (old + sx < old) err |= kErrOverflow;
+    const unsigned long long lo = (uint64_t)sx2;
+    const unsigned long long ol = atomicAdd(&s_x2lo, lo);
+    const unsigned long long carry = (ol + lo < ol) ? 1ull : 0ull;
+    atomicAdd(&s_x2hi, (unsigned long long)(sx2 >> 64) + carry);
+    atomicAdd(&s_hits, (unsigned long long)hits);
+    atomicAdd(&s_checked, (unsigned long long)checked);
+    if (err) atomicOr(&s_err, err);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t e2 = s_err;
+    const unsigned long long old = atomicAdd(&G->sum_x, s_x);
+    if (old + s_x < old) e2 |= kErrOverflow;
+    const unsigned long long ol = atomicAdd(&G->sum_x2_lo, s_x2lo);
+    atomicAdd(&G->sum_x2_hi, s_x2hi + ((ol + s_x2lo < ol) ? 1ull : 0ull));
+    atomicAdd(&G->hits, s_hits);
+    atomicAdd(&G->checked, s_checked);
+    if (blockIdx.x == 0) G->W = W;
+    if (e2) atomicOr(&G->err, e2);
+  }
+}
+
+// Exhaustive path sum (the proof of Claim 2): path p in [0, W) is the
+// (p - prefix[e])-th pair (p1, p3) of middle edge e, p1 major; the sum of
+// CheckMotif over all paths is the exact count C, the sum of squares gives
+// the exact variance of one sample.  Paths [first, first + count).
+__global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS_DECL) k_path_sum(const __grid_constant__ SamplerArgs A,
+                                                                            const __grid_constant__ Plan P,
+                                                                            uint64_t first, uint64_t count) {
+  const IndexHeader* H = A.hdr;
+  const uint64_t W = H->W;
+  const uint32_t shift = H->shift;
+  __shared__ uint32_t s_err;
+  __shared__ unsigned long long s_x, s_x2lo, s_x2hi, s_hits, s_checked;
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    s_x = s_x2lo = s_x2hi = s_hits = s_checked = 0;
+  }
+  __syncthreads();
+  const bool ok = H->magic == kIndexMagic && H->status == 0 && H->cls[0] == P.alpha1 && H->cls[1] == P.alpha3 &&
+                  H->cls[2] == P.beta1 && H->cls[3] == P.beta3 && H->closed == P.closed && H->anchor[0] == P.e1 &&
+                  H->anchor[1] == P.mid && H->anchor[2] == P.e3 && H->delta == A.delta &&
+                  H->graph_id == A.graph_id;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(&A.sums->err, H->magic == kIndexMagic && H->status ? H->status : kErrIndexMismatch);
+    return;
+  }
+  uint64_t sx = 0, hits = 0, checked = 0;
+  unsigned __int128 sx2 = 0;
+  uint32_t err = 0;
+  const uint64_t end = first + count < W ? first + count : W;
+  for (uint64_t p = first + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < end;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = (uint32_t)(p >> shift);
+    uint32_t lo = __ldg(A.guide + b), hi = __ldg(A.guide + b + 1);
+    while (lo < hi) {
+      const uint32_t mid = lo + ((hi - lo + 1) >> 1);
+      if (__ldg(A.prefix + mid) <= p) lo = mid; else hi = mid - 1;
+    }
+    const EdgeRec e = A.rec[lo];
+    if (e.d1 == 0 || e.d3 == 0) { err |= kErrBounds; continue; }
+    const uint64_t j = p - __ldg(A.prefix + lo);
+    const uint32_t p1 = e.lo1 + (uint32_t)(j / e.d3), p3 = e.lo3 + (uint32_t)(j % e.d3);
+    if (lo >= A.m || p1 >= A.m || p3 >= A.m) { err |= kErrBounds; continue; }
+    int32_t up, vp;
+    int64_t t1, t3;
+    if (P.alpha1 < 0) {
+      const InEdge x = A.in_e[p1];
+      up = x.src;
+      t1 = x.t;
+    } else {
+      const OutEdge x = A.out_e[p1];
+      up = x.dst;
+      t1 = x.t;
+    }
+    if (P.alpha3 < 0) {
+      const InEdge x = A.in_e[p3];
+      vp = x.src;
+      t3 = x.t;
+    } else {
+      const OutEdge x = A.out_e[p3];
+      vp = x.dst;
+      t3 = x.t;
+    }
+    const uint64_t X = check_motif(A, P, up, e.u, e.v, vp, t1, e.t, t3, &s_err, &checked);
+    const uint64_t nx = sx + X;
+    if (nx < sx) err |= kErrOverflow;
+    sx = nx;
+    sx2 += (unsigned __int128)X * X;
+    hits += X != 0;
+  }
+  block_commit(A.sums, W, sx, sx2, hits, checked, err, s_err, s_x, s_x2lo, s_x2hi, s_hits, s_checked);
+}
+
 
 template <bool Trace>
 __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __grid_constant__ SamplerArgs A,
@@ -445,47 +570,7 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __gr
     sx2 += (unsigned __int128)X * X;
     hits += X != 0;
   }
-  // warp reduction, then one atomic per warp into shared, one per block global
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint64_t ox = __shfl_down_sync(0xffffffffu, sx, o);
-    const uint64_t olo = __shfl_down_sync(0xffffffffu, (uint64_t)sx2, o);
-    const uint64_t ohi = __shfl_down_sync(0xffffffffu, (uint64_t)(sx2 >> 64), o);
-    const uint64_t oh = __shfl_down_sync(0xffffffffu, hits, o);
-    const uint64_t oc = __shfl_down_sync(0xffffffffu, checked, o);
-    const uint32_t oe = __shfl_down_sync(0xffffffffu, err, o);
-    const uint64_t nx = sx + ox;
-    if (nx < sx) err |= kErrOverflow;
-    sx = nx;
-    sx2 += ((unsigned __int128)ohi << 64) | olo;
-    hits += oh;
-    checked += oc;
-    err |= oe;
-  }
-  if ((threadIdx.x & 31) == 0) {
-    const unsigned long long old = atomicAdd(&s_x, (unsigned long long)sx);
-    if (old + sx < old) err |= kErrOverflow;
-    const unsigned long long lo = (uint64_t)sx2;
-    const unsigned long long ol = atomicAdd(&s_x2lo, lo);
-    unsigned long long carry = (ol + lo < ol) ? 1ull : 0ull;
-    atomicAdd(&s_x2hi, (unsigned long long)(sx2 >> 64) + carry);
-    atomicAdd(&s_hits, (unsigned long long)hits);
-    atomicAdd(&s_checked, (unsigned long long)checked);
-    if (err) atomicOr(&s_err, err);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    SampleSums* G = A.sums;
-    uint32_t e2 = s_err;
-    const unsigned long long old = atomicAdd(&G->sum_x, s_x);
-    if (old + s_x < old) e2 |= kErrOverflow;
-    const unsigned long long ol = atomicAdd(&G->sum_x2_lo, s_x2lo);
-    atomicAdd(&G->sum_x2_hi, s_x2hi + ((ol + s_x2lo < ol) ? 1ull : 0ull));
-    atomicAdd(&G->hits, s_hits);
-    atomicAdd(&G->checked, s_checked);
-    if (blockIdx.x == 0) G->W = W;
-    if (e2) atomicOr(&G->err, e2);
-  }
+  block_commit(A.sums, W, sx, sx2, hits, checked, err, s_err, s_x, s_x2lo, s_x2hi, s_hits, s_checked);
 }
 
 // Processing order of the samples.  Samples whose middle-edge draws r are
@@ -748,7 +833,7 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   const size_t hist_words = (size_t)kBuckets * tiles_b_max + 1;
   char* buf = nullptr;
   const size_t bytes = 12 * chunk + 4 * hist_words + sizeof(SegInfo) + 256;
-  TC_CUDA(cudaMallocAsync(&buf, bytes, st));
+  TC_CUDA(pool_malloc(&buf, bytes, st));
   uint32_t* ids_a = (uint32_t*)buf;                  // after pass A
   uint32_t* ids_b = (uint32_t*)(buf + 4 * chunk);    // after pass B
   uint16_t* keys_0 = (uint16_t*)(buf + 8 * chunk);   // id order
@@ -790,6 +875,36 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   }
   cudaFreeAsync(buf, st);
   return s;
+}
+
+tc_status launch_path_sum(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
+                          const void* index, uint64_t W, SampleSums* d_sums, cudaStream_t st) {
+  const uint64_t m = (uint64_t)g->m;
+  IndexView v = index_view(const_cast<void*>(index), m);
+  SamplerArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.out_e = g->out_e;
+  A.in_e = g->in_e;
+  A.pair_hash = g->pair_hash;
+  A.hash_mask = g->hash_mask;
+  A.pair_t = g->pair_t;
+  A.prefix = prefix;
+  A.hdr = v.hdr;
+  A.rec = v.rec;
+  A.guide = v.guide;
+  A.m = (uint32_t)m;
+  A.delta = delta;
+  A.graph_id = g->id;
+  A.sums = d_sums;
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_path_sum, 256, 0);
+  uint64_t blocks = (uint64_t)num_sms() * (bps > 0 ? bps : 1);
+  const uint64_t need = (W + 255) / 256;
+  if (need < blocks) blocks = need ? need : 1;
+  k_path_sum<<<(unsigned)blocks, 256, 0, st>>>(A, plan, 0, W);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
 }
 
 }  // namespace tc

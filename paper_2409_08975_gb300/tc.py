@@ -71,6 +71,7 @@ def lib():
                                       ctypes.POINTER(tc_estimate), vp],
             "tc_motif_plan": [ctypes.POINTER(tc_motif), vp, vp],
             "tc_prefix_sum_noalloc": [vp, u64, vp, ctypes.POINTER(u64), vp],
+            "tc_exact_count": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, ctypes.POINTER(tc_estimate), vp],
             "tc_mlp_create": [u64, ctypes.POINTER(vp)],
             "tc_mlp_destroy": [vp],
             "tc_mlp_get_params": [vp, vp],
@@ -238,6 +239,14 @@ def tc_sample_estimate(g, motif, delta, weights, k, seed=0, offset=0, stream=Non
     _check(lib().tc_sample_estimate(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix),
                                     _ptr(weights.index), int(k), int(seed), int(offset), ctypes.byref(e),
                                     _stream(stream)), "tc_sample_estimate")
+    return _est_dict(e)
+
+
+def tc_exact_count(g, motif, delta, weights, stream=None):
+    """Exact count C by summing CheckMotif over all W class paths."""
+    e = tc_estimate()
+    _check(lib().tc_exact_count(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix), _ptr(weights.index),
+                                ctypes.byref(e), _stream(stream)), "tc_exact_count")
     return _est_dict(e)
 
 

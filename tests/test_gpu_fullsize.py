@@ -92,3 +92,11 @@ def test_bench_launch_merges_exactly(setup):
     assert full["hits"] > 0 and full["estimate"] > 0
     # the estimate's standard error is small at this k
     assert full["std_err"] < 0.05 * full["estimate"]
+    # exact count by the exhaustive path sum: the estimate lies within five
+    # standard errors, and the sum of squares gives that standard error
+    ex = tc.tc_exact_count(g, mot, cfg["delta"], w)
+    C, W = ex["sum_x"], ex["W"]
+    assert abs(full["estimate"] - C) < 5 * full["std_err"]
+    var = ex["sum_x2"] / W - (C / W) ** 2
+    exact_se = W * (var / K) ** 0.5
+    assert 0.9 * exact_se < full["std_err"] < 1.1 * exact_se

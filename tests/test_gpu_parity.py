@@ -171,6 +171,33 @@ def test_key_sorted_sampling_bit_exact(tc, case):
             assert est[key] == osums[key]
 
 
+@pytest.mark.parametrize("case", GRAPHS, ids=lambda c: c[0])
+def test_exact_count_matches_path_sum(tc, case):
+    # the exhaustive GPU path sum equals the oracle's path sum (itself pinned
+    # to the literal count of Def. 2 on tiny graphs by the CPU tests)
+    name, n, src, dst, t = case
+    g, og = _build_both(tc, n, src, dst, t)
+    delta = 10_000 if name != "small" else 60
+    for edges in (C4, CHORD, MULTI, LATE_MID):
+        for window in (0, 1):
+            plan = oracle.compile_motif(edges, closed=bool(window))
+            mot = tc.make_motif(edges, window=window)
+            w = tc.tc_path_weights(g, mot, delta)
+            r = tc.tc_exact_count(g, mot, delta, w)
+            ps = oracle.path_sum(og, plan, delta)
+            assert r["sum_x"] == ps["C"] and r["sum_x2"] == ps["sum_x2"] and r["k"] == ps["paths"] == w.W
+
+
+def test_exact_count_hand_graphs(tc):
+    import torch
+    from _graphs import hand_graphs
+    for name, edges, delta, count, src, dst, t in hand_graphs():
+        g = tc.tc_build_temporal_csr(4, _dev(src, torch.int32), _dev(dst, torch.int32), _dev(t, torch.int64))
+        mot = tc.make_motif(edges)
+        w = tc.tc_path_weights(g, mot, delta)
+        assert tc.tc_exact_count(g, mot, delta, w)["sum_x"] == count, name
+
+
 def test_tiny_config_estimate(tc):
     from paper_2409_08975_gb300 import synth
     cfg = synth.tiny()
