@@ -226,41 +226,48 @@ constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kRadix = 256;
+constexpr int kMaxDigitBits = 11;
+constexpr int kMaxRadix = 1 << kMaxDigitBits;
 
 // warp w of a tile owns keys [w * 32 * kSortItems, (w + 1) * 32 * kSortItems)
 __device__ __forceinline__ uint64_t sort_index(uint64_t tile, int warp, int item, int lane) {
   return tile * kSortTile + (uint64_t)warp * 32 * kSortItems + (uint64_t)item * 32 + lane;
 }
 
+// hist[d * tiles + tile] = keys of the tile whose digit (key >> bit) & (2^nbits - 1) is d
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, uint64_t n,
                                                            int bit, int nbits, uint32_t* __restrict__ hist,
                                                            uint32_t tiles) {
-  __shared__ uint32_t s_hist[kRadix];
-  for (int i = threadIdx.x; i < kRadix; i += kSortThreads) s_hist[i] = 0;
+  extern __shared__ uint32_t s_hist[];
+  const int radix = 1 << nbits;
+  for (int i = threadIdx.x; i < radix; i += kSortThreads) s_hist[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t mask = (1u << nbits) - 1u;
+  const uint32_t mask = (uint32_t)radix - 1u;
 #pragma unroll 4
   for (int j = 0; j < kSortItems; j++) {
     const uint64_t i = sort_index(blockIdx.x, warp, j, lane);
     if (i < n) atomicAdd(&s_hist[(keys[i] >> bit) & mask], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[(uint64_t)d * tiles + blockIdx.x] = s_hist[d];
+  for (int d = threadIdx.x; d < radix; d += kSortThreads) hist[(uint64_t)d * tiles + blockIdx.x] = s_hist[d];
 }
 
+// Stable scatter: per-warp digit counts (warp-level multisplit with
+// __match_any_sync) in input order, then each warp's keys go to the digit's
+// global offset plus the counts of earlier warps and lanes.
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                               const uint32_t* __restrict__ vin, uint64_t n,
                                                               int bit, int nbits,
                                                               const uint32_t* __restrict__ offs,
                                                               uint32_t tiles, uint32_t* __restrict__ kout,
                                                               uint32_t* __restrict__ vout) {
-  __shared__ uint32_t s_cnt[kSortWarps][kRadix];
+  extern __shared__ uint32_t s_cnt[];  // [kSortWarps][radix]
+  const int radix = 1 << nbits;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t mask = (1u << nbits) - 1u;
+  const uint32_t mask = (uint32_t)radix - 1u;
   const uint32_t lt = (1u << lane) - 1u;
-  for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < kSortWarps * radix; i += kSortThreads) s_cnt[i] = 0;
   __syncthreads();
   uint32_t key[kSortItems], val[kSortItems];
 #pragma unroll
@@ -269,61 +276,72 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
     key[j] = i < n ? kin[i] : 0u;
     val[j] = i < n ? vin[i] : 0u;
   }
-  // phase 1: per-warp digit counts
+  uint32_t* my = s_cnt + warp * radix;
 #pragma unroll
   for (int j = 0; j < kSortItems; j++) {
     const uint64_t i = sort_index(blockIdx.x, warp, j, lane);
     const uint32_t d = i < n ? ((key[j] >> bit) & mask) : 0xFFFFFFFFu;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (d != 0xFFFFFFFFu && (peers & lt) == 0) s_cnt[warp][d] += __popc(peers);
+    if (d != 0xFFFFFFFFu && (peers & lt) == 0) my[d] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // per digit: global tile offset + counts of earlier warps
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+  for (int d = threadIdx.x; d < radix; d += kSortThreads) {
     uint32_t run = offs[(uint64_t)d * tiles + blockIdx.x];
     for (int w = 0; w < kSortWarps; w++) {
-      const uint32_t c = s_cnt[w][d];
-      s_cnt[w][d] = run;
+      const uint32_t c = s_cnt[w * radix + d];
+      s_cnt[w * radix + d] = run;
       run += c;
     }
   }
   __syncthreads();
-  // phase 2: stable scatter in input order
 #pragma unroll
   for (int j = 0; j < kSortItems; j++) {
     const uint64_t i = sort_index(blockIdx.x, warp, j, lane);
     const uint32_t d = i < n ? ((key[j] >> bit) & mask) : 0xFFFFFFFFu;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     if (d != 0xFFFFFFFFu) {
-      const uint32_t pos = s_cnt[warp][d] + __popc(peers & lt);
+      const uint32_t pos = my[d] + __popc(peers & lt);
       kout[pos] = key[j];
       vout[pos] = val[j];
     }
     __syncwarp();
-    if (d != 0xFFFFFFFFu && (peers & lt) == 0) s_cnt[warp][d] += __popc(peers);
+    if (d != 0xFFFFFFFFu && (peers & lt) == 0) my[d] += __popc(peers);
     __syncwarp();
   }
 }
 
+// Sorts on bits [bit0, bit1) in ceil((bit1 - bit0) / 11) passes of equal
+// width (at most 11 bits, 2048 digits).
 tc_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint64_t n, int bit0,
                            int bit1, cudaStream_t st) {
   if (n <= 1 || bit1 <= bit0) return TC_OK;
+  static bool attr = false;
+  if (!attr) {
+    TC_CUDA(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(uint32_t) * kSortWarps * kMaxRadix)));
+    attr = true;
+  }
+  const int total = bit1 - bit0;
+  const int passes = (total + kMaxDigitBits - 1) / kMaxDigitBits;
+  const int width = (total + passes - 1) / passes;
   const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
   uint32_t* hist = nullptr;
-  TC_CUDA(pool_malloc(&hist, sizeof(uint32_t) * (kRadix * tiles + 1), st));
+  TC_CUDA(pool_malloc(&hist, sizeof(uint32_t) * ((uint64_t)(1 << width) * tiles + 1), st));
   tc_status s = TC_OK;
   uint32_t *ka = k0, *va = v0, *kb = k1, *vb = v1;
-  for (int bit = bit0; bit < bit1 && s == TC_OK; bit += 8) {
-    const int nbits = std::min(8, bit1 - bit);
-    k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, n, bit, nbits, hist, (uint32_t)tiles);
+  for (int bit = bit0; bit < bit1 && s == TC_OK; bit += width) {
+    const int nbits = std::min(width, bit1 - bit);
+    const int radix = 1 << nbits;
+    k_sort_hist<<<(unsigned)tiles, kSortThreads, sizeof(uint32_t) * radix, st>>>(ka, n, bit, nbits, hist,
+                                                                                (uint32_t)tiles);
     TC_LAUNCHED(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { s = cuda_status(e, "k_sort_hist"); break; }
-    s = scan_rec<uint32_t>(hist, hist, kRadix * tiles, false, nullptr, st);
+    s = scan_rec<uint32_t>(hist, hist, (uint64_t)radix * tiles, false, nullptr, st);
     if (s != TC_OK) break;
-    k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, va, n, bit, nbits, hist, (uint32_t)tiles, kb,
-                                                             vb);
+    k_sort_scatter<<<(unsigned)tiles, kSortThreads, sizeof(uint32_t) * kSortWarps * radix, st>>>(
+        ka, va, n, bit, nbits, hist, (uint32_t)tiles, kb, vb);
     TC_LAUNCHED(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) { s = cuda_status(e, "k_sort_scatter"); break; }
@@ -387,13 +405,11 @@ __global__ void k_high_time_keys(const OutEdge* __restrict__ pack, const uint32_
     keys[i] = (uint32_t)(((uint64_t)pack[perm[i]].t - (uint64_t)tmin) >> 32);
 }
 
-// keys[i] = src (field 0) or dst (field 1) of edge perm[i]
-__global__ void k_gather_key(const OutEdge* __restrict__ pack, const uint32_t* __restrict__ perm, uint64_t m,
-                             int field, uint32_t* keys) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
-    const OutEdge r = pack[perm[i]];
-    keys[i] = (uint32_t)(field ? r.dst : r.src);
-  }
+// keys[i] = col[perm[i]] (the 4-byte column stays in L2 better than the records)
+__global__ void k_gather_key(const int32_t* __restrict__ col, const uint32_t* __restrict__ perm, uint64_t m,
+                             uint32_t* keys) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x)
+    keys[i] = (uint32_t)col[perm[i]];
 }
 
 // off[v] = first position whose (sorted) key is >= v, for v in [0, n]
@@ -593,7 +609,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
 
   // 2. out-lists: stable by src of the time order -> (src, t, index)
   if (M) {
-    k_gather_key<<<gr, 256, 0, st>>>(pack, permT, M, 0, ka);
+    k_gather_key<<<gr, 256, 0, st>>>(d_src, permT, M, ka);
     TC_LAUNCHED(1);
     TRY_C(cudaMemcpyAsync(va, permT, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
@@ -608,7 +624,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
 
   // 3. in-lists: stable by dst of the time order -> (dst, t, index)
   if (M) {
-    k_gather_key<<<gr, 256, 0, st>>>(pack, permT, M, 1, ka);
+    k_gather_key<<<gr, 256, 0, st>>>(d_dst, permT, M, ka);
     TC_LAUNCHED(1);
     TRY_C(cudaMemcpyAsync(va, permT, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
@@ -623,7 +639,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   // 4. pair lists: stable by src of the in-list order -> (src, dst, t, index)
   uint32_t P = 0;
   if (M) {
-    k_gather_key<<<gr, 256, 0, st>>>(pack, va, M, 0, ka);
+    k_gather_key<<<gr, 256, 0, st>>>(d_src, va, M, ka);
     TC_LAUNCHED(1);
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
     TRY_S(dmalloc(&flags, M, st));
