@@ -44,9 +44,13 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--samples", type=int, default=None, help="samples per step (default: the config's k)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--exact-max-paths", type=float, default=2e11,
+                    help="run the exhaustive exact count when W is at most this")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--train-samples", type=int, default=10_000_000)
+    ap.add_argument("--workload", default="mid", choices=["mid", "learned", "large"],
+                    help="mid: the 20M-edge graph (default); learned: n=2e7, m=1e8; large: n=1e8, m=3e8")
     return ap.parse_args()
 
 
@@ -122,9 +126,19 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def workload():
+def workload(name="mid"):
     from paper_2409_08975_gb300 import synth
-    return synth.mid()
+    return synth.CONFIGS[name]()
+
+
+WORKLOADS = {
+    "mid": "mid: Chung-Lu-weighted bursty graph n=1M m=20M gamma=2.1 max_deg~1e5 30% multi-edges over 1e8 s; "
+           "motif a->b,b->c,c->d,a->d (path+chord), delta=3600, k=1e8 samples per step",
+    "learned": "learned: the mid generator at n=20M m=100M; path+chord, delta=3600, k=1e8 samples per step; "
+               "learned proposal trained on 1e7 plain samples",
+    "large": "large: n=100M m=300M, top degree ~1e6, pair multiplicities Zipf(1.8), daily periodicity over 1e8 s; "
+             "directed 4-cycle (M4-0), delta=3600, k=1e9 samples per step",
+}
 
 
 def cpu_baseline(cfg, k_total, sample_k=300_000):
@@ -152,7 +166,7 @@ def cpu_baseline(cfg, k_total, sample_k=300_000):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    cfg = workload()
+    cfg = workload(args.workload)
     k = args.samples or cfg["k"]
     import oracle
     og = oracle.build_csr(cfg["n"], cfg["src"], cfg["dst"], cfg["t"], sort="lexsort")
@@ -230,9 +244,10 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
 
 
 def config_dict(cfg, k, world):
-    return {"workload": "mid: Chung-Lu n=1M m=20M gamma=2.1 max_deg~1e5 30% multi-edges, bursty times over 1e8 s; "
-                        "motif a->b,b->c,c->d,a->d (path+chord), delta=3600, k=1e8 samples per step",
-            "n": int(cfg["n"]), "m": int(len(cfg["src"])), "motif": "path+chord", "delta": int(cfg["delta"]),
+    return {"workload": WORKLOADS[cfg["name"]],
+            "n": int(cfg["n"]), "m": int(len(cfg["src"])),
+            "motif": "path+chord" if cfg["motif"] == [(0, 1), (1, 2), (2, 3), (0, 3)] else "directed 4-cycle",
+            "delta": int(cfg["delta"]),
             "k": int(k), "seed": 0, "parallelism": "dp%d (sample-id ranges)" % world,
             "l2": "inputs larger than L2 (graph + index ~2.4 GB resident)"}
 
@@ -256,7 +271,7 @@ def main():
         torch.distributed.barrier()
     tc.lib()
 
-    cfg = workload()
+    cfg = workload(args.workload)
     k = args.samples or cfg["k"]
     n, m, delta = cfg["n"], len(cfg["src"]), cfg["delta"]
     stream = torch.cuda.current_stream()
@@ -328,12 +343,14 @@ def main():
     r0 = results[-1]
     # exact count by the exhaustive path sum (all W paths), for the relative error
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    ev[0].record(stream)
-    ex = tc.tc_exact_count(g, mot, delta, wts)
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    exact = {"C": ex["sum_x"], "paths": ex["k"], "ms": ev[0].elapsed_time(ev[1]),
-             "rel_error_plain": abs(r0["estimate"] - ex["sum_x"]) / max(ex["sum_x"], 1)}
+    exact = None
+    if r0["W"] <= args.exact_max_paths:
+        ev[0].record(stream)
+        ex = tc.tc_exact_count(g, mot, delta, wts)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        exact = {"C": ex["sum_x"], "paths": ex["k"], "ms": ev[0].elapsed_time(ev[1]),
+                 "rel_error_plain": abs(r0["estimate"] - ex["sum_x"]) / max(ex["sum_x"], 1)}
     merged = None
     if world > 1:  # the one exchange: exact integer sums of the last step over ranks
         from paper_2409_08975_gb300 import dist as tcdist
@@ -375,11 +392,11 @@ def main():
 
     learned = None if (args.no_learned or rank != 0) else learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
                                                               args.train_samples, stream)
-    if learned:
+    if learned and exact:
         learned["rel_error"] = abs(learned["estimate"] - exact["C"]) / max(exact["C"], 1)
 
     base = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.workload == "mid":
         base = cpu_baseline(cfg, k)[0]
 
     if world > 1:

@@ -74,6 +74,9 @@ def dense_tiny(seed=1011, n=24, m=20000, span=1_000_000, bursty=False):
             "delta": 10_000, "k": 100_000}
 
 
+ZIPF_CAP = 1000
+
+
 def _power_weights(n, gamma, i0):
     return (np.arange(n, dtype=np.float64) + i0) ** (-1.0 / (gamma - 1.0))
 
@@ -92,7 +95,7 @@ def _solve_i0(n, pairs, gamma, max_deg):
 
 
 def chung_lu(n, m, gamma=2.1, max_deg=1e5, multi_frac=0.30, span=100_000_000, pareto_alpha=1.5, seed=1002,
-             mean_burst_edges=200, burst_degree=(1.5, 24.0), daily=False):
+             mean_burst_edges=200, burst_degree=(1.5, 24.0), daily=False, zipf_repeats=None):
     """Directed power-law multigraph whose edges arrive in bursts.
 
     Bursts start at uniform times over the span (a Poisson process
@@ -106,9 +109,21 @@ def chung_lu(n, m, gamma=2.1, max_deg=1e5, multi_frac=0.30, span=100_000_000, pa
     A vertex's degree is then proportional to its weight, and edges close in
     time share vertices, as in transaction and communication networks.  A share
     multi_frac of all edges repeat an earlier edge's pair a Pareto gap later.
-    ``daily`` modulates burst starts by 1 + 0.5 sin(2 pi t / 86400)."""
+    ``daily`` modulates burst starts by 1 + 0.5 sin(2 pi t / 86400).
+    ``zipf_repeats = s`` replaces the uniform repeats: every pair of the
+    burst edges gets a total multiplicity drawn from Zipf(s) (truncated at
+    ZIPF_CAP), the repeats following the pair's first edge after Pareto gaps,
+    and the base edge count and top degree are scaled by the mean
+    multiplicity so that the total is m and the top degree about max_deg."""
     rng = np.random.default_rng(seed)
     base_m = int(round(m * (1.0 - multi_frac)))
+    base_max_deg = max_deg
+    if zipf_repeats:
+        j = np.arange(1, ZIPF_CAP + 1, dtype=np.float64)
+        p = j ** (-float(zipf_repeats))
+        mean_mult = float((j * p).sum() / p.sum())
+        base_m = int(m / mean_mult)
+        base_max_deg = max_deg / mean_mult  # the repeats multiply degrees
     sizes = rng.geometric(1.0 / mean_burst_edges, int(base_m / mean_burst_edges * 1.2) + 100)
     cs = np.cumsum(sizes)
     S = int(np.searchsorted(cs, base_m)) + 1
@@ -121,7 +136,7 @@ def chung_lu(n, m, gamma=2.1, max_deg=1e5, multi_frac=0.30, span=100_000_000, pa
         deg = np.exp(rng.uniform(np.log(lo), np.log(hi), S))
     nv = np.maximum(4, np.round(sizes / deg)).astype(np.int64)
     slots_total = int(nv.sum())
-    i0 = _solve_i0(n, base_m, gamma, max_deg)
+    i0 = _solve_i0(n, base_m, gamma, base_max_deg)
     w = _power_weights(n, gamma, i0)
     cdf = np.cumsum(w / w.sum())
     cdf[-1] = 1.0
@@ -153,8 +168,23 @@ def chung_lu(n, m, gamma=2.1, max_deg=1e5, multi_frac=0.30, span=100_000_000, pa
     cum = cum - cum[first][burst]
     t = np.minimum(start[burst] + cum, span - 1)
     extra = m - base_m
-    pick = rng.integers(0, base_m, extra)
-    rt = np.minimum(t[pick] + np.floor(rng.pareto(pareto_alpha, extra) + 1.0).astype(np.int64), span - 1)
+    if zipf_repeats:  # copies of pair i: Zipf(s) - 1 more, then trimmed to m in total
+        mult = np.minimum(rng.zipf(float(zipf_repeats), base_m), ZIPF_CAP) - 1
+        cum = np.cumsum(mult)
+        if cum[-1] < extra:  # top up uniformly (rare)
+            mult[rng.integers(0, base_m, extra - int(cum[-1]))] += 1
+            cum = np.cumsum(mult)
+        cut = int(np.searchsorted(cum, extra))
+        mult[cut] -= int(cum[cut] - extra)
+        mult[cut + 1:] = 0
+        pick = np.repeat(np.arange(base_m), mult)  # grouped by pair
+        gsum = np.cumsum(np.floor(rng.pareto(pareto_alpha, len(pick)) + 1.0).astype(np.int64))
+        first = np.repeat(np.cumsum(mult) - mult, mult)  # index of the pair's first repeat
+        offset = gsum - np.concatenate([[0], gsum])[first]  # Pareto gaps summed since the first edge
+        rt = np.minimum(t[pick] + offset, span - 1)
+    else:
+        pick = rng.integers(0, base_m, extra)
+        rt = np.minimum(t[pick] + np.floor(rng.pareto(pareto_alpha, extra) + 1.0).astype(np.int64), span - 1)
     src = np.concatenate([src, src[pick]]).astype(np.int32)
     dst = np.concatenate([dst, dst[pick]]).astype(np.int32)
     t = np.concatenate([t, rt]).astype(np.int64)
@@ -175,4 +205,20 @@ def scaled_mid(n, m, seed=1002, k=1_000_000):
     return g
 
 
-CONFIGS = {"tiny": tiny, "mid": mid}
+def learned(seed=1004):
+    """Learned-proposal configuration: the mid generator at n = 2e7, m = 1e8."""
+    g = chung_lu(20_000_000, 100_000_000, gamma=2.1, max_deg=5e5, multi_frac=0.30, seed=seed)
+    g.update({"name": "learned", "motif": PATH_CHORD, "delta": 3600, "k": 100_000_000})
+    return g
+
+
+def large(seed=1005):
+    """Large transaction-like graph: n = 1e8, m = 3e8, top degree ~1e6,
+    pair multiplicities Zipf(1.8), burst starts with daily periodicity."""
+    g = chung_lu(100_000_000, 300_000_000, gamma=2.1, max_deg=1e6, seed=seed, daily=True, zipf_repeats=1.8)
+    g.update({"name": "large", "motif": C4, "motifs": {"c4": C4, "path_chord": PATH_CHORD}, "delta": 3600,
+              "k": 1_000_000_000})
+    return g
+
+
+CONFIGS = {"tiny": tiny, "mid": mid, "learned": learned, "large": large}
