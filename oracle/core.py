@@ -81,6 +81,7 @@ class Plan:
         self.beta3 = -1 if e3 < mid else +1
         self.labels = labels  # motif labels of (u', u, v, v')
         self.closed = int(bool(closed))
+        self.kind = 0
         ranks = sorted((e1, mid, e3))
         self.gaps = [
             [f for f in range(ranks[0] + 1, ranks[1])],
@@ -90,12 +91,12 @@ class Plan:
 
     @property
     def cls(self):
-        s = {-1: "-", 1: "+"}
-        b = {-1: "<", 1: ">"}
+        s = {-1: "-", 1: "+", 0: "0"}
+        b = {-1: "<", 1: ">", 0: "0"}
         return (s[self.alpha1], s[self.alpha3], b[self.beta1], b[self.beta3])
 
     def array(self):
-        a = np.zeros(45, dtype=np.int32)
+        a = np.zeros(46, dtype=np.int32)
         a[0] = self.r
         for i, (x, y) in enumerate(self.edges):
             a[1 + i] = x
@@ -104,7 +105,40 @@ class Plan:
         a[36:40] = (self.alpha1, self.alpha3, self.beta1, self.beta3)
         a[40] = self.closed
         a[41:45] = self.labels
+        a[45] = self.kind
         return a
+
+
+class WedgePlan(Plan):
+    """Anchor of a 3-vertex motif (wedge sampling, Sec. "Brief Description of
+    Wedge Sampling"): the base is motif edge 0, the edge sampled in
+    proportion to its weight; the second edge is motif edge j, which shares
+    exactly one vertex s with the base and is later in time order, so it lies
+    in s's out-list (alpha = +1, the paper's <+,>> wedge when s is the base's
+    source) or in-list (alpha = -1) within (t, t + delta] of the base.  The
+    weight of a base edge is the size of that window.  kind 1: s is the
+    base's source (second edge stored as e1); kind 2: its destination (e3)."""
+
+    def __init__(self, edges, j, closed):
+        self.edges = [tuple(e) for e in edges]
+        self.r = len(edges)
+        A, B = self.edges[0]
+        x, y = self.edges[j]
+        shared = A if A in (x, y) else B
+        third = y if x == shared else x
+        alpha = +1 if x == shared else -1
+        self.kind = 1 if shared == A else 2
+        self.mid = 0
+        if self.kind == 1:
+            self.e1, self.e3 = j, -1
+            self.alpha1, self.beta1, self.alpha3, self.beta3 = alpha, +1, 0, 0
+            self.labels = (third, A, B, -1)
+        else:
+            self.e1, self.e3 = -1, j
+            self.alpha1, self.beta1, self.alpha3, self.beta3 = 0, 0, alpha, +1
+            self.labels = (-1, A, B, third)
+        self.closed = int(bool(closed))
+        self.gaps = [[f for f in range(1, j)], [f for f in range(j + 1, self.r)]]
 
 
 def anchor_candidates(edges):
@@ -130,21 +164,37 @@ def anchor_candidates(edges):
     return out
 
 
+def wedge_candidates(edges):
+    """Motif edges j > 0 that share exactly one vertex with edge 0."""
+    return [j for j in range(1, len(edges)) if len(set(edges[0]) & set(edges[j])) == 1]
+
+
 def compile_motif(edges, anchor=None, closed=False):
     """Anchor rule: among the candidate 3-paths containing edge 0, take the one
     whose sorted triple of ranks is lexicographically smallest (Alg. 5 leaves
     the choice open; any choice is unbiased by Claim 2).  ``anchor`` may force
-    (e1, mid, e3)."""
+    (e1, mid, e3).  A motif on three vertex labels gets a wedge anchor: edge 0
+    as the base and the smallest j whose edge shares one vertex with it
+    (forced as (j, 0, -1) or (-1, 0, j))."""
     edges = [tuple(int(v) for v in e) for e in edges]
-    if not 3 <= len(edges) <= 16:
-        raise ValueError("motif needs 3..16 edges")
     labs = set()
     for x, y in edges:
         if x == y or not (0 <= x < 4 and 0 <= y < 4):
             raise ValueError("motif edges join two distinct labels in 0..3")
         labs |= {x, y}
+    if len(labs) == 3:
+        if not 2 <= len(edges) <= 16:
+            raise ValueError("a 3-vertex motif needs 2..16 edges")
+        js = wedge_candidates(edges)
+        if anchor is not None:
+            js = [j for j in js if tuple(anchor) in ((j, 0, -1), (-1, 0, j))]
+        if not js:
+            raise ValueError("no wedge anchor containing edge 0")
+        return WedgePlan(edges, js[0], closed)
+    if not 3 <= len(edges) <= 16:
+        raise ValueError("motif needs 3..16 edges")
     if labs != {0, 1, 2, 3}:
-        raise ValueError("motif must use all four vertex labels")
+        raise ValueError("motif must use three or all four vertex labels")
     cands = anchor_candidates(edges)
     if anchor is not None:
         cands = [c for c in cands if (c[1], c[2], c[3]) == tuple(anchor)]
@@ -324,15 +374,20 @@ def brute_force_count(src, dst, t, edges, delta):
 
 def brute_force_paths(src, dst, t, plan, delta):
     """Literal Def. 4/5: all (e1, e2, e3) edge triples of the anchor's class,
-    per middle edge (input index).  Tiny graphs only."""
+    per middle edge (input index); for a wedge anchor, all second edges per
+    base edge.  Tiny graphs only."""
     m = len(src)
     per_mid = [0] * m
     for e2 in range(m):
         u, v, tm = int(src[e2]), int(dst[e2]), int(t[e2])
-        c1 = c3 = 0
+        # a wedge's unused end (alpha = 0) counts as one position
+        c1 = 1 if plan.alpha1 == 0 else 0
+        c3 = 1 if plan.alpha3 == 0 else 0
         for e in range(m):
             te = int(t[e])
             for alpha, beta, x, which in ((plan.alpha1, plan.beta1, u, 1), (plan.alpha3, plan.beta3, v, 3)):
+                if alpha == 0:
+                    continue
                 inc = (int(dst[e]) == x) if alpha < 0 else (int(src[e]) == x)
                 if not inc:
                     continue

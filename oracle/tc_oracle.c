@@ -172,6 +172,14 @@ typedef struct {
  *                  beta1, beta3   (-1 = before the middle edge, +1 = after)
  *   plan[40]       1 = closed windows (Claim 1 literally), 0 = strict
  *   plan[41..44]   motif vertex labels of u', u, v, v'
+ *   plan[45]       kind: 0 = 3-path anchor (4-vertex motif); 1 or 2 = wedge
+ *                  anchor (3-vertex motif, Sec. "Brief Description of Wedge
+ *                  Sampling"): the base is motif edge 0 (the sampled edge,
+ *                  stored as the middle) and the second edge shares the
+ *                  base's source (1; stored as e1 with alpha1, beta1 = +1,
+ *                  third vertex label in slot u') or its destination (2;
+ *                  stored as e3 with alpha3, beta3 = +1, label in slot v').
+ *                  The unused end has index -1, alpha = beta = 0, label -1.
  */
 typedef struct {
   int r;
@@ -180,6 +188,7 @@ typedef struct {
   int alpha1, alpha3, beta1, beta3;
   int closed;
   int lab[4];
+  int kind;
 } or_plan;
 
 static void read_plan(const int32_t *p, or_plan *pl) {
@@ -189,6 +198,7 @@ static void read_plan(const int32_t *p, or_plan *pl) {
   pl->alpha1 = p[36]; pl->alpha3 = p[37]; pl->beta1 = p[38]; pl->beta3 = p[39];
   pl->closed = p[40];
   for (int i = 0; i < 4; i++) pl->lab[i] = p[41 + i];
+  pl->kind = p[45];
 }
 
 /*
@@ -212,6 +222,35 @@ static void window_list(const or_graph *g, int alpha, int beta, int closed, int6
 }
 
 /*
+ * Wedge anchor: the window of the base edge e's shared vertex in which its
+ * second edge lies, (t, t + delta] strict or [t, t + delta] closed, taken
+ * from the shared vertex's out-list (alpha = +1) or in-list (-1).  The
+ * wedge weight is its size (for the paper's <+,>> wedge, d+_u[t, t+delta]).
+ * It is returned as [a, b) for a wedge at the base's source and [c, d) for
+ * one at its destination; the unused side is [0, 1).
+ */
+static void wedge_window(const or_graph *g, const or_plan *pl, int64_t e, int64_t delta,
+                         int64_t *a, int64_t *b, int64_t *c, int64_t *d) {
+  *a = 0; *b = 1; *c = 0; *d = 1;
+  if (pl->kind == 1)
+    window_list(g, pl->alpha1, pl->beta1, pl->closed, g->src[e], g->t[e], delta, a, b);
+  else
+    window_list(g, pl->alpha3, pl->beta3, pl->closed, g->dst[e], g->t[e], delta, c, d);
+}
+
+/* The anchor's windows around middle (base) edge e: the two end windows of
+ * a 3-path, or a wedge's window and the single dummy position [0, 1). */
+static void anchor_windows(const or_graph *g, const or_plan *pl, int64_t e, int64_t delta,
+                           int64_t *a, int64_t *b, int64_t *c, int64_t *d) {
+  if (pl->kind == 0) {
+    window_list(g, pl->alpha1, pl->beta1, pl->closed, g->src[e], g->t[e], delta, a, b);
+    window_list(g, pl->alpha3, pl->beta3, pl->closed, g->dst[e], g->t[e], delta, c, d);
+  } else {
+    wedge_window(g, pl, e, delta, a, b, c, d);
+  }
+}
+
+/*
  * Path weights (Claim 1, Alg. 1, one entry per edge in canonical order):
  *   w[i] = d^{alpha1}_u[window1(t)] * d^{alpha3}_v[window3(t)]
  * together with the list positions of both windows (used by Sample).
@@ -227,8 +266,8 @@ int or_path_weights(int64_t n, int64_t m, const int32_t *src, const int32_t *dst
   for (int64_t i = 0; i < m; i++) {
     int64_t e = out_perm[i];
     int64_t a, b, c, d;
-    window_list(&g, pl.alpha1, pl.beta1, pl.closed, src[e], t[e], delta, &a, &b);
-    window_list(&g, pl.alpha3, pl.beta3, pl.closed, dst[e], t[e], delta, &c, &d);
+    anchor_windows(&g, &pl, e, delta, &a, &b, &c, &d);
+    /* a wedge's unused window is [0, 1): w is the size of its one window */
     w[i] = (uint64_t)(b - a) * (uint64_t)(d - c);
     if (lo1) { lo1[i] = a; d1[i] = b - a; lo3[i] = c; d3[i] = d - c; }
   }
@@ -424,6 +463,65 @@ static uint64_t check_motif(const or_graph *g, const or_plan *pl, int64_t delta,
 }
 
 /*
+ * CheckMotif for a sampled wedge of a 3-vertex motif: base edge i2 (motif
+ * edge 0) and second edge at list position p of the shared vertex.  The
+ * three vertices must be distinct, the second edge strictly later than the
+ * base and within delta of it; the remaining motif edges fall in two gaps,
+ * ranks between the base and the second edge (times strictly between the
+ * two) and ranks after the second edge (times after it, up to t(base) +
+ * delta), and X is the product of the gaps' ListCounts.
+ */
+static uint64_t check_wedge(const or_graph *g, const or_plan *pl, int64_t delta, int64_t i2, int64_t p,
+                            int *ovf) {
+  int64_t e0 = g->out_perm[i2];
+  int at_src = pl->kind == 1;
+  int alpha = at_src ? pl->alpha1 : pl->alpha3;
+  int64_t e = edge_of_pos(g, alpha, p);
+  int64_t u = g->src[e0], v = g->dst[e0];
+  int64_t y = alpha < 0 ? g->src[e] : g->dst[e]; /* the end away from the shared vertex */
+  if (u == v || y == u || y == v) return 0;
+  int64_t phi[4];
+  phi[pl->lab[1]] = u;
+  phi[pl->lab[2]] = v;
+  phi[at_src ? pl->lab[0] : pl->lab[3]] = y;
+  int j = at_src ? pl->e1 : pl->e3;
+  int64_t t0 = g->t[e0], tj = g->t[e];
+  if (!(t0 < tj) || (uint64_t)tj - (uint64_t)t0 > (uint64_t)delta) return 0;
+  uint64_t X = 1;
+  for (int gap = 0; gap < 2; gap++) {
+    int64_t rlo = gap == 0 ? 0 : j, rhi = gap == 0 ? j : pl->r;
+    int64_t tlo = gap == 0 ? t0 : tj, thi = gap == 0 ? tj : sat_add(t0, delta);
+    const int64_t *lists[16];
+    int64_t lens[16];
+    int64_t *buf[16];
+    int l = 0;
+    for (int64_t f = rlo + 1; f < rhi; f++) {
+      int64_t a, b;
+      pair_window(g, phi[pl->msrc[f]], phi[pl->mdst[f]], tlo, thi, gap == 1, &a, &b);
+      buf[l] = (int64_t *)malloc(sizeof(int64_t) * (size_t)((b - a) ? (b - a) : 1));
+      for (int64_t q = a; q < b; q++) buf[l][q - a] = g->t[g->pair_perm[q]];
+      lists[l] = buf[l];
+      lens[l] = b - a;
+      l++;
+    }
+    uint64_t c = or_list_count(l, lists, lens, ovf);
+    for (int q = 0; q < l; q++) free(buf[q]);
+    u128 prod = (u128)X * c;
+    if (prod >> 64) *ovf = 1;
+    X = (uint64_t)prod;
+  }
+  return X;
+}
+
+/* CheckMotif of the anchor drawn at middle (base) edge i2 with end-edge list
+ * positions p1 and p3 (a wedge uses the one on its side). */
+static uint64_t anchor_check(const or_graph *g, const or_plan *pl, int64_t delta, int64_t i2, int64_t p1,
+                             int64_t p3, int *ovf) {
+  if (pl->kind == 0) return check_motif(g, pl, delta, i2, p1, p3, ovf);
+  return check_wedge(g, pl, delta, i2, pl->kind == 1 ? p1 : p3, ovf);
+}
+
+/*
  * Sample + CheckMotif for sample ids offset .. offset+k-1 (Alg. 2, Alg. 5's
  * loop).  prefix has m+1 entries (prefix[m] = W).  Optional trace[4*k]
  * receives (i2, p1, p3, X) per sample.  sums[0..4] = (sum X, sum X^2 low,
@@ -456,14 +554,14 @@ int or_sample_run(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, 
     }
     int64_t i2 = lo, e2 = out_perm[i2];
     int64_t a, b, c, d;
-    window_list(&g, pl.alpha1, pl.beta1, pl.closed, src[e2], t[e2], delta, &a, &b);
-    window_list(&g, pl.alpha3, pl.beta3, pl.closed, dst[e2], t[e2], delta, &c, &d);
+    anchor_windows(&g, &pl, e2, delta, &a, &b, &c, &d);
+    /* e1 by draw 1, e3 by draw 2; a wedge's unused end has range 1 (r = 0) */
     st = or_bounded(seed, s, 1, (uint64_t)(b - a), &r1);
     if (st) return st;
     st = or_bounded(seed, s, 2, (uint64_t)(d - c), &r3);
     if (st) return st;
     int64_t p1 = a + (int64_t)r1, p3 = c + (int64_t)r3;
-    uint64_t X = check_motif(&g, &pl, delta, i2, p1, p3, &ovf);
+    uint64_t X = anchor_check(&g, &pl, delta, i2, p1, p3, &ovf);
     if (trace) {
       trace[4 * i + 0] = (uint64_t)i2; trace[4 * i + 1] = (uint64_t)p1;
       trace[4 * i + 2] = (uint64_t)p3; trace[4 * i + 3] = X;
@@ -502,11 +600,10 @@ int or_path_sum(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, co
   for (int64_t i2 = 0; i2 < m; i2++) {
     int64_t e2 = out_perm[i2];
     int64_t a, b, c, d;
-    window_list(&g, pl.alpha1, pl.beta1, pl.closed, src[e2], t[e2], delta, &a, &b);
-    window_list(&g, pl.alpha3, pl.beta3, pl.closed, dst[e2], t[e2], delta, &c, &d);
+    anchor_windows(&g, &pl, e2, delta, &a, &b, &c, &d);
     for (int64_t p1 = a; p1 < b; p1++)
       for (int64_t p3 = c; p3 < d; p3++) {
-        uint64_t X = check_motif(&g, &pl, delta, i2, p1, p3, &ovf);
+        uint64_t X = anchor_check(&g, &pl, delta, i2, p1, p3, &ovf);
         sx += X;
         sx2 += (u128)X * X;
         paths++;
@@ -626,8 +723,7 @@ int or_edge_features(int64_t n, int64_t m, const int32_t *src, const int32_t *ds
     int64_t e = out_perm[i];
     int64_t u = src[e], v = dst[e], te = t[e];
     int64_t a, b, c, d;
-    window_list(&g, pl.alpha1, pl.beta1, pl.closed, u, te, delta, &a, &b);
-    window_list(&g, pl.alpha3, pl.beta3, pl.closed, v, te, delta, &c, &d);
+    anchor_windows(&g, &pl, e, delta, &a, &b, &c, &d);
     double *f = feat + 12 * i;
     int64_t lo = sat_sub(te, delta), hi = sat_add(te, delta);
     f[0] = (double)(b - a);
@@ -685,14 +781,14 @@ int or_sample_run_q(int64_t n, int64_t m, const int32_t *src, const int32_t *dst
     }
     int64_t i2 = lo, e2 = out_perm[i2];
     int64_t a, b, c, d;
-    window_list(&g, pl.alpha1, pl.beta1, pl.closed, src[e2], t[e2], delta, &a, &b);
-    window_list(&g, pl.alpha3, pl.beta3, pl.closed, dst[e2], t[e2], delta, &c, &d);
+    anchor_windows(&g, &pl, e2, delta, &a, &b, &c, &d);
+    /* e1 by draw 1, e3 by draw 2; a wedge's unused end has range 1 (r = 0) */
     st = or_bounded(seed, s, 1, (uint64_t)(b - a), &r1);
     if (st) return st;
     st = or_bounded(seed, s, 2, (uint64_t)(d - c), &r3);
     if (st) return st;
     int64_t p1 = a + (int64_t)r1, p3 = c + (int64_t)r3;
-    uint64_t X = check_motif(&g, &pl, delta, i2, p1, p3, &ovf);
+    uint64_t X = anchor_check(&g, &pl, delta, i2, p1, p3, &ovf);
     if (trace) {
       trace[4 * i + 0] = (uint64_t)i2; trace[4 * i + 1] = (uint64_t)p1;
       trace[4 * i + 2] = (uint64_t)p3; trace[4 * i + 3] = X;
@@ -729,15 +825,14 @@ int or_path_sum_q(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, 
   for (int64_t i2 = 0; i2 < m; i2++) {
     int64_t e2 = out_perm[i2];
     int64_t a, b, c, d;
-    window_list(&g, pl.alpha1, pl.beta1, pl.closed, src[e2], t[e2], delta, &a, &b);
-    window_list(&g, pl.alpha3, pl.beta3, pl.closed, dst[e2], t[e2], delta, &c, &d);
+    anchor_windows(&g, &pl, e2, delta, &a, &b, &c, &d);
     if (a == b || c == d) continue;
     uint32_t hv = h[i2];
     if (hv < h_lo || hv > h_hi) return OR_INVALID;
     uint64_t *bin = acc + 3 * (hv - h_lo);
     for (int64_t p1 = a; p1 < b; p1++)
       for (int64_t p3 = c; p3 < d; p3++) {
-        uint64_t X = check_motif(&g, &pl, delta, i2, p1, p3, &ovf);
+        uint64_t X = anchor_check(&g, &pl, delta, i2, p1, p3, &ovf);
         bin[0] += X;
         u128 x2 = ((u128)bin[2] << 64 | bin[1]) + (u128)X * X;
         bin[1] = (uint64_t)x2; bin[2] = (uint64_t)(x2 >> 64);
