@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--train-samples", type=int, default=10_000_000)
-    ap.add_argument("--workload", default="mid", choices=["mid", "learned", "large"],
+    ap.add_argument("--workload", default="mid", choices=["mid", "learned", "large", "batch"],
                     help="mid: the 20M-edge graph (default); learned: n=2e7, m=1e8; large: n=1e8, m=3e8")
     return ap.parse_args()
 
@@ -138,6 +138,10 @@ WORKLOADS = {
                "learned proposal trained on 1e7 plain samples",
     "large": "large: n=100M m=300M, top degree ~1e6, pair multiplicities Zipf(1.8), daily periodicity over 1e8 s; "
              "directed 4-cycle (M4-0), delta=3600, k=1e9 samples per step",
+    "batch": "batch: 136 queries in one persistent launch replayed from a CUDA graph; a 50M-edge graph of the mid "
+             "generator (n=2.5M) with all 24 time-rank orders of the directed 4-cycle x delta in {600, 3600, 86400}, "
+             "plus 64 graphs of 1e4-2e6 edges (log-uniform) with one query each; 1e6-1e8 samples per query "
+             "(log-uniform), ~2.5e9 samples per step",
 }
 
 
@@ -168,6 +172,9 @@ def run_reference(args, rank, world):
         return
     cfg = workload(args.workload)
     k = args.samples or cfg["k"]
+    if args.workload == "batch":  # the oracle on the big graph's first query, scaled to all samples
+        gi, edges, delta = cfg["queries"][0][:3]
+        cfg = dict(cfg["graphs"][gi], name="batch", motif=edges, delta=delta)
     import oracle
     og = oracle.build_csr(cfg["n"], cfg["src"], cfg["dst"], cfg["t"], sort="lexsort")
     plan = oracle.compile_motif(cfg["motif"])
@@ -244,12 +251,127 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
 
 
 def config_dict(cfg, k, world):
+    if cfg["name"] == "batch":
+        return {"workload": WORKLOADS["batch"], "k": int(k), "seed": 0,
+                "parallelism": "dp%d (sample-id ranges)" % world,
+                "reference_sample": "oracle on the 50M-edge graph, first query (4-cycle, delta=600)"}
     return {"workload": WORKLOADS[cfg["name"]],
             "n": int(cfg["n"]), "m": int(len(cfg["src"])),
             "motif": "path+chord" if cfg["motif"] == [(0, 1), (1, 2), (2, 3), (0, 3)] else "directed 4-cycle",
             "delta": int(cfg["delta"]),
             "k": int(k), "seed": 0, "parallelism": "dp%d (sample-id ranges)" % world,
             "l2": "inputs larger than L2 (graph + index ~2.4 GB resident)"}
+
+
+def run_batch(args, rank, world, local):
+    """The batched-query workload: every step is one tc_batch_run (weights
+    per distinct key, key sorts, one persistent sampling launch)."""
+    import torch
+    from paper_2409_08975_gb300 import tc
+    cfg = workload("batch")
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dev = [(torch.from_numpy(g["src"]).cuda(), torch.from_numpy(g["dst"]).cuda(), torch.from_numpy(g["t"]).cuda())
+           for g in cfg["graphs"]]
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    graphs = [tc.tc_build_temporal_csr(g["n"], *d) for g, d in zip(cfg["graphs"], dev)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    csr_ms = ev0.elapsed_time(ev1)
+    del dev
+    # rank r answers every query over its own sample-id range
+    queries = [(graphs[gi], edges, delta, k, seed, rank * k) for gi, edges, delta, k, seed, _ in cfg["queries"]]
+    k_total = sum(q[3] for q in queries)
+    t0 = time.perf_counter()
+    b = tc.Batch(queries)
+    create_s = time.perf_counter() - t0
+    info = b.info()
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = tc.tc_kernel_launches()
+    samp = []
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(args.steps):
+        res = b.run()
+        samp.append(b.timing()[1])
+    end.record(stream)
+    torch.cuda.synchronize()
+    launches = tc.tc_kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * k_total / (ms_per_step / 1e3)
+    sampler_ms = statistics.median(samp)
+    checked = sum(r["checked"] for r in res)
+    bytes_per_sample = SECTOR * (5 + 4 * checked / k_total)
+    peak, peak_kind = load_peaks()
+    achieved = bytes_per_sample * k_total / (sampler_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_sample_batch (persistent sampler over all queries, Alg. 2-4)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_kind": peak_kind, "bytes_per_sample": bytes_per_sample, "sampler_ms": sampler_ms}
+    b.destroy()
+    # end to end: host edge arrays -> device, graph builds, batch creation with
+    # the tuned shape (no CUDA graph), one run, results to the host
+    pinned = [(torch.from_numpy(g["src"]).pin_memory(), torch.from_numpy(g["dst"]).pin_memory(),
+               torch.from_numpy(g["t"]).pin_memory()) for g in cfg["graphs"]]
+    m_total = sum(len(g["src"]) for g in cfg["graphs"])
+    e2e_times = []
+    for i in range(1 + args.e2e_steps if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gs = []
+        for g, (s_h, d_h, t_h) in zip(cfg["graphs"], pinned):
+            d = (s_h.to("cuda", non_blocking=True), d_h.to("cuda", non_blocking=True),
+                 t_h.to("cuda", non_blocking=True))
+            gs.append(tc.tc_build_temporal_csr(g["n"], *d))
+        qs = [(gs[gi], edges, delta, k, seed, rank * k) for gi, edges, delta, k, seed, _ in cfg["queries"]]
+        bb = tc.Batch(qs, block_size=info["block_size"], tile=info["tile"], use_graph=False)
+        bb.run()
+        bb.destroy()
+        for g in gs:
+            g.destroy()
+        dt = time.perf_counter() - t0
+        if i > 0:
+            e2e_times.append(dt)
+    e2e = None
+    if e2e_times:
+        e2e_s = statistics.mean(e2e_times)
+        # device->host per graph build 24 B; per query the sums (56 B); per
+        # weights key W (8 B) and its error word (4 B)
+        d2h = 24 * len(cfg["graphs"]) + 56 * len(queries) + 12 * info["weight_slots"]
+        e2e = {"value": world * k_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * m_total,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch"], "queries": len(queries), "graphs": len(graphs),
+                       "m_total": int(m_total), "k": int(k_total), "seed": 0,
+                       "parallelism": "dp%d (sample-id ranges)" % world,
+                       "l2": "inputs larger than L2 (big graph + 12 weight indexes ~30 GB resident)"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": None,
+            "csr_build_ms": csr_ms, "batch": dict(info, create_s=create_s, sampling_ms_median=sampler_ms),
+            "estimates": [{"W": r["W"], "k": r["k"], "estimate": r["estimate"], "std_err": r["std_err"]}
+                          for r in res[:8]],
+        }))
+    for g in graphs:
+        g.destroy()
 
 
 def main():
@@ -270,6 +392,11 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     tc.lib()
+    if args.workload == "batch":
+        run_batch(args, rank, world, local)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
 
     cfg = workload(args.workload)
     k = args.samples or cfg["k"]

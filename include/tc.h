@@ -67,15 +67,26 @@ typedef struct tc_graph tc_graph;
 
 /*
  * Temporal motif M = (H, pi, delta) without delta (Def. 1).  Edge i of H runs
- * from vertex label src[i] to dst[i] (labels 0..3, all four used, no
- * self-loops) and has time rank i: the permutation pi is the identity on the
- * listed order.  anchor = {e1, middle, e3} motif edge indices forces the
- * anchor 3-path (it must contain edge 0); {-1,-1,-1} selects it by the rule
- * of Alg. 5: among the 3-paths over the four vertices that contain edge 0,
- * the one whose sorted triple of ranks is lexicographically smallest.
+ * from vertex label src[i] to dst[i] (labels 0..3, no self-loops) and has
+ * time rank i: the permutation pi is the identity on the listed order.
+ *
+ * Four labels used (3..16 edges): the anchor is a 3-path.  anchor = {e1,
+ * middle, e3} motif edge indices forces it (it must contain edge 0);
+ * {-1,-1,-1} selects it by the rule of Alg. 5: among the 3-paths over the
+ * four vertices that contain edge 0, the one whose sorted triple of ranks is
+ * lexicographically smallest.
+ *
+ * Three labels used (2..16 edges): the anchor is a wedge (wedge sampling for
+ * 3-vertex motifs): the base is edge 0, sampled with weight equal to the
+ * number of possible second edges, and the second edge is the motif edge j
+ * that shares one vertex s with the base, drawn uniformly from s's out-list
+ * (if edge j leaves s; for s the base's source this is the paper's <+,>>
+ * wedge) or in-list within (t, t + delta] of the base (closed: [t, t +
+ * delta]).  {-1,-1,-1} takes the smallest such j; {j, 0, -1} (s the base's
+ * source) or {-1, 0, j} (s its destination) forces one.
  */
 typedef struct {
-  int32_t num_edges;                 /* 3 .. TC_MAX_MOTIF_EDGES */
+  int32_t num_edges;                 /* 2 or 3 .. TC_MAX_MOTIF_EDGES */
   int8_t src[TC_MAX_MOTIF_EDGES];
   int8_t dst[TC_MAX_MOTIF_EDGES];
   int32_t anchor[3];
@@ -90,8 +101,9 @@ typedef struct {
   uint64_t sum_x2_lo;  /* sum of X^2, low 64 bits */
   uint64_t sum_x2_hi;  /* sum of X^2, high 64 bits */
   uint64_t hits;       /* samples with X > 0 */
-  uint64_t checked;    /* samples whose path spans four vertices with the anchor's
-                          time order and span <= delta (reached the list lookups) */
+  uint64_t checked;    /* samples whose path (wedge) spans four (three) vertices with
+                          the anchor's time order and span <= delta (reached the
+                          list lookups) */
   double estimate;     /* C_hat = sum_x * W / k (exact integer division, then FP64) */
   double std_err;      /* W * sqrt(s^2 / k), s^2 the unbiased sample variance of X */
 } tc_estimate;
@@ -345,6 +357,68 @@ tc_status tc_sample_estimate_q(const tc_graph* g, const tc_motif* motif, int64_t
                                const uint16_t* d_h, const uint64_t* d_qprefix, const void* d_qindex,
                                uint64_t k, uint64_t seed, uint64_t sample_offset, tc_estimate* h_out,
                                uint64_t* h_bins, uint64_t* d_trace, void* stream);
+
+/*
+ * Batched queries.  A batch is a fixed list of queries, each a motif and
+ * window on a built graph with k samples (sample ids sample_offset ..
+ * sample_offset + k - 1 of seed), answered together: every run recomputes
+ * the path weights, prefix and index once per distinct (graph, anchor class,
+ * window kind, delta), puts every query's samples in key order, and samples
+ * all queries in one persistent launch whose blocks take (query, tile) work
+ * items from a counter.  With use_graph, that whole sequence is captured
+ * once into a CUDA graph at creation and each run replays it.  The sums of
+ * each query are bit-identical to tc_sample_estimate on the same query (the
+ * samples are keyed by id and the sums are integers).
+ *
+ * Graphs are borrowed: they must outlive the batch.  The batch owns device
+ * memory for each distinct weights key (prefix and index, 8 (m + 1) plus
+ * tc_sample_index_bytes) and 4 k bytes of sample order per query with
+ * k >= 65536; k may be at most 2^40.
+ */
+typedef struct {
+  const tc_graph* graph;
+  tc_motif motif;
+  int64_t delta;
+  uint64_t k, seed, sample_offset;
+} tc_query;
+
+typedef struct {
+  int32_t block_size; /* threads per block of the batch launch: 128, 256 or 512; 0 = autotune */
+  uint32_t tile;      /* samples per work item, a multiple of block_size; 0 = autotune */
+  int32_t use_graph;  /* nonzero: capture one CUDA graph at creation and replay it */
+  int32_t reserved;
+} tc_batch_options;
+
+typedef struct tc_batch tc_batch;
+
+/* Validates the queries (as tc_sample_estimate would), allocates the batch's
+ * memory and, when block_size or tile is 0, times every candidate
+ * (block size 128/256/512 x tile 2048/8192/32768) on one full run and keeps
+ * the fastest.  opts may be NULL (autotune, use_graph = 1).  Synchronises
+ * stream.  Errors: TC_ERR_INVALID_ARG for a NULL or bad argument,
+ * TC_ERR_UNSUPPORTED_MOTIF, TC_ERR_OOM, TC_ERR_CUDA. */
+tc_status tc_batch_create(const tc_query* h_queries, int64_t nq, const tc_batch_options* opts, void* stream,
+                          tc_batch** out);
+
+/* One run: h_out[nq] receives every query's estimate (as
+ * tc_sample_estimate).  Synchronises stream.  A query whose weights
+ * overflow or whose samples hit a device error makes the call return that
+ * status; h_out is still filled for the others. */
+tc_status tc_batch_run(tc_batch* b, tc_estimate* h_out, void* stream);
+
+/* The batch's chosen launch shape, the kernels one run launches, the
+ * device bytes the batch holds and its number of distinct weights keys
+ * (any pointer may be NULL). */
+tc_status tc_batch_info(const tc_batch* b, tc_batch_options* h_opts, uint64_t* h_launches_per_run,
+                        uint64_t* h_device_bytes, uint64_t* h_weight_slots);
+
+/* Device time of the last completed run, from CUDA events recorded inside
+ * the sequence: the whole run (weights, key sorts, sampling) and the
+ * persistent sampling launch alone, in milliseconds.  Call after
+ * tc_batch_run has returned. */
+tc_status tc_batch_timing(const tc_batch* b, float* h_run_ms, float* h_sampling_ms);
+
+tc_status tc_batch_destroy(tc_batch* b);
 
 /* Number of kernels this library has launched in this process so far
  * (a diagnostic for counting launches around a region). */

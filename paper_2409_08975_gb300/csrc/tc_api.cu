@@ -75,10 +75,76 @@ tc_status device_status(uint32_t bits, const char* what) {
 // Anchor rule (Alg. 5): the 3-path over the four vertices that contains
 // edge 0 and whose sorted ranks are lexicographically smallest; its class
 // <alpha1, alpha3, beta1, beta3> (Def. 5); the non-anchor edges per gap.
+// Wedge anchor of a 3-vertex motif: base = edge 0, second edge = the
+// smallest j sharing exactly one vertex with it (or the forced one).
+static tc_status compile_wedge(const tc_motif* M, Plan* P, std::string* why) {
+  const int r = M->num_edges;
+  const bool forced = !(M->anchor[0] == -1 && M->anchor[1] == -1 && M->anchor[2] == -1);
+  const int A = M->src[0], B = M->dst[0];
+  int best = -1;
+  for (int j = 1; j < r && best < 0; j++) {
+    const int x = M->src[j], y = M->dst[j];
+    const int shared = (x == A || y == A) + (x == B || y == B);
+    if (shared != 1) continue;
+    const bool at_src = x == A || y == A;
+    if (forced && !(at_src ? (M->anchor[0] == j && M->anchor[1] == 0 && M->anchor[2] == -1)
+                           : (M->anchor[0] == -1 && M->anchor[1] == 0 && M->anchor[2] == j)))
+      continue;
+    best = j;
+  }
+  if (best < 0) {
+    *why = forced ? "forced anchor is not a wedge on edge 0" : "motif has no wedge that contains edge 0";
+    return TC_ERR_UNSUPPORTED_MOTIF;
+  }
+  const int x = M->src[best], y = M->dst[best];
+  const bool at_src = x == A || y == A;
+  const int s = at_src ? A : B;
+  const int third = x == s ? y : x;
+  const int alpha = x == s ? +1 : -1;  // the second edge leaves s: out-list
+  std::memset(P, 0, sizeof(*P));
+  P->r = r;
+  P->mid = 0;
+  P->closed = M->window == TC_WINDOW_CLOSED;
+  P->wedge = at_src ? 1 : 2;
+  P->lab[1] = A;
+  P->lab[2] = B;
+  if (at_src) {
+    P->e1 = best;
+    P->e3 = -1;
+    P->alpha1 = alpha;
+    P->beta1 = +1;
+    P->lab[0] = third;
+    P->lab[3] = -1;
+  } else {
+    P->e1 = -1;
+    P->e3 = best;
+    P->alpha3 = alpha;
+    P->beta3 = +1;
+    P->lab[0] = -1;
+    P->lab[3] = third;
+  }
+  P->rk[0] = 0;
+  P->rk[1] = best;
+  P->rk[2] = r;
+  int role[4] = {-1, -1, -1, -1};  // label -> position in (u', u, v, v')
+  role[A] = 1;
+  role[B] = 2;
+  role[third] = at_src ? 0 : 3;
+  for (int gp = 0; gp < 2; gp++) {
+    const int lo = gp == 0 ? 0 : best, hi = gp == 0 ? best : r;
+    for (int f = lo + 1; f < hi; f++) {
+      P->gx[gp][P->ngap[gp]] = (int8_t)role[M->src[f]];
+      P->gy[gp][P->ngap[gp]] = (int8_t)role[M->dst[f]];
+      P->ngap[gp]++;
+    }
+  }
+  return TC_OK;
+}
+
 tc_status compile_plan(const tc_motif* M, Plan* P, std::string* why) {
   const int r = M->num_edges;
-  if (r < 3 || r > TC_MAX_MOTIF_EDGES) {
-    *why = "motif needs 3..16 edges";
+  if (r < 2 || r > TC_MAX_MOTIF_EDGES) {
+    *why = "motif needs 2..16 edges (3..16 on four vertices)";
     return TC_ERR_INVALID_ARG;
   }
   if (M->window != TC_WINDOW_STRICT && M->window != TC_WINDOW_CLOSED) {
@@ -94,8 +160,10 @@ tc_status compile_plan(const tc_motif* M, Plan* P, std::string* why) {
     }
     used |= (1 << x) | (1 << y);
   }
-  if (used != 0xF) {
-    *why = "motif must use all four vertex labels";
+  const int nlab = __builtin_popcount((unsigned)used);
+  if (nlab == 3) return compile_wedge(M, P, why);
+  if (nlab != 4 || r < 3) {
+    *why = "motif must use three vertex labels (2..16 edges) or four (3..16 edges)";
     return TC_ERR_INVALID_ARG;
   }
   const bool forced = !(M->anchor[0] == -1 && M->anchor[1] == -1 && M->anchor[2] == -1);
@@ -181,6 +249,8 @@ static tc_status plan_of(const tc_motif* motif, Plan* p) {
   return TC_OK;
 }
 
+tc_status compile_plan_checked(const tc_motif* motif, Plan* p) { return plan_of(motif, p); }
+
 static void free_graph_arrays(tc_graph* g) {
   void* ps[] = {g->out_off, g->out_e, g->perm, g->in_off, g->in_e, g->in_eid, g->pair_off,
                 g->pair_dst, g->pair_eoff, g->pair_t, g->pair_eid, g->pair_hash};
@@ -190,7 +260,7 @@ static void free_graph_arrays(tc_graph* g) {
 
 // Host form of C_hat = sum_x * W / k (Alg. 5): exact 128-bit product and
 // division, then q + r / k in FP64; standard error W * sqrt(s^2 / k).
-static void finish_estimate(tc_estimate* o) {
+void finish_estimate(tc_estimate* o) {
   o->estimate = 0.0;
   o->std_err = 0.0;
   if (o->k == 0 || o->W == 0) return;

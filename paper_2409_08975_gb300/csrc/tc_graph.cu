@@ -192,31 +192,42 @@ uint64_t scan_u64_scratch_words(uint64_t n) {
 }
 
 // The same reduce-then-scan as scan_rec, with the tile sums of every level
-// placed in caller scratch (scan_u64_scratch_words(n) words) instead of
+// placed in caller scratch (scan_u64_scratch_words(n) elements) instead of
 // stream-ordered allocations.
-tc_status scan_u64_in_scratch(const uint64_t* in, uint64_t* out, uint64_t n, bool write_total, uint32_t* d_err,
-                              uint64_t* scratch, uint64_t scratch_words, cudaStream_t st) {
+template <class T>
+static tc_status scan_in_scratch(const T* in, T* out, uint64_t n, bool write_total, uint32_t* d_err, T* scratch,
+                                 uint64_t scratch_words, cudaStream_t st) {
   if (n == 0) {
-    if (write_total) TC_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
+    if (write_total) TC_CUDA(cudaMemsetAsync(out, 0, sizeof(T), st));
     return TC_OK;
   }
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles == 1) {
-    k_tile_scan<uint64_t><<<1, kScanThreads, 0, st>>>(in, n, nullptr, out, write_total, d_err);
+    k_tile_scan<T><<<1, kScanThreads, 0, st>>>(in, n, nullptr, out, write_total, d_err);
     TC_LAUNCHED(1);
     TC_CUDA(cudaGetLastError());
     return TC_OK;
   }
   if (scratch_words < tiles) return set_error(TC_ERR_INVALID_ARG, "scan scratch too small");
-  uint64_t* sums = scratch;
-  k_tile_reduce<uint64_t><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums, d_err);
+  T* sums = scratch;
+  k_tile_reduce<T><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums, d_err);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
-  TC_TRY(scan_u64_in_scratch(sums, sums, tiles, false, d_err, scratch + tiles, scratch_words - tiles, st));
-  k_tile_scan<uint64_t><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums, out, write_total, d_err);
+  TC_TRY(scan_in_scratch<T>(sums, sums, tiles, false, d_err, scratch + tiles, scratch_words - tiles, st));
+  k_tile_scan<T><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums, out, write_total, d_err);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
+}
+
+tc_status scan_u64_in_scratch(const uint64_t* in, uint64_t* out, uint64_t n, bool write_total, uint32_t* d_err,
+                              uint64_t* scratch, uint64_t scratch_words, cudaStream_t st) {
+  return scan_in_scratch<uint64_t>(in, out, n, write_total, d_err, scratch, scratch_words, st);
+}
+
+tc_status scan_u32_in_scratch(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* scratch,
+                              uint64_t scratch_words, cudaStream_t st) {
+  return scan_in_scratch<uint32_t>(in, out, n, true, nullptr, scratch, scratch_words, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -85,12 +85,19 @@ enum : uint32_t {
 // ---------------------------------------------------------------------------
 // Compiled motif: anchor, class and the non-anchor edges grouped by gap.
 
+// A 3-vertex motif has a wedge anchor (wedge != 0): the base edge (motif
+// edge 0) is stored as the middle edge and the second edge as e1 (wedge 1:
+// it shares the base's source u) or e3 (wedge 2: it shares the base's
+// destination v), with beta = +1; the unused end has index -1, alpha = beta
+// = 0 (a dummy window of one position) and label -1.  Gaps: ranks between
+// the base and the second edge, and after the second edge.
 struct Plan {
   int32_t r;                 // motif edges
   int32_t e1, mid, e3;       // anchor motif edge indices (= time ranks)
-  int32_t alpha1, alpha3;    // -1 in-list, +1 out-list
+  int32_t alpha1, alpha3;    // -1 in-list, +1 out-list, 0 none (wedge)
   int32_t beta1, beta3;      // -1 before the middle edge, +1 after
   int32_t closed;            // 1: closed windows
+  int32_t wedge;             // 0: 3-path anchor; 1 or 2: wedge anchor
   int32_t lab[4];            // motif labels of u', u, v, v'
   int32_t rk[3];             // anchor ranks sorted ascending (rk[0] = 0)
   int32_t ngap[3];           // non-anchor lists per gap
@@ -269,7 +276,9 @@ __device__ __forceinline__ void window_range(const OutEdge* __restrict__ out_e,
 // not overlap unless in == out.
 tc_status scan_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint32_t* d_err, cudaStream_t st);
 tc_status scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, cudaStream_t st);
-uint64_t scan_u64_scratch_words(uint64_t n);
+uint64_t scan_u64_scratch_words(uint64_t n);  // also the element count for u32 scans
+tc_status scan_u32_in_scratch(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* scratch,
+                              uint64_t scratch_words, cudaStream_t st);
 tc_status scan_u64_in_scratch(const uint64_t* in, uint64_t* out, uint64_t n, bool write_total, uint32_t* d_err,
                               uint64_t* scratch, uint64_t scratch_words, cudaStream_t st);
 
@@ -321,5 +330,32 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
                          const void* index, uint64_t k, uint64_t seed, uint64_t offset, uint64_t* trace,
                          SampleSums* d_sums, cudaStream_t st, const void* qindex = nullptr,
                          const uint16_t* h = nullptr, unsigned long long* bins = nullptr);
+
+// Key-ordered sampling: samples are processed in chunks of at most
+// kChunkSamples, each put in key order by sort_sample_ids (no allocation;
+// scratch of sort_scratch_bytes(count)); calls below kSortedMinSamples
+// samples run in id order.
+constexpr uint64_t kSortedMinSamples = 1ull << 16;
+constexpr uint64_t kChunkSamples = 1ull << 28;
+size_t sort_scratch_bytes(uint64_t count);
+tc_status sort_sample_ids(const IndexHeader* hdr, uint64_t seed, uint64_t first, uint64_t count, void* scratch,
+                          uint32_t* order, cudaStream_t st);
+
+// Batched sampling: each query's arguments are a kBatchQueryBytes-byte
+// record in device memory, written on the host by batch_query_record; the
+// queries' work items (tiles of `tile` samples) are numbered query after
+// query, query q owning items [tile_begin[q], tile_begin[q + 1]).  order is
+// the query's key order (chunk after chunk) or NULL for id order.
+constexpr size_t kBatchQueryBytes = 512;
+void batch_query_record(void* h_rec, const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
+                        const void* index, uint64_t k, uint64_t seed, uint64_t offset, const uint32_t* order);
+int sample_batch_blocks_per_sm(int block_size);  // 0: unsupported block size
+tc_status launch_sample_batch(int block_size, uint32_t tile, unsigned blocks, const void* d_records,
+                              const uint64_t* d_tile_begin, uint32_t nq, unsigned long long* d_next_item,
+                              SampleSums* d_sums, cudaStream_t st);
+
+// Host form of the estimate from the sums (tc_api.cu).
+void finish_estimate(tc_estimate* o);
+tc_status compile_plan_checked(const tc_motif* motif, Plan* p);
 
 }  // namespace tc

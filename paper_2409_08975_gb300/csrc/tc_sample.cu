@@ -18,6 +18,15 @@ namespace tc {
 //          its (lo3, d3) is parked in w at the edge's canonical position;
 //   pass 2 runs over the canonical order (edges grouped by u), finds u's
 //          window, writes the sampler record and w_e.
+// A wedge anchor (3-vertex motif) has one window, at u or at v; the other
+// side is the dummy [0, 1), so w_e is the size of that window, and pass 1 is
+// skipped when the window is at u.
+
+// Edges per thread of the weight kernels, processed together so that the
+// loads of their independent searches overlap.
+#ifndef TC_WEIGHTS_ILP
+#define TC_WEIGHTS_ILP 2
+#endif
 
 __global__ void __launch_bounds__(256) k_weights_dst(const OutEdge* __restrict__ out_e,
                                                      const uint32_t* __restrict__ out_off,
@@ -26,12 +35,26 @@ __global__ void __launch_bounds__(256) k_weights_dst(const OutEdge* __restrict__
                                                      const uint32_t* __restrict__ in_eid, uint64_t m, Plan plan,
                                                      int64_t delta, uint64_t* __restrict__ w) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += stride) {
-    const InEdge e = in_e[p];
-    uint32_t lo3, hi3;
-    window_range(out_e, out_off, in_e, in_off, plan.alpha3, plan.beta3, plan.closed, e.dst, e.t, delta, &lo3,
-                 &hi3);
-    w[in_eid[p]] = (uint64_t)lo3 | ((uint64_t)(hi3 - lo3) << 32);
+  for (uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < m; p0 += stride * TC_WEIGHTS_ILP) {
+    InEdge e[TC_WEIGHTS_ILP];
+    uint32_t lo3[TC_WEIGHTS_ILP], hi3[TC_WEIGHTS_ILP];
+#pragma unroll
+    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
+      const uint64_t p = p0 + j * stride;
+      if (p < m) e[j] = in_e[p];
+    }
+#pragma unroll
+    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
+      const uint64_t p = p0 + j * stride;
+      if (p < m)
+        window_range(out_e, out_off, in_e, in_off, plan.alpha3, plan.beta3, plan.closed, e[j].dst, e[j].t, delta,
+                     &lo3[j], &hi3[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
+      const uint64_t p = p0 + j * stride;
+      if (p < m) w[in_eid[p]] = (uint64_t)lo3[j] | ((uint64_t)(hi3[j] - lo3[j]) << 32);
+    }
   }
 }
 
@@ -42,22 +65,39 @@ __global__ void __launch_bounds__(256) k_weights_src(const OutEdge* __restrict__
                                                      int64_t delta, EdgeRec* __restrict__ rec,
                                                      uint64_t* __restrict__ w) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-    const OutEdge e = out_e[i];
-    uint32_t lo1, hi1;
-    window_range(out_e, out_off, in_e, in_off, plan.alpha1, plan.beta1, plan.closed, e.src, e.t, delta, &lo1,
-                 &hi1);
-    const uint64_t parked = w[i];
-    EdgeRec r;
-    r.u = e.src;
-    r.v = e.dst;
-    r.t = e.t;
-    r.lo1 = lo1;
-    r.d1 = hi1 - lo1;
-    r.lo3 = (uint32_t)parked;
-    r.d3 = (uint32_t)(parked >> 32);
-    rec[i] = r;
-    w[i] = (uint64_t)r.d1 * (uint64_t)r.d3;
+  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += stride * TC_WEIGHTS_ILP) {
+    OutEdge e[TC_WEIGHTS_ILP];
+    uint32_t lo1[TC_WEIGHTS_ILP], hi1[TC_WEIGHTS_ILP];
+#pragma unroll
+    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
+      const uint64_t i = i0 + j * stride;
+      if (i < m) e[j] = out_e[i];
+    }
+#pragma unroll
+    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
+      const uint64_t i = i0 + j * stride;
+      lo1[j] = 0;  // a wedge at v: the u side is the one-position dummy
+      hi1[j] = 1;
+      if (i < m && plan.alpha1 != 0)
+        window_range(out_e, out_off, in_e, in_off, plan.alpha1, plan.beta1, plan.closed, e[j].src, e[j].t, delta,
+                     &lo1[j], &hi1[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
+      const uint64_t i = i0 + j * stride;
+      if (i >= m) continue;
+      const uint64_t parked = plan.alpha3 != 0 ? w[i] : (1ull << 32);  // v side [0, 1) for a wedge at u
+      EdgeRec r;
+      r.u = e[j].src;
+      r.v = e[j].dst;
+      r.t = e[j].t;
+      r.lo1 = lo1[j];
+      r.d1 = hi1[j] - lo1[j];
+      r.lo3 = (uint32_t)parked;
+      r.d3 = (uint32_t)(parked >> 32);
+      rec[i] = r;
+      w[i] = (uint64_t)r.d1 * (uint64_t)r.d3;
+    }
   }
 }
 
@@ -65,10 +105,12 @@ tc_status launch_weights(const tc_graph* g, const Plan& plan, int64_t delta, Edg
                          cudaStream_t st) {
   const uint64_t m = (uint64_t)g->m;
   if (m == 0) return TC_OK;
-  const unsigned blocks = (unsigned)((m + 255) / 256);
-  k_weights_dst<<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->in_eid, m, plan, delta, w);
-  TC_LAUNCHED(1);
-  TC_CUDA(cudaGetLastError());
+  const unsigned blocks = (unsigned)((m + 256 * TC_WEIGHTS_ILP - 1) / (256 * TC_WEIGHTS_ILP));
+  if (plan.alpha3 != 0) {  // a wedge at u has no v-side window
+    k_weights_dst<<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->in_eid, m, plan, delta, w);
+    TC_LAUNCHED(1);
+    TC_CUDA(cudaGetLastError());
+  }
   k_weights_src<<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, m, plan, delta, rec, w);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
@@ -309,30 +351,22 @@ __device__ __noinline__ uint64_t gap_count_multi(const SamplerArgs& A, const Pla
   return list_count_merge(A.pair_t, a, b, l, err);
 }
 
-// CheckMotif (Alg. 3) of the path (u' -e1- u -e2- v -e3- v').
-__device__ __forceinline__ uint64_t check_motif(const SamplerArgs& A, const Plan& P, int32_t up, int32_t u,
-                                                int32_t v, int32_t vp, int64_t t1, int64_t t2, int64_t t3,
-                                                uint32_t* err, uint64_t* checked) {
-  if (up == u || up == v || up == vp || u == v || u == vp || v == vp) return 0;
-  // anchor edges ordered by rank must have strictly increasing times
-  int64_t ta[3];  // times of anchor ranks rk[0] < rk[1] < rk[2]
-#pragma unroll
-  for (int j = 0; j < 3; j++) {
-    const int r = P.rk[j];
-    ta[j] = r == P.e1 ? t1 : (r == P.mid ? t2 : t3);
-  }
-  if (!(ta[0] < ta[1] && ta[1] < ta[2])) return 0;
-  if ((uint64_t)ta[2] - (uint64_t)ta[0] > (uint64_t)A.delta) return 0;
-  ++*checked;
-  // phi of a motif vertex, by its role on the path (u', u, v, v')
+// Product over the gaps of their ListCounts (Alg. 3, 4): gap gp holds the
+// non-anchor motif edges of ranks between anchor ranks NG gp and gp + 1, with
+// times in (ta[gp], ta[gp + 1]); the last gap runs up to ta[0] + delta
+// inclusive.  phi maps path roles (u', u, v, v') to graph vertices.
+template <int NG>
+__device__ __forceinline__ uint64_t gaps_product(const SamplerArgs& A, const Plan& P, const int64_t* ta, int32_t up,
+                                                 int32_t u, int32_t v, int32_t vp, uint32_t* err) {
   auto phi = [&](int role) { return role == 0 ? up : (role == 1 ? u : (role == 2 ? v : vp)); };
   uint64_t X = 1;
-  for (int gp = 0; gp < 3; gp++) {
+#pragma unroll
+  for (int gp = 0; gp < NG; gp++) {
     const int l = P.ngap[gp];
     if (l == 0) continue;
     const int64_t tlo = ta[gp];
-    const int64_t thi = gp < 2 ? ta[gp + 1] : sat_add(ta[0], A.delta);
-    const bool incl = gp == 2;
+    const int64_t thi = gp < NG - 1 ? ta[gp + 1] : sat_add(ta[0], A.delta);
+    const bool incl = gp == NG - 1;
     uint64_t c;
     if (l == 1) {  // one list: its length in the window
       uint32_t a0, b0;
@@ -347,6 +381,76 @@ __device__ __forceinline__ uint64_t check_motif(const SamplerArgs& A, const Plan
     X *= c;
   }
   return X;
+}
+
+// CheckMotif of a wedge (3-vertex motif): base (u, v, t0) and second edge
+// to or from y at time tj; the three vertices distinct, t0 < tj <= t0 + delta.
+__device__ __forceinline__ uint64_t check_wedge(const SamplerArgs& A, const Plan& P, int32_t y, int32_t u, int32_t v,
+                                                int64_t t0, int64_t tj, uint32_t* err, uint64_t* checked) {
+  if (u == v || y == u || y == v) return 0;
+  if (!(t0 < tj) || (uint64_t)tj - (uint64_t)t0 > (uint64_t)A.delta) return 0;
+  ++*checked;
+  const int64_t ta[2] = {t0, tj};
+  return gaps_product<2>(A, P, ta, y, u, v, y, err);
+}
+
+// CheckMotif (Alg. 3) of the path (u' -e1- u -e2- v -e3- v'), or of the
+// wedge (u' -e1- u -e2- v) / (u -e2- v -e3- v') of a wedge anchor.
+__device__ __forceinline__ uint64_t check_motif(const SamplerArgs& A, const Plan& P, int32_t up, int32_t u,
+                                                int32_t v, int32_t vp, int64_t t1, int64_t t2, int64_t t3,
+                                                uint32_t* err, uint64_t* checked) {
+  if (P.wedge)
+    return P.wedge == 1 ? check_wedge(A, P, up, u, v, t2, t1, err, checked)
+                        : check_wedge(A, P, vp, u, v, t2, t3, err, checked);
+  if (up == u || up == v || up == vp || u == v || u == vp || v == vp) return 0;
+  // anchor edges ordered by rank must have strictly increasing times
+  int64_t ta[3];  // times of anchor ranks rk[0] < rk[1] < rk[2]
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const int r = P.rk[j];
+    ta[j] = r == P.e1 ? t1 : (r == P.mid ? t2 : t3);
+  }
+  if (!(ta[0] < ta[1] && ta[1] < ta[2])) return 0;
+  if ((uint64_t)ta[2] - (uint64_t)ta[0] > (uint64_t)A.delta) return 0;
+  ++*checked;
+  return gaps_product<3>(A, P, ta, up, u, v, vp, err);
+}
+
+// The far vertex and time of the end edge at list position p of an alpha
+// list (alpha = 0: a wedge's dummy end, vertex -1).
+__device__ __forceinline__ void end_edge(const SamplerArgs& A, int alpha, uint32_t p, int32_t* x, int64_t* t) {
+  if (alpha < 0) {
+    const InEdge e = A.in_e[p];
+    *x = e.src;
+    *t = e.t;
+  } else if (alpha > 0) {
+    const OutEdge e = A.out_e[p];
+    *x = e.dst;
+    *t = e.t;
+  } else {
+    *x = -1;
+    *t = 0;
+  }
+}
+
+// Per-thread running sums of a sampling kernel.
+struct ThreadSums {
+  uint64_t sx = 0, hits = 0, checked = 0;
+  unsigned __int128 sx2 = 0;
+  uint32_t err = 0;
+};
+
+// The index must have been built for this graph, anchor class and delta
+// (the weights depend on nothing else); a proposal's records come from the
+// plain index.  Returns 0 or the error bits to report.
+__device__ __forceinline__ uint32_t index_check(const SamplerArgs& A, const Plan& P) {
+  const IndexHeader* H = A.hdr;
+  if (H->magic == kIndexMagic && H->status) return H->status;  // the weights pass overflowed
+  auto matches = [&](const IndexHeader* X) {
+    return X->magic == kIndexMagic && X->cls[0] == P.alpha1 && X->cls[1] == P.alpha3 && X->cls[2] == P.beta1 &&
+           X->cls[3] == P.beta3 && X->closed == P.closed && X->delta == A.delta && X->graph_id == A.graph_id;
+  };
+  return (matches(H) && (A.rec_hdr == nullptr || matches(A.rec_hdr))) ? 0u : kErrIndexMismatch;
 }
 
 // Resident blocks per SM the sampler is compiled for (caps its registers).
@@ -399,7 +503,7 @@ __device__ __forceinline__ void block_commit(SampleSums* G, uint64_t W, uint64_t
     atomicAdd(&G->sum_x2_hi, s_x2hi + ((ol + s_x2lo < ol) ? 1ull : 0ull));
     atomicAdd(&G->hits, s_hits);
     atomicAdd(&G->checked, s_checked);
-    if (blockIdx.x == 0) G->W = W;
+    G->W = W;
     if (e2) atomicOr(&G->err, e2);
   }
 }
@@ -421,12 +525,9 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS_DECL) k_path_sum(con
     s_x = s_x2lo = s_x2hi = s_hits = s_checked = 0;
   }
   __syncthreads();
-  const bool ok = H->magic == kIndexMagic && H->status == 0 && H->cls[0] == P.alpha1 && H->cls[1] == P.alpha3 &&
-                  H->cls[2] == P.beta1 && H->cls[3] == P.beta3 && H->closed == P.closed && H->anchor[0] == P.e1 &&
-                  H->anchor[1] == P.mid && H->anchor[2] == P.e3 && H->delta == A.delta &&
-                  H->graph_id == A.graph_id;
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(&A.sums->err, H->magic == kIndexMagic && H->status ? H->status : kErrIndexMismatch);
+  const uint32_t bad = index_check(A, P);
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(&A.sums->err, bad);
     return;
   }
   uint64_t sx = 0, hits = 0, checked = 0;
@@ -448,24 +549,8 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS_DECL) k_path_sum(con
     if (lo >= A.m || p1 >= A.m || p3 >= A.m) { err |= kErrBounds; continue; }
     int32_t up, vp;
     int64_t t1, t3;
-    if (P.alpha1 < 0) {
-      const InEdge x = A.in_e[p1];
-      up = x.src;
-      t1 = x.t;
-    } else {
-      const OutEdge x = A.out_e[p1];
-      up = x.dst;
-      t1 = x.t;
-    }
-    if (P.alpha3 < 0) {
-      const InEdge x = A.in_e[p3];
-      vp = x.src;
-      t3 = x.t;
-    } else {
-      const OutEdge x = A.out_e[p3];
-      vp = x.dst;
-      t3 = x.t;
-    }
+    end_edge(A, P.alpha1, p1, &up, &t1);
+    end_edge(A, P.alpha3, p3, &vp, &t3);
     const uint64_t X = check_motif(A, P, up, e.u, e.v, vp, t1, e.t, t3, &s_err, &checked);
     const uint64_t nx = sx + X;
     if (nx < sx) err |= kErrOverflow;
@@ -476,6 +561,58 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS_DECL) k_path_sum(con
   block_commit(A.sums, W, sx, sx2, hits, checked, err, s_err, s_x, s_x2lo, s_x2hi, s_hits, s_checked);
 }
 
+
+// One sample (Alg. 2, 3): sample index i within the call (id offset + i).
+template <bool Trace>
+__device__ __forceinline__ void sample_one(const SamplerArgs& A, const Plan& P, uint64_t W, uint32_t shift,
+                                           uint64_t i, ThreadSums& T, uint32_t* s_err) {
+  const uint64_t s = A.offset + i;
+  uint64_t r2, r1, r3;
+  if (!bounded_draw(A.seed, s, 0, W, &r2)) { T.err |= kErrRng; return; }
+  // middle edge: the unique e with prefix[e] <= r2 < prefix[e + 1]
+  const uint32_t b = (uint32_t)(r2 >> shift);
+  uint32_t lo = __ldg(A.guide + b), hi = __ldg(A.guide + b + 1);
+  while (lo < hi) {
+    const uint32_t mid = lo + ((hi - lo + 1) >> 1);
+    if (__ldg(A.prefix + mid) <= r2) lo = mid; else hi = mid - 1;
+  }
+  const EdgeRec e = A.rec[lo];
+  if (e.d1 == 0 || e.d3 == 0) { T.err |= kErrBounds; return; }  // index not built from this prefix
+  // e1 by draw 1, e3 by draw 2; a draw over one position is 0 without
+  // drawing (a wedge's dummy end, or a window of one edge)
+  r1 = r3 = 0;
+  if ((e.d1 > 1 && !bounded_draw(A.seed, s, 1, e.d1, &r1)) || (e.d3 > 1 && !bounded_draw(A.seed, s, 2, e.d3, &r3))) {
+    T.err |= kErrRng;
+    return;
+  }
+  const uint32_t p1 = e.lo1 + (uint32_t)r1, p3 = e.lo3 + (uint32_t)r3;
+  if (lo >= A.m || p1 >= A.m || p3 >= A.m) { T.err |= kErrBounds; return; }
+  int32_t up, vp;
+  int64_t t1, t3;
+  end_edge(A, P.alpha1, p1, &up, &t1);
+  end_edge(A, P.alpha3, p3, &vp, &t3);
+  const uint64_t X = check_motif(A, P, up, e.u, e.v, vp, t1, e.t, t3, s_err, &T.checked);
+  if (A.h && X) {  // exact per-h bins of the proposal estimator
+    unsigned long long* bin = A.bins + 3 * (uint64_t)__ldg(A.h + lo);
+    atomicAdd(bin, (unsigned long long)X);
+    const unsigned __int128 x2 = (unsigned __int128)X * X;
+    const unsigned long long l2 = (uint64_t)x2;
+    const unsigned long long old = atomicAdd(bin + 1, l2);
+    const unsigned long long carry = (old + l2 < old) ? 1ull : 0ull;
+    if ((x2 >> 64) || carry) atomicAdd(bin + 2, (unsigned long long)(x2 >> 64) + carry);
+  }
+  if (Trace) {
+    A.trace[4 * i + 0] = lo;
+    A.trace[4 * i + 1] = p1;
+    A.trace[4 * i + 2] = p3;
+    A.trace[4 * i + 3] = X;
+  }
+  const uint64_t nx = T.sx + X;
+  if (nx < T.sx) T.err |= kErrOverflow;
+  T.sx = nx;
+  T.sx2 += (unsigned __int128)X * X;
+  T.hits += X != 0;
+}
 
 template <bool Trace>
 __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __grid_constant__ SamplerArgs A,
@@ -490,87 +627,18 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __gr
     s_x = s_x2lo = s_x2hi = s_hits = s_checked = 0;
   }
   __syncthreads();
-  if (H->magic == kIndexMagic && H->status) {  // the weights pass overflowed
-    if (threadIdx.x == 0) atomicOr(&A.sums->err, H->status);
+  const uint32_t bad = index_check(A, P);
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(&A.sums->err, bad);
     return;
   }
-  auto matches = [&](const IndexHeader* X) {
-    return X->magic == kIndexMagic && X->cls[0] == P.alpha1 && X->cls[1] == P.alpha3 && X->cls[2] == P.beta1 &&
-           X->cls[3] == P.beta3 && X->closed == P.closed && X->anchor[0] == P.e1 && X->anchor[1] == P.mid &&
-           X->anchor[2] == P.e3 && X->delta == A.delta && X->graph_id == A.graph_id;
-  };
-  bool header_ok = matches(H) && (A.rec_hdr == nullptr || matches(A.rec_hdr));
-  if (!header_ok) {
-    if (threadIdx.x == 0) atomicOr(&A.sums->err, kErrIndexMismatch);
-    return;
-  }
-  uint64_t sx = 0, hits = 0, checked = 0;
-  unsigned __int128 sx2 = 0;
-  uint32_t err = 0;
+  ThreadSums T;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < A.count && W; j += stride) {
     const uint64_t i = A.chunk_base + (A.order ? __ldg(A.order + j) : j);  // sample index within the call
-    const uint64_t s = A.offset + i;
-    uint64_t r2, r1, r3;
-    if (!bounded_draw(A.seed, s, 0, W, &r2)) { err |= kErrRng; continue; }
-    // middle edge: the unique e with prefix[e] <= r2 < prefix[e + 1]
-    const uint32_t b = (uint32_t)(r2 >> shift);
-    uint32_t lo = __ldg(A.guide + b), hi = __ldg(A.guide + b + 1);
-    while (lo < hi) {
-      const uint32_t mid = lo + ((hi - lo + 1) >> 1);
-      if (__ldg(A.prefix + mid) <= r2) lo = mid; else hi = mid - 1;
-    }
-    const EdgeRec e = A.rec[lo];
-    if (e.d1 == 0 || e.d3 == 0) { err |= kErrBounds; continue; }  // index not built from this prefix
-    if (!bounded_draw(A.seed, s, 1, e.d1, &r1) || !bounded_draw(A.seed, s, 2, e.d3, &r3)) {
-      err |= kErrRng;
-      continue;
-    }
-    const uint32_t p1 = e.lo1 + (uint32_t)r1, p3 = e.lo3 + (uint32_t)r3;
-    if (lo >= A.m || p1 >= A.m || p3 >= A.m) { err |= kErrBounds; continue; }
-    int32_t up, vp;
-    int64_t t1, t3;
-    if (P.alpha1 < 0) {
-      const InEdge x = A.in_e[p1];
-      up = x.src;
-      t1 = x.t;
-    } else {
-      const OutEdge x = A.out_e[p1];
-      up = x.dst;
-      t1 = x.t;
-    }
-    if (P.alpha3 < 0) {
-      const InEdge x = A.in_e[p3];
-      vp = x.src;
-      t3 = x.t;
-    } else {
-      const OutEdge x = A.out_e[p3];
-      vp = x.dst;
-      t3 = x.t;
-    }
-    const uint64_t X = check_motif(A, P, up, e.u, e.v, vp, t1, e.t, t3, &s_err, &checked);
-    if (A.h && X) {  // exact per-h bins of the proposal estimator
-      unsigned long long* bin = A.bins + 3 * (uint64_t)__ldg(A.h + lo);
-      atomicAdd(bin, (unsigned long long)X);
-      const unsigned __int128 x2 = (unsigned __int128)X * X;
-      const unsigned long long l2 = (uint64_t)x2;
-      const unsigned long long old = atomicAdd(bin + 1, l2);
-      const unsigned long long carry = (old + l2 < old) ? 1ull : 0ull;
-      if ((x2 >> 64) || carry) atomicAdd(bin + 2, (unsigned long long)(x2 >> 64) + carry);
-    }
-    if (Trace) {
-      A.trace[4 * i + 0] = lo;
-      A.trace[4 * i + 1] = p1;
-      A.trace[4 * i + 2] = p3;
-      A.trace[4 * i + 3] = X;
-    }
-    const uint64_t nx = sx + X;
-    if (nx < sx) err |= kErrOverflow;
-    sx = nx;
-    sx2 += (unsigned __int128)X * X;
-    hits += X != 0;
+    sample_one<Trace>(A, P, W, shift, i, T, &s_err);
   }
-  block_commit(A.sums, W, sx, sx2, hits, checked, err, s_err, s_x, s_x2lo, s_x2hi, s_hits, s_checked);
+  block_commit(A.sums, W, T.sx, T.sx2, T.hits, T.checked, T.err, s_err, s_x, s_x2lo, s_x2hi, s_hits, s_checked);
 }
 
 // Processing order of the samples.  Samples whose middle-edge draws r are
@@ -760,8 +828,81 @@ __global__ void __launch_bounds__(256) k_key_scatter_b(const uint16_t* __restric
   tile_scatter(lo, hi, keys, ids, 0, base_s, nullptr, ids_out, cnt, start, warp_tot, stage, stage_k);
 }
 
-constexpr uint64_t kSortedMinSamples = 1ull << 16;  // below this, samples run in id order
-constexpr uint64_t kChunkSamples = 1ull << 28;
+// Scratch layout of sort_sample_ids for count samples: ids after pass A,
+// keys in id order and after pass A, the digit histogram, the segment tiling
+// and the histogram scan's tile sums.
+struct SortScratch {
+  uint32_t tiles, tiles_b;
+  size_t ids_a, keys_0, keys_a, hist, info, scan, bytes;  // byte offsets; total
+  uint64_t scan_words;
+};
+
+static SortScratch sort_scratch(uint64_t count) {
+  SortScratch L;
+  L.tiles = (uint32_t)((count + kBucketTile - 1) / kBucketTile);
+  L.tiles_b = L.tiles + kBuckets;
+  const uint64_t cap = (uint64_t)L.tiles * kBucketTile;
+  L.scan_words = scan_u64_scratch_words((uint64_t)kBuckets * L.tiles_b) + 1;
+  size_t p = 0;
+  L.ids_a = p;
+  p += align256(4 * cap);
+  L.keys_0 = p;
+  p += align256(2 * cap);
+  L.keys_a = p;
+  p += align256(2 * cap);
+  L.hist = p;
+  p += align256(4 * ((uint64_t)kBuckets * L.tiles_b + 1));
+  L.info = p;
+  p += align256(sizeof(SegInfo));
+  L.scan = p;
+  p += align256(4 * L.scan_words);
+  L.bytes = p;
+  return L;
+}
+
+size_t sort_scratch_bytes(uint64_t count) { return sort_scratch(count).bytes; }
+
+// Writes the indices 0..count-1 of samples first..first+count-1 into order
+// in key order (top 16 bits of each sample's middle-edge draw), using only
+// the given scratch of sort_scratch_bytes(count) bytes (no allocation).
+tc_status sort_sample_ids(const IndexHeader* hdr, uint64_t seed, uint64_t first, uint64_t count, void* scratch,
+                          uint32_t* order, cudaStream_t st) {
+  const SortScratch L = sort_scratch(count);
+  const uint32_t tiles = L.tiles, tiles_b = L.tiles_b;
+  char* base = (char*)scratch;
+  uint32_t* ids_a = (uint32_t*)(base + L.ids_a);
+  uint16_t* keys_0 = (uint16_t*)(base + L.keys_0);
+  uint16_t* keys_a = (uint16_t*)(base + L.keys_a);
+  uint32_t* hist = (uint32_t*)(base + L.hist);
+  SegInfo* info = (SegInfo*)(base + L.info);
+  uint32_t* scan_scratch = (uint32_t*)(base + L.scan);
+  const uint64_t scan_words = L.scan_words;
+  tc_status s = TC_OK;
+  auto ok = [&](const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_status(e, what);
+    return s == TC_OK;
+  };
+  k_key_hist<<<tiles, 256, 0, st>>>(hdr, seed, first, count, keys_0, hist, tiles);
+  TC_LAUNCHED(1);
+  if (!ok("k_key_hist")) return s;
+  TC_TRY(scan_u32_in_scratch(hist, hist, (uint64_t)kBuckets * tiles, scan_scratch, scan_words, st));
+  k_key_scatter_a<<<tiles, 256, 0, st>>>(count, keys_0, hist, tiles, keys_a, ids_a);
+  TC_LAUNCHED(1);
+  if (!ok("k_key_scatter_a")) return s;
+  k_seg_info<<<1, kBuckets, 0, st>>>(hist, tiles, count, info);
+  TC_LAUNCHED(1);
+  if (!ok("k_seg_info")) return s;
+  TC_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)kBuckets * tiles_b, st));
+  k_key_hist_b<<<tiles_b, 256, 0, st>>>(keys_a, info, hist);
+  TC_LAUNCHED(1);
+  if (!ok("k_key_hist_b")) return s;
+  TC_TRY(scan_u32_in_scratch(hist, hist, (uint64_t)kBuckets * tiles_b, scan_scratch, scan_words, st));
+  k_key_scatter_b<<<tiles_b, 256, 0, st>>>(keys_a, ids_a, info, hist, order);
+  TC_LAUNCHED(1);
+  ok("k_key_scatter_b");
+  return s;
+}
 
 tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
                          const void* index, uint64_t k, uint64_t seed, uint64_t offset, uint64_t* trace,
@@ -828,50 +969,15 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   if (k < kSortedMinSamples) return run(nullptr, 0, k);
   // samples in chunks; each chunk is put in key order first
   const uint64_t chunk = k < kChunkSamples ? k : kChunkSamples;
-  const uint64_t tiles_max = (chunk + kBucketTile - 1) / kBucketTile;
-  const uint64_t tiles_b_max = tiles_max + kBuckets;
-  const size_t hist_words = (size_t)kBuckets * tiles_b_max + 1;
+  const size_t sbytes = sort_scratch_bytes(chunk);
   char* buf = nullptr;
-  const size_t bytes = 12 * chunk + 4 * hist_words + sizeof(SegInfo) + 256;
-  TC_CUDA(pool_malloc(&buf, bytes, st));
-  uint32_t* ids_a = (uint32_t*)buf;                  // after pass A
-  uint32_t* ids_b = (uint32_t*)(buf + 4 * chunk);    // after pass B
-  uint16_t* keys_0 = (uint16_t*)(buf + 8 * chunk);   // id order
-  uint16_t* keys_a = (uint16_t*)(buf + 10 * chunk);  // after pass A
-  uint32_t* hist = (uint32_t*)(buf + 12 * chunk);
-  SegInfo* info = (SegInfo*)(((uintptr_t)(hist + hist_words) + 255) & ~(uintptr_t)255);
+  TC_CUDA(pool_malloc(&buf, sbytes + 4 * chunk, st));
+  uint32_t* order = (uint32_t*)(buf + sbytes);
   tc_status s = TC_OK;
-  auto ok = [&](const char* what) {
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) s = cuda_status(e, what);
-    return s == TC_OK;
-  };
   for (uint64_t base = 0; base < k && s == TC_OK; base += chunk) {
     const uint64_t count = (k - base) < chunk ? (k - base) : chunk;
-    const uint32_t tiles = (uint32_t)((count + kBucketTile - 1) / kBucketTile);
-    const uint32_t tiles_b = tiles + kBuckets;
-    k_key_hist<<<tiles, 256, 0, st>>>(v.hdr, seed, offset + base, count, keys_0, hist, tiles);
-    TC_LAUNCHED(1);
-    if (!ok("k_key_hist")) break;
-    if ((s = scan_u32(hist, hist, (uint64_t)kBuckets * tiles, st)) != TC_OK) break;
-    k_key_scatter_a<<<tiles, 256, 0, st>>>(count, keys_0, hist, tiles, keys_a, ids_a);
-    TC_LAUNCHED(1);
-    if (!ok("k_key_scatter_a")) break;
-    k_seg_info<<<1, kBuckets, 0, st>>>(hist, tiles, count, info);
-    TC_LAUNCHED(1);
-    if (!ok("k_seg_info")) break;
-    if (cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)kBuckets * tiles_b, st) != cudaSuccess) {
-      s = cuda_status(cudaGetLastError(), "memset");
-      break;
-    }
-    k_key_hist_b<<<tiles_b, 256, 0, st>>>(keys_a, info, hist);
-    TC_LAUNCHED(1);
-    if (!ok("k_key_hist_b")) break;
-    if ((s = scan_u32(hist, hist, (uint64_t)kBuckets * tiles_b, st)) != TC_OK) break;
-    k_key_scatter_b<<<tiles_b, 256, 0, st>>>(keys_a, ids_a, info, hist, ids_b);
-    TC_LAUNCHED(1);
-    if (!ok("k_key_scatter_b")) break;
-    s = run(ids_b, base, count);
+    s = sort_sample_ids(v.hdr, seed, offset + base, count, buf, order, st);
+    if (s == TC_OK) s = run(order, base, count);
   }
   cudaFreeAsync(buf, st);
   return s;
@@ -902,6 +1008,150 @@ tc_status launch_path_sum(const tc_graph* g, const Plan& plan, int64_t delta, co
   const uint64_t need = (W + 255) / 256;
   if (need < blocks) blocks = need ? need : 1;
   k_path_sum<<<(unsigned)blocks, 256, 0, st>>>(A, plan, 0, W);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched sampling: one persistent launch over the tiles of many queries
+// (graphs, motifs, windows).  Each block takes the next work item from a
+// global counter; items are numbered query after query, so a block sees
+// its queries in increasing order, keeps per-thread sums while the query
+// stays the same and commits them to that query's sums when it changes.
+// A query's samples and sums are those of the same query run alone.
+
+struct alignas(16) BatchQuery {
+  SamplerArgs A;
+  Plan P;
+};
+static_assert(sizeof(BatchQuery) <= kBatchQueryBytes, "batch record too large");
+static_assert(kBatchQueryBytes % 16 == 0, "batch record must be whole 16-byte words");
+
+void batch_query_record(void* h_rec, const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
+                        const void* index, uint64_t k, uint64_t seed, uint64_t offset, const uint32_t* order) {
+  std::memset(h_rec, 0, kBatchQueryBytes);
+  BatchQuery* Q = (BatchQuery*)h_rec;
+  const uint64_t m = (uint64_t)g->m;
+  IndexView v = index_view(const_cast<void*>(index), m);
+  SamplerArgs& A = Q->A;
+  A.out_e = g->out_e;
+  A.in_e = g->in_e;
+  A.pair_hash = g->pair_hash;
+  A.hash_mask = g->hash_mask;
+  A.pair_t = g->pair_t;
+  A.prefix = prefix;
+  A.hdr = v.hdr;
+  A.rec = v.rec;
+  A.guide = v.guide;
+  A.k = k;
+  A.seed = seed;
+  A.offset = offset;
+  A.order = order;
+  A.chunk_base = 0;
+  A.count = k;
+  A.m = (uint32_t)m;
+  A.delta = delta;
+  A.graph_id = g->id;
+  Q->P = plan;
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS, (256 * TC_SAMPLE_MIN_BLOCKS) / BS)
+    k_sample_batch(const char* __restrict__ records, const uint64_t* __restrict__ tile_begin, uint32_t nq,
+                   uint32_t tile, unsigned long long* __restrict__ next_item, SampleSums* __restrict__ sums) {
+  __shared__ BatchQuery s_q;
+  __shared__ unsigned long long s_item;
+  __shared__ uint32_t s_query;
+  __shared__ uint32_t s_err;
+  __shared__ unsigned long long s_x, s_x2lo, s_x2hi, s_hits, s_checked;
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    s_x = s_x2lo = s_x2hi = s_hits = s_checked = 0;
+  }
+  const uint64_t total = tile_begin[nq];
+  uint32_t cur = 0xFFFFFFFFu, bad = 0, shift = 0;
+  uint64_t W = 0;
+  ThreadSums T;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long item = atomicAdd(next_item, 1ull);
+      uint32_t q = nq;
+      if (item < total) {  // the last query whose first item is <= item
+        uint32_t lo = 0, hi = nq - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (tile_begin[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        q = lo;
+      }
+      s_item = item;
+      s_query = q;
+    }
+    __syncthreads();
+    const uint64_t item = s_item;
+    const uint32_t q = s_query;
+    if (q != cur) {  // block-uniform
+      if (cur != 0xFFFFFFFFu && !bad) {
+        block_commit(sums + cur, W, T.sx, T.sx2, T.hits, T.checked, T.err, s_err, s_x, s_x2lo, s_x2hi, s_hits,
+                     s_checked);
+        T = ThreadSums();
+        if (threadIdx.x == 0) {
+          s_err = 0;
+          s_x = s_x2lo = s_x2hi = s_hits = s_checked = 0;
+        }
+      }
+      if (q >= nq) break;
+      // the records are kBatchQueryBytes apart
+      const uint4* src = reinterpret_cast<const uint4*>(records + (uint64_t)q * kBatchQueryBytes);
+      uint4* dst = reinterpret_cast<uint4*>(&s_q);
+      for (uint32_t w = threadIdx.x; w < sizeof(BatchQuery) / 16; w += BS) dst[w] = src[w];
+      __syncthreads();
+      cur = q;
+      bad = index_check(s_q.A, s_q.P);
+      W = s_q.A.hdr->W;
+      shift = s_q.A.hdr->shift;
+      if (bad && threadIdx.x == 0) atomicOr(&sums[q].err, bad);
+    }
+    if (!bad && W) {
+      const uint64_t j0 = (item - tile_begin[q]) * tile;
+      const uint64_t j1 = j0 + tile < s_q.A.count ? j0 + tile : s_q.A.count;
+      const uint32_t* order = s_q.A.order;
+      for (uint64_t j = j0 + threadIdx.x; j < j1; j += BS) {
+        const uint64_t i = order ? (j & ~(kChunkSamples - 1)) + __ldg(order + j) : j;
+        sample_one<false>(s_q.A, s_q.P, W, shift, i, T, &s_err);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int sample_batch_blocks_per_sm(int bs) {
+  static int cache[3] = {0, 0, 0};
+  const int i = bs == 128 ? 0 : bs == 256 ? 1 : bs == 512 ? 2 : -1;
+  if (i < 0) return 0;
+  if (!cache[i]) {
+    int b = 0;
+    if (bs == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample_batch<128>, 128, 0);
+    if (bs == 256) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample_batch<256>, 256, 0);
+    if (bs == 512) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample_batch<512>, 512, 0);
+    cache[i] = b > 0 ? b : 1;
+  }
+  return cache[i];
+}
+
+tc_status launch_sample_batch(int bs, uint32_t tile, unsigned blocks, const void* d_records,
+                              const uint64_t* d_tile_begin, uint32_t nq, unsigned long long* d_next_item,
+                              SampleSums* d_sums, cudaStream_t st) {
+  const char* Q = (const char*)d_records;
+  if (bs == 128)
+    k_sample_batch<128><<<blocks, 128, 0, st>>>(Q, d_tile_begin, nq, tile, d_next_item, d_sums);
+  else if (bs == 256)
+    k_sample_batch<256><<<blocks, 256, 0, st>>>(Q, d_tile_begin, nq, tile, d_next_item, d_sums);
+  else if (bs == 512)
+    k_sample_batch<512><<<blocks, 512, 0, st>>>(Q, d_tile_begin, nq, tile, d_next_item, d_sums);
+  else
+    return set_error(TC_ERR_INVALID_ARG, "batch block size must be 128, 256 or 512");
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;

@@ -221,4 +221,36 @@ def large(seed=1005):
     return g
 
 
-CONFIGS = {"tiny": tiny, "mid": mid, "learned": learned, "large": large}
+BATCH_DELTAS = (600, 3600, 86400)
+
+
+def batch(seed=1003, n_small=64):
+    """Batched queries: a 50M-edge graph of the mid generator (n = 2.5M)
+    queried with all 24 time-rank orders of the directed 4-cycle at each
+    delta in BATCH_DELTAS, plus n_small graphs of 1e4 - 2e6 edges
+    (log-uniform) with one query each (rank order i mod 24, delta i mod 3).
+    Samples per query are log-uniform in [1e6, 1e8].  Queries are
+    (graph index, edges, delta, k, seed, sample_offset); graph 0 is the big
+    graph."""
+    import itertools
+    rng = np.random.default_rng(seed)
+    graphs = [chung_lu(2_500_000, 50_000_000, gamma=2.1, max_deg=2.5e5, multi_frac=0.30, seed=seed)]
+    sizes = np.exp(rng.uniform(np.log(1e4), np.log(2e6), n_small)).astype(np.int64)
+    for i, m_i in enumerate(sizes):
+        n_i = int(max(1000, m_i // 20))
+        graphs.append(chung_lu(n_i, int(m_i), gamma=2.1, max_deg=max(10.0, 1e5 * m_i / 20_000_000),
+                               multi_frac=0.30, seed=seed + 1 + i))
+    orders = [[C4[j] for j in p] for p in itertools.permutations(range(4))]
+    def k_draw():
+        return int(np.exp(rng.uniform(np.log(1e6), np.log(1e8))))
+    queries = []
+    for o, edges in enumerate(orders):
+        for d in BATCH_DELTAS:
+            queries.append((0, edges, d, k_draw(), 0, 0))
+    for i in range(n_small):
+        queries.append((1 + i, orders[i % 24], BATCH_DELTAS[i % 3], k_draw(), 0, 0))
+    return {"name": "batch", "graphs": graphs, "queries": queries, "motif": C4, "delta": 3600,
+            "k": sum(q[3] for q in queries)}
+
+
+CONFIGS = {"tiny": tiny, "mid": mid, "learned": learned, "large": large, "batch": batch}

@@ -41,6 +41,16 @@ class tc_estimate(ctypes.Structure):
                 ("checked", ctypes.c_uint64), ("estimate", ctypes.c_double), ("std_err", ctypes.c_double)]
 
 
+class tc_query(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("motif", tc_motif), ("delta", ctypes.c_int64), ("k", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("sample_offset", ctypes.c_uint64)]
+
+
+class tc_batch_options(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_int32), ("tile", ctypes.c_uint32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class tc_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("num_pairs", ctypes.c_int64),
                 ("t_min", ctypes.c_int64), ("t_max", ctypes.c_int64)]
@@ -86,6 +96,13 @@ def lib():
                                     vp, vp, vp, ctypes.POINTER(u64), vp],
             "tc_sample_estimate_q": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, vp, u64, u64, u64,
                                      ctypes.POINTER(tc_estimate), vp, vp, vp],
+            "tc_batch_create": [ctypes.POINTER(tc_query), i64, ctypes.POINTER(tc_batch_options), vp,
+                                ctypes.POINTER(vp)],
+            "tc_batch_run": [vp, ctypes.POINTER(tc_estimate), vp],
+            "tc_batch_info": [vp, ctypes.POINTER(tc_batch_options), ctypes.POINTER(u64), ctypes.POINTER(u64),
+                              ctypes.POINTER(u64)],
+            "tc_batch_timing": [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+            "tc_batch_destroy": [vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -417,3 +434,62 @@ def tc_sample_estimate_q(g, motif, delta, weights, proposal, k, seed=0, offset=0
     if trace:
         out["trace"] = tr[:k]
     return out
+
+
+class Batch:
+    """A fixed list of queries answered together (tc_batch_*).  queries: a
+    list of (graph, motif edges or tc_motif, delta, k, seed, sample_offset);
+    the graphs must outlive the batch."""
+
+    def __init__(self, queries, block_size=0, tile=0, use_graph=True, stream=None):
+        self._graphs = [q[0] for q in queries]
+        arr = (tc_query * max(1, len(queries)))()
+        for i, (g, motif, delta, k, seed, offset) in enumerate(queries):
+            arr[i].graph = g.handle
+            arr[i].motif = motif if isinstance(motif, tc_motif) else make_motif(motif)
+            arr[i].delta = int(delta)
+            arr[i].k = int(k)
+            arr[i].seed = int(seed)
+            arr[i].sample_offset = int(offset)
+        opts = tc_batch_options(int(block_size), int(tile), 1 if use_graph else 0, 0)
+        h = ctypes.c_void_p()
+        _check(lib().tc_batch_create(arr, len(queries), ctypes.byref(opts), _stream(stream), ctypes.byref(h)),
+               "tc_batch_create")
+        self._h = h
+        self.nq = len(queries)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("batch destroyed")
+        return self._h
+
+    def run(self, stream=None):
+        out = (tc_estimate * max(1, self.nq))()
+        _check(lib().tc_batch_run(self.handle, out, _stream(stream)), "tc_batch_run")
+        return [_est_dict(out[i]) for i in range(self.nq)]
+
+    def info(self):
+        o = tc_batch_options()
+        launches, nbytes, slots = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().tc_batch_info(self.handle, ctypes.byref(o), ctypes.byref(launches), ctypes.byref(nbytes),
+                                   ctypes.byref(slots)), "tc_batch_info")
+        return {"block_size": o.block_size, "tile": o.tile, "use_graph": bool(o.use_graph),
+                "launches_per_run": launches.value, "device_bytes": nbytes.value, "weight_slots": slots.value}
+
+    def timing(self):
+        """Device milliseconds of the last run: (whole run, sampling launch)."""
+        run, samp = ctypes.c_float(), ctypes.c_float()
+        _check(lib().tc_batch_timing(self.handle, ctypes.byref(run), ctypes.byref(samp)), "tc_batch_timing")
+        return run.value, samp.value
+
+    def destroy(self):
+        if self._h:
+            lib().tc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -41,7 +41,11 @@ def test_motif_plan_host_only(libtc):
     # the library's motif compiler agrees with the oracle's on anchor and class
     zoo = path_motifs_all_classes() + [[(0, 1), (1, 2), (2, 3), (3, 0)], [(0, 1), (1, 2), (2, 3), (0, 3)],
                                        [(1, 2), (0, 1), (2, 3), (3, 0)], [(2, 3), (1, 2), (0, 1), (0, 3)],
-                                       [(0, 1), (1, 2), (2, 3), (3, 2), (2, 1), (1, 0), (0, 1), (1, 2), (2, 3)]]
+                                       [(0, 1), (1, 2), (2, 3), (3, 2), (2, 1), (1, 0), (0, 1), (1, 2), (2, 3)],
+                                       # 3-vertex motifs: wedge anchors at the base's source and head
+                                       [(0, 1), (0, 2), (1, 2)], [(0, 1), (1, 2), (2, 0)], [(0, 1), (2, 1), (0, 2)],
+                                       [(0, 1), (2, 0), (2, 1)], [(0, 1), (0, 2)],
+                                       [(0, 1), (1, 0), (0, 1), (1, 2), (2, 1)]]
     for edges in zoo:
         anchor, cls = tc.tc_motif_plan(tc.make_motif(edges))
         p = oracle.compile_motif(edges)
@@ -50,9 +54,10 @@ def test_motif_plan_host_only(libtc):
 
 
 @pytest.mark.parametrize("edges,status", [
-    ([(0, 1), (1, 2)], 1),                       # too few edges
+    ([(0, 1)], 1),                               # too few edges
+    ([(0, 1), (2, 3)], 1),                       # four labels need three edges
     ([(0, 1), (1, 1), (2, 3)], 1),               # self-loop
-    ([(0, 1), (1, 2), (2, 0)], 1),               # only three labels
+    ([(0, 1), (1, 0), (0, 1)], 1),               # only two labels
     ([(0, 1), (2, 3), (0, 1), (2, 3)], 5),       # no 3-path through edge 0
 ])
 def test_motif_errors(libtc, edges, status):
