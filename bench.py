@@ -32,6 +32,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "temporal-path samples/sec"
+MOTIFS = {  # name -> edges in time-rank order
+    "c4": [(0, 1), (1, 2), (2, 3), (3, 0)],             # directed 4-cycle (M4-0)
+    "path_chord": [(0, 1), (1, 2), (2, 3), (0, 3)],     # a->b, b->c, c->d, then a->d
+    "ff_triangle": [(0, 1), (0, 2), (1, 2)],            # 3-vertex: a->b, a->c, b->c (wedge anchor <+,>>)
+    "cyclic_triangle": [(0, 1), (1, 2), (2, 0)],        # 3-vertex: a->b, b->c, c->a
+}
+MOTIF_NAMES = {str(v): k for k, v in MOTIFS.items()}
+# DRAM bytes (read + write) per sample of the sampler kernel, from one ncu
+# capture of the benchmark's own launch (dram__bytes_read.sum +
+# dram__bytes_write.sum over two 1e8-sample launches); valid while the kernel
+# is unchanged, null for workloads that were not captured
+SAMPLER_TRAFFIC_PER_SAMPLE = {("mid", "path_chord"): 87.2}
 UNIT = "samples/s"
 SECTOR = 32
 
@@ -49,7 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--train-samples", type=int, default=10_000_000)
-    ap.add_argument("--workload", default="mid", choices=["mid", "learned", "large", "batch"],
+    ap.add_argument("--motif", default=None, choices=sorted(MOTIFS),
+                    help="another motif on the workload's graph (default: the workload's own)")
+    ap.add_argument("--workload", default="mid", choices=["mid", "learned", "large", "batch", "small", "batch_small"],
                     help="mid: the 20M-edge graph (default); learned: n=2e7, m=1e8; large: n=1e8, m=3e8")
     return ap.parse_args()
 
@@ -138,6 +152,9 @@ WORKLOADS = {
                "learned proposal trained on 1e7 plain samples",
     "large": "large: n=100M m=300M, top degree ~1e6, pair multiplicities Zipf(1.8), daily periodicity over 1e8 s; "
              "directed 4-cycle (M4-0), delta=3600, k=1e9 samples per step",
+    "small": "small (profiling case): the mid generator at n=5e5 m=1e7; path+chord, delta=3600, k=1e7",
+    "batch_small": "batch_small (profiling case): as batch with a 1e7-edge big graph, 8 small graphs and 1e5-1e7 "
+                   "samples per query",
     "batch": "batch: 136 queries in one persistent launch replayed from a CUDA graph; a 50M-edge graph of the mid "
              "generator (n=2.5M) with all 24 time-rank orders of the directed 4-cycle x delta in {600, 3600, 86400}, "
              "plus 64 graphs of 1e4-2e6 edges (log-uniform) with one query each; 1e6-1e8 samples per query "
@@ -172,9 +189,11 @@ def run_reference(args, rank, world):
         return
     cfg = workload(args.workload)
     k = args.samples or cfg["k"]
-    if args.workload == "batch":  # the oracle on the big graph's first query, scaled to all samples
+    if args.workload in ("batch", "batch_small"):  # the oracle on the big graph's first query, scaled
         gi, edges, delta = cfg["queries"][0][:3]
-        cfg = dict(cfg["graphs"][gi], name="batch", motif=edges, delta=delta)
+        cfg = dict(cfg["graphs"][gi], name=args.workload, motif=edges, delta=delta)
+    elif args.motif:
+        cfg["motif"], cfg["motif_override"] = MOTIFS[args.motif], args.motif
     import oracle
     og = oracle.build_csr(cfg["n"], cfg["src"], cfg["dst"], cfg["t"], sort="lexsort")
     plan = oracle.compile_motif(cfg["motif"])
@@ -221,6 +240,8 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
         return out, a.elapsed_time(b)
 
     feat, feat_ms = timed(lambda: tc.tc_edge_features(g, mot, delta, wts))
+    # sample statistics from n_train plain samples of another seed than the training paths
+    _, sfeat_ms = timed(lambda: tc.tc_sample_features(g, mot, delta, wts, feat, n_train, seed=777))
     mlp = tc.MLP(seed=1)
     losses, train_ms = timed(lambda: tc.tc_mlp_train(mlp, g, mot, delta, wts, feat, n_train, seed=12345,
                                                      batch=16384, lr=3e-3))
@@ -241,23 +262,27 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
     tp = t_1pct(var_plain, plain_sampler_ms / k)
     tl = t_1pct(var_learned, q_ms / k)
     mlp.destroy()
-    return {"train_samples": n_train, "train_ms": train_ms, "features_ms": feat_ms, "proposal_ms": prop_ms,
+    return {"train_samples": n_train, "train_ms": train_ms, "features_ms": feat_ms,
+            "sample_features_ms": sfeat_ms, "proposal_ms": prop_ms,
             "loss_first_batch": losses[0], "loss_last_batch": losses[1],
             "sampler_ms": q_ms, "samples_per_s": k / (q_ms / 1e3), "estimate": c, "std_err": rq["std_err"],
             "plain_estimate": plain["estimate"], "plain_std_err": plain["std_err"],
             "variance_ratio_learned_over_plain": var_learned / var_plain,
             "time_to_1pct_ms_plain": tp, "time_to_1pct_ms_learned": tl, "time_ratio_learned_over_plain": tl / tp,
-            "time_ratio_with_setup": (tl + feat_ms + train_ms + prop_ms) / (tp + weights_ms)}
+            "time_ratio_with_setup": (tl + feat_ms + sfeat_ms + train_ms + prop_ms) / (tp + weights_ms)}
 
 
 def config_dict(cfg, k, world):
-    if cfg["name"] == "batch":
-        return {"workload": WORKLOADS["batch"], "k": int(k), "seed": 0,
+    if cfg["name"] in ("batch", "batch_small"):
+        return {"workload": WORKLOADS[cfg["name"]], "k": int(k), "seed": 0,
                 "parallelism": "dp%d (sample-id ranges)" % world,
                 "reference_sample": "oracle on the 50M-edge graph, first query (4-cycle, delta=600)"}
-    return {"workload": WORKLOADS[cfg["name"]],
+    wl = WORKLOADS[cfg["name"]]
+    if cfg.get("motif_override"):
+        wl += "; motif replaced by %s" % cfg["motif_override"]
+    return {"workload": wl,
             "n": int(cfg["n"]), "m": int(len(cfg["src"])),
-            "motif": "path+chord" if cfg["motif"] == [(0, 1), (1, 2), (2, 3), (0, 3)] else "directed 4-cycle",
+            "motif": MOTIF_NAMES.get(str([tuple(e) for e in cfg["motif"]]), str(cfg["motif"])),
             "delta": int(cfg["delta"]),
             "k": int(k), "seed": 0, "parallelism": "dp%d (sample-id ranges)" % world,
             "l2": "inputs larger than L2 (graph + index ~2.4 GB resident)"}
@@ -268,7 +293,7 @@ def run_batch(args, rank, world, local):
     per distinct key, key sorts, one persistent sampling launch)."""
     import torch
     from paper_2409_08975_gb300 import tc
-    cfg = workload("batch")
+    cfg = workload(args.workload)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     dev = [(torch.from_numpy(g["src"]).cuda(), torch.from_numpy(g["dst"]).cuda(), torch.from_numpy(g["t"]).cuda())
@@ -361,10 +386,10 @@ def run_batch(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS["batch"], "queries": len(queries), "graphs": len(graphs),
+            "config": {"workload": WORKLOADS[args.workload], "queries": len(queries), "graphs": len(graphs),
                        "m_total": int(m_total), "k": int(k_total), "seed": 0,
                        "parallelism": "dp%d (sample-id ranges)" % world,
-                       "l2": "inputs larger than L2 (big graph + 12 weight indexes ~30 GB resident)"},
+                       "l2": "inputs larger than L2 (the big graph and its weight indexes)"},
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": None,
             "csr_build_ms": csr_ms, "batch": dict(info, create_s=create_s, sampling_ms_median=sampler_ms),
             "estimates": [{"W": r["W"], "k": r["k"], "estimate": r["estimate"], "std_err": r["std_err"]}
@@ -392,13 +417,15 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     tc.lib()
-    if args.workload == "batch":
+    if args.workload in ("batch", "batch_small"):
         run_batch(args, rank, world, local)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
     cfg = workload(args.workload)
+    if args.motif:
+        cfg["motif"], cfg["motif_override"] = MOTIFS[args.motif], args.motif
     k = args.samples or cfg["k"]
     n, m, delta = cfg["n"], len(cfg["src"]), cfg["delta"]
     stream = torch.cuda.current_stream()
@@ -418,6 +445,8 @@ def main():
 
     wts = tc.alloc_weights(g)
 
+    kernel_ms = []
+
     def step(i, sample_events=None):
         # step i of rank r draws sample ids [(i * world + r) * k, + k)
         tc.tc_path_weights(g, mot, delta, out=wts, want_W=False)
@@ -426,6 +455,7 @@ def main():
         r = tc.tc_sample_estimate(g, mot, delta, wts, k, seed=0, offset=(i * world + rank) * k)
         if sample_events is not None:
             sample_events[1].record(stream)
+            kernel_ms.append(tc.tc_last_sampler_ms())
         return r
 
     for i in range(args.warmup):
@@ -439,6 +469,7 @@ def main():
     time.sleep(0.3)
     pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = tc.tc_kernel_launches()
+    tc.tc_set_timing(True)  # events around the sampling launch inside each call
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     start.record(stream)
@@ -447,6 +478,7 @@ def main():
         results.append(step(args.warmup + i, pairs[i]))
     end.record(stream)
     torch.cuda.synchronize()
+    tc.tc_set_timing(False)
     launches = tc.tc_kernel_launches() - launches0
     clk = clocks.stop()
     total_ms = start.elapsed_time(end)
@@ -488,12 +520,21 @@ def main():
     # (pair_off, pair_dst, pair_eoff, pair_t: 4 sectors)
     bytes_per_sample = SECTOR * (5 + 4 * checked_frac)
     peak, peak_kind = load_peaks()
-    achieved = bytes_per_sample * k / (sampler_ms / 1e3) / 1e9
+    k_sample_ms = statistics.mean(kernel_ms)  # the sampling launch alone, key-order sort excluded
+    achieved = bytes_per_sample * k / (k_sample_ms / 1e3) / 1e9
+    tps = SAMPLER_TRAFFIC_PER_SAMPLE.get((cfg["name"], MOTIF_NAMES.get(str([tuple(e) for e in cfg["motif"]]))))
     roofline = {"bound": "hbm", "kernel": "k_sample (sampler, Alg. 2-4)", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_sample": bytes_per_sample, "sampler_ms": sampler_ms}
-    weights_bytes = 64 * m + 16 * m + 4 * (2 ** max(1, (m - 1).bit_length()))
-    weights = {"ms": weights_ms, "bytes": weights_bytes,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": tps * k if tps else None, "peak_kind": peak_kind,
+                "bytes_per_sample": bytes_per_sample, "kernel_ms": k_sample_ms, "sampler_call_ms": sampler_ms}
+    # algorithmic bytes of the weights step, per the kernels: the v-window pass
+    # 44 B/edge (absent for a wedge whose window is at u); the u-window pass
+    # 16 B edge + 8 B parked v window + 16 B of the searched list (absent for
+    # a wedge at v) + 32 B record + 8 B w; the exact scan 24 B/edge; the
+    # guide 8 B/edge plus 4 B per bucket
+    alpha1, alpha3 = tc.tc_motif_plan(mot)[1][:2]
+    per_edge = (44 if alpha3 else 0) + 16 + (8 if alpha3 else 0) + (16 if alpha1 else 0) + 40 + 24 + 8
+    weights_bytes = per_edge * m + 4 * (2 ** max(1, (m - 1).bit_length()))
+    weights = {"ms": weights_ms, "bytes": weights_bytes, "bytes_per_edge": per_edge,
                "achieved_gbs": weights_bytes / (weights_ms / 1e3) / 1e9,
                "frac": weights_bytes / (weights_ms / 1e3) / 1e9 / peak}
 

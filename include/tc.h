@@ -293,8 +293,9 @@ tc_status tc_mlp_get_params(const tc_mlp* mlp, float* h_params);
 tc_status tc_mlp_set_params(tc_mlp* mlp, const float* h_params);
 
 /*
- * Per canonical edge e = (u, v, t), bf16 features (row stride 16, last 4 zero),
- * each log1p of a count: 0 d1, 1 d3, 2 w_e (the anchor's windows, Claim 1),
+ * Per canonical edge e = (u, v, t), bf16 features (row stride 16; columns
+ * 12..15 are set to zero here and filled by tc_sample_features), each log1p
+ * of a count: 0 d1, 1 d3, 2 w_e (the anchor's windows, Claim 1),
  * 3..6 in- and out-degree of u, then of v, over [t - delta, t + delta],
  * 7 sigma_{u,v}[t - delta, t + delta], 8 sigma_{v,u}[t - delta, t + delta]
  * (Def. 3), 9 out-degree of u, 10 in-degree of v, 11 in-degree of u.
@@ -304,21 +305,43 @@ tc_status tc_mlp_set_params(tc_mlp* mlp, const float* h_params);
 tc_status tc_edge_features(const tc_graph* g, const tc_motif* motif, int64_t delta, const void* d_index,
                            uint16_t* d_feat, void* stream);
 
+/*
+ * Sample-statistics features, columns 12..15 of every row of d_feat: draws
+ * n_samples paths with the plain sampler (sample ids sample_offset ..
+ * sample_offset + n_samples - 1 of seed, as tc_sample_trace) and, with the
+ * time bucket b(t) = (floor(t / D) - floor(t_min / D)) mod 2^32 for D =
+ * max(delta, 1) and t_min the graph's earliest time, the keys K1 = (u, v),
+ * K2 = (u, b(t)), K3 = (v, b(t)) of an edge: n_K = the samples whose middle
+ * edge has key K, s_K = the sum of their X^2, prior = sum X^2 / n_samples.
+ * Columns: log1p((s_K + prior) / (n_K + 1)) for K1, K2, K3, then
+ * log1p(n_K1), in bf16.  The other columns are left as they are.  Draw
+ * these samples disjoint from those tc_mlp_train uses (another seed or id
+ * range), so that no training path sees its own outcome.  d_feat must be
+ * 16-byte aligned.  Synchronises the stream.  Errors as tc_sample_estimate.
+ */
+tc_status tc_sample_features(const tc_graph* g, const tc_motif* motif, int64_t delta, const uint64_t* d_prefix,
+                             const void* d_index, uint64_t n_samples, uint64_t seed, uint64_t sample_offset,
+                             uint16_t* d_feat, void* stream);
+
 /* Logits z of rows d_rows[i] (or i when d_rows is NULL) of d_feat into
  * d_logits[n] (FP32); g = sigmoid(z). */
 tc_status tc_mlp_forward(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, uint64_t n,
                          float* d_logits, void* stream);
 
-/* Gradient of the mean binary cross-entropy of sigmoid(z) against d_labels
- * (0 or 1) over n rows into d_grad[TC_MLP_PARAMS] (FP32, overwritten);
- * h_loss (optional) receives the mean loss.  Synchronises the stream. */
+/* Gradient over n rows of the mean closure loss of g = sigmoid(z) against
+ * the closure counts d_labels (y >= 0): y softplus(-z) = -y log g for y > 0,
+ * softplus(z) = -log(1 - g) for y = 0 -- the binary cross-entropy when every
+ * y is 0 or 1, and minimised at g = E[X] / (E[X] + P(X = 0)) -- into
+ * d_grad[TC_MLP_PARAMS] (FP32, overwritten); h_loss (optional) receives the
+ * mean loss.  Synchronises the stream. */
 tc_status tc_mlp_grad(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, const float* d_labels,
                       uint64_t n, float* d_grad, float* h_loss, void* stream);
 
 /*
  * Train on n_samples paths drawn by the plain sampler (tc_sample_trace with
- * seed, ids 0..n_samples-1): input the features of the middle edge, label
- * [X > 0].  One pass of Adam (lr, betas 0.9 / 0.999) in batches of `batch`.
+ * seed, ids 0..n_samples-1): input the 16 features of the middle edge,
+ * label the closure count X, loss as tc_mlp_grad.  One pass of Adam (lr,
+ * betas 0.9 / 0.999) in batches of `batch`.
  * h_losses (optional) receives the mean loss of the first and last batch.
  * Synchronises the stream.
  */
@@ -423,6 +446,14 @@ tc_status tc_batch_destroy(tc_batch* b);
 /* Number of kernels this library has launched in this process so far
  * (a diagnostic for counting launches around a region). */
 uint64_t tc_kernel_launches(void);
+
+/* Diagnostic timing on this thread: while enabled, tc_sample_estimate,
+ * tc_sample_trace and tc_sample_estimate_q record CUDA events around their
+ * sampling launches (the key-order sort excluded), and tc_last_sampler_ms
+ * returns the device time of those launches in the last such call, in
+ * milliseconds (0 when timing was off). */
+tc_status tc_set_timing(int32_t enabled);
+float tc_last_sampler_ms(void);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* tc_last_error(void);

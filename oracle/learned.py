@@ -6,8 +6,10 @@ integer h_e >= 1: the path P with middle edge e is drawn with probability
 (w_e h_e / Q)(1 / w_e) = h_e / Q, so Y = X Q / h_e has E[Y] = C, where
 Q = sum_e w_e h_e.  Here:
   * ``edge_features``   the 12 per-edge counts (plain definitions)
+  * ``sample_features`` four per-edge statistics of the plain sampler's
+    outcomes (columns 12..15)
   * ``bf16`` / ``features_bf16``   log1p then bf16 rounding (to nearest even)
-  * ``mlp_forward`` / ``mlp_backward``   12 -> 64 -> 64 -> 1 network in FP64
+  * ``mlp_forward`` / ``mlp_backward``   16 -> 64 -> 64 -> 1 network in FP64
     on bf16 weights and inputs, activations rounded to bf16 between layers
   * ``proposal_h``      h = max(1, floor(S (eps + g) + 1/2))
   * ``sample_run_q``    Alg. 2 / 3 / 5 with the proposal, per-h exact bins
@@ -52,6 +54,45 @@ def edge_features(g, plan, delta):
     return f
 
 
+def sample_features(g, plan, delta, prefix, n, seed, offset=0):
+    """Sample-statistics features (columns 12..15 of a feature row) of every
+    canonical edge e = (u, v, t), from n samples of the plain sampler (ids
+    offset .. offset + n - 1 of seed; Alg. 2, 3).  With the time bucket
+    b(t) = (floor(t / D) - floor(t_min / D)) mod 2^32, D = max(delta, 1),
+    t_min the graph's earliest time, and the keys K1 = (u, v), K2 = (u, b(t)),
+    K3 = (v, b(t)): n_K is the number of samples whose middle edge has key K
+    and s_K the sum of their X^2; prior = (sum of all X^2) / n.  Returns FP64
+    [m, 4]: (s_K1 + prior) / (n_K1 + 1), the same for K2 and K3, and n_K1
+    (log1p is applied with the other features)."""
+    from .core import sample_run
+    m = g.m
+    out = np.zeros((m, 4), np.float64)
+    if m == 0 or n == 0:
+        return out
+    _, tr = sample_run(g, plan, delta, prefix, n, seed, offset, trace=True)
+    i2 = tr[:, 0].astype(np.int64)
+    x2 = tr[:, 3].astype(np.float64) ** 2
+    prior = float(x2.sum()) / n
+    u = g.src[g.out_perm].astype(np.uint64)
+    v = g.dst[g.out_perm].astype(np.uint64)
+    t = g.t[g.out_perm]
+    D = max(int(delta), 1)
+    b = ((t // D) - (int(g.t.min()) // D)).astype(np.int64).astype(np.uint64) & np.uint64(0xFFFFFFFF)
+    sh = np.uint64(32)
+    for col, key in enumerate(((u << sh) | v, (u << sh) | b, (v << sh) | b)):
+        ks, inv = np.unique(key[i2], return_inverse=True)
+        cnt = np.bincount(inv, minlength=len(ks)).astype(np.float64)
+        sx2 = np.bincount(inv, weights=x2, minlength=len(ks))
+        pos = np.minimum(np.searchsorted(ks, key), len(ks) - 1)
+        hit = ks[pos] == key
+        n_e = np.where(hit, cnt[pos], 0.0)
+        s_e = np.where(hit, sx2[pos], 0.0)
+        out[:, col] = (s_e + prior) / (n_e + 1.0)
+        if col == 0:
+            out[:, 3] = n_e
+    return out
+
+
 def bf16(x):
     """Round to bfloat16 (through float32, both to nearest even); returns
     float32 values that are exactly representable in bfloat16."""
@@ -61,10 +102,14 @@ def bf16(x):
     return r.astype(np.uint32).view(np.float32).reshape(f.shape)
 
 
-def features_bf16(counts):
-    """log1p of the counts, rounded to bf16, padded to 16 columns."""
+def features_bf16(counts, sample_stats=None):
+    """log1p of the counts, rounded to bf16, in 16 columns; the four
+    sample-statistics values (``sample_features``) fill columns 12..15 when
+    given, else those columns are zero."""
     out = np.zeros((counts.shape[0], K_PAD), np.float32)
     out[:, :N_FEAT] = bf16(np.log1p(counts))
+    if sample_stats is not None:
+        out[:, N_FEAT:] = bf16(np.log1p(sample_stats))
     return out
 
 
@@ -73,9 +118,8 @@ def init_params(rng):
     def u(shape, fan_in):
         b = 1.0 / math.sqrt(fan_in)
         return rng.uniform(-b, b, shape)
-    W1 = np.zeros((HIDDEN, K_PAD))
-    W1[:, :N_FEAT] = u((HIDDEN, N_FEAT), N_FEAT)
-    return {"W1": W1, "b1": u(HIDDEN, N_FEAT), "W2": u((HIDDEN, HIDDEN), HIDDEN), "b2": u(HIDDEN, HIDDEN),
+    return {"W1": u((HIDDEN, K_PAD), K_PAD), "b1": u(HIDDEN, K_PAD), "W2": u((HIDDEN, HIDDEN), HIDDEN),
+            "b2": u(HIDDEN, HIDDEN),
             "W3": u(HIDDEN, HIDDEN), "b3": u(1, HIDDEN)}
 
 
@@ -125,14 +169,17 @@ def mlp_forward(params, x, round_acts=True, quantized=True):
     return z3, (x, z1, a1, z2, a2)
 
 
-def bce_loss(z3, y):
-    """Mean binary cross-entropy of sigmoid(z3) against y, in the stable form
-    softplus(z3) - y z3."""
-    return float(np.mean(np.logaddexp(0.0, z3) - y * z3))
+def closure_loss(z3, y):
+    """Mean closure loss of g = sigmoid(z3) against closure counts y >= 0:
+    y softplus(-z3) = -y log g where y > 0, softplus(z3) = -log(1 - g) where
+    y = 0.  For labels 0 and 1 it is the binary cross-entropy; its minimiser
+    per input is g = E[y] / (E[y] + P(y = 0))."""
+    y = np.asarray(y, np.float64)
+    return float(np.mean(np.where(y > 0, y * np.logaddexp(0.0, -z3), np.logaddexp(0.0, z3))))
 
 
 def mlp_backward(params, x, y, round_acts=True, quantized=True):
-    """Gradients of bce_loss(mlp_forward(x), y) with respect to the FP32
+    """Gradients of closure_loss(mlp_forward(x), y) with respect to the FP32
     parameters (the bf16 roundings are treated as identity in the chain rule,
     as in the library's backward)."""
     z3, (xb, z1, a1, z2, a2) = mlp_forward(params, x, round_acts, quantized)
@@ -143,7 +190,9 @@ def mlp_backward(params, x, y, round_acts=True, quantized=True):
     else:
         W2 = np.asarray(params["W2"], np.float64)
         W3 = np.asarray(params["W3"], np.float64)
-    dz3 = (1.0 / (1.0 + np.exp(-z3)) - y) / B
+    y = np.asarray(y, np.float64)
+    g3 = 1.0 / (1.0 + np.exp(-z3))
+    dz3 = np.where(y > 0, -y * (1.0 - g3), g3) / B
     g = {"W3": a2.T @ dz3, "b3": np.array([dz3.sum()])}
     dz2 = np.outer(dz3, W3) * (z2 > 0)
     g["W2"] = dz2.T @ a1
@@ -151,7 +200,7 @@ def mlp_backward(params, x, y, round_acts=True, quantized=True):
     dz1 = (dz2 @ W2) * (z1 > 0)
     g["W1"] = dz1.T @ xb
     g["b1"] = dz1.sum(0)
-    return g, bce_loss(z3, y)
+    return g, closure_loss(z3, y)
 
 
 def proposal_h(g, eps, scale):

@@ -288,6 +288,13 @@ const char* tc_last_error(void) { return t_err.c_str(); }
 
 uint64_t tc_kernel_launches(void) { return g_launches.load(); }
 
+tc_status tc_set_timing(int32_t enabled) {
+  set_timing(enabled != 0);
+  return TC_OK;
+}
+
+float tc_last_sampler_ms(void) { return last_sampler_ms(); }
+
 tc_status tc_motif_plan(const tc_motif* motif, int32_t* h_anchor, int32_t* h_class) {
   Plan p;
   TC_TRY(plan_of(motif, &p));
@@ -605,6 +612,43 @@ tc_status tc_edge_features(const tc_graph* g, const tc_motif* motif, int64_t del
   TC_TRY(check_index_header(g, plan, delta, d_index, st));
   const EdgeRec* rec = (const EdgeRec*)((const char*)d_index + kIndexHeaderBytes);
   return launch_features(g, rec, delta, d_feat, st);
+}
+
+tc_status tc_sample_features(const tc_graph* g, const tc_motif* motif, int64_t delta, const uint64_t* d_prefix,
+                             const void* d_index, uint64_t n_samples, uint64_t seed, uint64_t sample_offset,
+                             uint16_t* d_feat, void* stream) {
+  TC_TRY(check_graph(g));
+  Plan plan;
+  TC_TRY(plan_of(motif, &plan));
+  if (delta < 0) return set_error(TC_ERR_INVALID_ARG, "delta must be >= 0");
+  if (!d_prefix || !d_index || !d_feat) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
+  if (((uintptr_t)d_feat & 15) != 0) return set_error(TC_ERR_INVALID_ARG, "features must be 16-byte aligned");
+  cudaStream_t st = S(stream);
+  uint64_t* trace = nullptr;
+  SampleSums* sums = nullptr;
+  uint32_t* err = nullptr;
+  tc_status s = TC_OK;
+  cudaError_t e = pool_malloc(&trace, 32 * (n_samples ? n_samples : 1), st);
+  if (e == cudaSuccess) e = pool_malloc(&sums, sizeof(SampleSums) + 16, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(SampleSums) + 16, st);
+  if (e != cudaSuccess) s = cuda_status(e, "tc_sample_features allocation");
+  if (s == TC_OK) err = (uint32_t*)(sums + 1);
+  if (s == TC_OK && n_samples)
+    s = launch_sampler(g, plan, delta, d_prefix, d_index, n_samples, seed, sample_offset, trace, sums, st);
+  if (s == TC_OK) s = launch_sample_features(g, trace, n_samples, delta, d_feat, err, st);
+  SampleSums hs;
+  uint32_t herr = 0;
+  std::memset(&hs, 0, sizeof(hs));
+  if (s == TC_OK) {
+    e = cudaMemcpyAsync(&hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_status(e, "tc_sample_features");
+  }
+  if (trace) cudaFreeAsync(trace, st);
+  if (sums) cudaFreeAsync(sums, st);
+  if (s == TC_OK && (hs.err | herr)) s = device_status(hs.err | herr, "tc_sample_features");
+  return s;
 }
 
 tc_status tc_mlp_forward(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, uint64_t n,

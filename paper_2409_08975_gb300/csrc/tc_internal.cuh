@@ -313,6 +313,8 @@ tc_status launch_mlp_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t*
                           uint64_t n, float* grad, float* loss_sum, cudaStream_t st);
 tc_status mlp_adam(tc_mlp* M, float lr, cudaStream_t st);
 float* mlp_grad_buffer(tc_mlp* M);
+tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint64_t n, int64_t delta,
+                                 uint16_t* feat, uint32_t* d_err, cudaStream_t st);
 tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st);
 tc_status launch_proposal(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
                           float scale, uint16_t* h, uint64_t* q, cudaStream_t st);
@@ -353,6 +355,10 @@ int sample_batch_blocks_per_sm(int block_size);  // 0: unsupported block size
 tc_status launch_sample_batch(int block_size, uint32_t tile, unsigned blocks, const void* d_records,
                               const uint64_t* d_tile_begin, uint32_t nq, unsigned long long* d_next_item,
                               SampleSums* d_sums, cudaStream_t st);
+
+// Diagnostic timing of the sampling launches (tc_set_timing, tc_last_sampler_ms).
+void set_timing(bool on);
+float last_sampler_ms();
 
 // Host form of the estimate from the sums (tc_api.cu).
 void finish_estimate(tc_estimate* o);

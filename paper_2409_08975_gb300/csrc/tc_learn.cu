@@ -1,4 +1,4 @@
-// Learned proposal: edge features, a 12 -> 64 -> 64 -> 1 network (bf16
+// Learned proposal: edge features, a 16 -> 64 -> 64 -> 1 network (bf16
 // operands on the tensor cores through mma.sync m16n8k16, FP32 accumulation,
 // FP32 backward and Adam on FP32 master weights) and the proposal
 // h_e = max(1, floor(S (eps + g_e) + 1/2)), q_e = w_e h_e.  Sampling middle
@@ -16,7 +16,7 @@
 namespace tc {
 
 constexpr int kH = 64;      // hidden width
-constexpr int kF = 16;      // feature row stride (12 used)
+constexpr int kF = 16;      // feature row: 12 edge counts + 4 sample statistics
 constexpr int kNFeat = 12;
 constexpr int kNParams = kH * kF + kH + kH * kH + kH + kH + 1;  // 5313
 // flat parameter layout: W1[64][16], b1[64], W2[64][64], b2[64], W3[64], b3
@@ -106,6 +106,114 @@ __global__ void __launch_bounds__(256) k_features(const OutEdge* __restrict__ ou
     uint4* dst = reinterpret_cast<uint4*>(feat + i * kF);
     dst[0] = reinterpret_cast<const uint4*>(row)[0];
     dst[1] = reinterpret_cast<const uint4*>(row)[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sample-statistics features (columns 12..15 of a feature row) from n plain
+// samples (middle edge e_i, outcome X_i): with the time bucket
+// b(t) = (floor(t / D) - floor(t_min / D)) mod 2^32, D = max(delta, 1), and the
+// keys K1 = (u, v), K2 = (u, b(t)), K3 = (v, b(t)) of an edge, n_K counts the
+// samples whose middle edge has key K and s_K sums their X^2; prior = sum X^2
+// / n.  Columns: log1p((s_K + prior) / (n_K + 1)) for K1, K2, K3, and
+// log1p(n_K1).  Per key kind one open-addressing table (SplitMix64 finaliser,
+// linear probing, load at most 2/3) with exact integer counts and sums.
+
+constexpr uint64_t kTeEmpty = ~0ull;  // no real key: vertex ids are below 2^31
+
+struct TeTables {
+  unsigned long long* key;  // [3][cap]
+  unsigned long long* sum;  // [3][cap] sum of X^2
+  uint32_t* cnt;            // [3][cap]
+  uint64_t cap;             // power of two
+};
+
+__device__ __forceinline__ int64_t floor_div(int64_t a, int64_t d) {
+  const int64_t q = a / d;
+  return (a % d != 0 && a < 0) ? q - 1 : q;
+}
+
+__device__ __forceinline__ void te_keys(int32_t u, int32_t v, int64_t t, int64_t D, int64_t b0, uint64_t* k) {
+  const uint64_t b = ((uint64_t)floor_div(t, D) - (uint64_t)b0) & 0xFFFFFFFFull;
+  k[0] = ((uint64_t)(uint32_t)u << 32) | (uint32_t)v;
+  k[1] = ((uint64_t)(uint32_t)u << 32) | b;
+  k[2] = ((uint64_t)(uint32_t)v << 32) | b;
+}
+
+__global__ void __launch_bounds__(256) k_te_insert(const uint64_t* __restrict__ trace, uint64_t n,
+                                                   const OutEdge* __restrict__ out_e, uint64_t m, int64_t D,
+                                                   int64_t b0, TeTables T, unsigned long long* __restrict__ total,
+                                                   uint32_t* __restrict__ err) {
+  unsigned long long local = 0;
+  uint32_t bad = 0;
+  const uint64_t mask = T.cap - 1;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t e = trace[4 * i], X = trace[4 * i + 3];
+    if (e >= m) {
+      bad |= kErrBounds;
+      continue;
+    }
+    if (X >> 32) bad |= kErrOverflow;
+    const unsigned long long x2 = (unsigned long long)X * X;
+    local += x2;
+    const OutEdge r = out_e[e];
+    uint64_t k[3];
+    te_keys(r.src, r.dst, r.t, D, b0, k);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      unsigned long long* keys = T.key + c * T.cap;
+      uint64_t h = mix64(k[c]) & mask;
+      bool done = false;
+      for (uint64_t probe = 0; probe <= mask && !done; probe++) {
+        const unsigned long long prev = atomicCAS(keys + h, kTeEmpty, (unsigned long long)k[c]);
+        if (prev == kTeEmpty || prev == k[c]) {
+          atomicAdd(T.cnt + c * T.cap + h, 1u);
+          if (x2) atomicAdd(T.sum + c * T.cap + h, x2);
+          done = true;
+        }
+        h = (h + 1) & mask;
+      }
+      if (!done) bad |= kErrBounds;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(total, local);
+  if (bad) atomicOr(err, bad);
+}
+
+__global__ void __launch_bounds__(256) k_te_lookup(const OutEdge* __restrict__ out_e, uint64_t m, uint64_t n,
+                                                   int64_t D, int64_t b0, TeTables T,
+                                                   const unsigned long long* __restrict__ total,
+                                                   __nv_bfloat16* __restrict__ feat) {
+  const double prior = n ? (double)*total / (double)n : 0.0;
+  const uint64_t mask = T.cap - 1;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    const OutEdge r = out_e[i];
+    uint64_t k[3];
+    te_keys(r.src, r.dst, r.t, D, b0, k);
+    __align__(8) __nv_bfloat16 col[4];
+    uint32_t n1 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const unsigned long long* keys = T.key + c * T.cap;
+      uint64_t h = mix64(k[c]) & mask;
+      uint32_t cnt = 0;
+      unsigned long long s = 0;
+      for (uint64_t probe = 0; probe <= mask; probe++) {
+        const unsigned long long kk = keys[h];
+        if (kk == k[c]) {
+          cnt = T.cnt[c * T.cap + h];
+          s = T.sum[c * T.cap + h];
+          break;
+        }
+        if (kk == kTeEmpty) break;
+        h = (h + 1) & mask;
+      }
+      if (c == 0) n1 = cnt;
+      col[c] = __float2bfloat16_rn(log1pf((float)(((double)s + prior) / ((double)cnt + 1.0))));
+    }
+    col[3] = __float2bfloat16_rn(log1pf((float)n1));
+    *reinterpret_cast<uint2*>(feat + i * kF + kNFeat) = *reinterpret_cast<const uint2*>(col);
   }
 }
 
@@ -333,15 +441,18 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_mlp_grad(const float* __re
     TileAct T;
     tile_forward(S.net, x, T);
     const int ra = warp * 16 + g, rb = ra + 8;
+    // closure count y: loss y softplus(-z) if y > 0, else softplus(z) (the
+    // binary cross-entropy when y is 0 or 1); dloss/dz = -y (1 - g) or g
     const float ya = va ? labels[ia] : 0.f, yb = vb ? labels[ib] : 0.f;
-    const float dza = va ? (sigmoidf_(T.z3g) - ya) * inv_batch : 0.f;
-    const float dzb = vb ? (sigmoidf_(T.z3g8) - yb) * inv_batch : 0.f;
+    auto dloss = [](float z, float y) { return y > 0.f ? -y * (1.f - sigmoidf_(z)) : sigmoidf_(z); };
+    const float dza = va ? dloss(T.z3g, ya) * inv_batch : 0.f;
+    const float dzb = vb ? dloss(T.z3g8, yb) * inv_batch : 0.f;
     if (q == 0) {
       S.dz3[ra] = dza;
       S.dz3[rb] = dzb;
-      // softplus(z) - y z, stable
-      auto bce = [](float z, float y) { return fmaxf(z, 0.f) - y * z + log1pf(expf(-fabsf(z))); };
-      loss_acc += (va ? bce(T.z3g, ya) : 0.f) + (vb ? bce(T.z3g8, yb) : 0.f);
+      auto softplus = [](float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); };
+      auto loss = [&](float z, float y) { return y > 0.f ? y * softplus(-z) : softplus(z); };
+      loss_acc += (va ? loss(T.z3g, ya) : 0.f) + (vb ? loss(T.z3g8, yb) : 0.f);
     }
     // inputs and activations of the rows (bf16 values held as FP32)
     {
@@ -431,10 +542,6 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m1, float* __r
                        float* __restrict__ grad, float lr, float b1, float b2, float eps, float c1, float c2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParams) return;
-  if (i >= kOffW1 && i < kOffB1 && (i % kF) >= kNFeat) {  // padding columns stay zero
-    grad[i] = 0.f;
-    return;
-  }
   const float gr = grad[i];
   const float a = b1 * m1[i] + (1.f - b1) * gr;
   const float v = b2 * m2[i] + (1.f - b2) * gr * gr;
@@ -445,16 +552,11 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m1, float* __r
 }
 
 // Initial weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from Philox keyed by
-// (seed, parameter index); padding columns of W1 are zero.
+// (seed, parameter index).
 __global__ void k_mlp_init(float* __restrict__ p, uint64_t seed) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParams) return;
-  int fan_in = kH;
-  if (i < kOffW2) fan_in = kNFeat;
-  if (i >= kOffW1 && i < kOffB1 && (i % kF) >= kNFeat) {
-    p[i] = 0.f;
-    return;
-  }
+  const int fan_in = i < kOffW2 ? kF : kH;
   const uint4 r = philox4x32_10(make_uint4((uint32_t)i, 0u, 0x6d6c7000u, 0u),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
   const float u01 = (float)(r.x >> 8) * (1.0f / 16777216.0f);  // [0, 1)
@@ -462,12 +564,12 @@ __global__ void k_mlp_init(float* __restrict__ p, uint64_t seed) {
 }
 
 // Training rows from a trace of the plain sampler: row = middle edge,
-// label = [X > 0].
+// label = the closure count X.
 __global__ void k_trace_to_rows(const uint64_t* __restrict__ trace, uint64_t n, uint32_t* __restrict__ rows,
                                 float* __restrict__ labels) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     rows[i] = (uint32_t)trace[4 * i];
-    labels[i] = trace[4 * i + 3] > 0 ? 1.f : 0.f;
+    labels[i] = (float)trace[4 * i + 3];
   }
 }
 
@@ -537,6 +639,44 @@ tc_status launch_features(const tc_graph* g, const EdgeRec* rec, int64_t delta, 
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
+}
+
+tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint64_t n, int64_t delta,
+                                 uint16_t* feat, uint32_t* d_err, cudaStream_t st) {
+  const uint64_t m = (uint64_t)g->m;
+  if (!m) return TC_OK;
+  const int64_t D = delta > 0 ? delta : 1;
+  const int64_t b0 = g->tmin / D - ((g->tmin % D != 0 && g->tmin < 0) ? 1 : 0);
+  uint64_t cap = 1024;
+  while (cap < n + n / 2) cap <<= 1;  // load at most 2/3
+  TeTables T;
+  T.cap = cap;
+  char* buf = nullptr;
+  const size_t bytes = 3 * cap * (8 + 8 + 4) + 256;
+  TC_CUDA(pool_malloc(&buf, bytes, st));
+  T.key = (unsigned long long*)buf;
+  T.sum = T.key + 3 * cap;
+  T.cnt = (uint32_t*)(T.sum + 3 * cap);
+  unsigned long long* total = (unsigned long long*)(buf + 3 * cap * 20);
+  tc_status s = TC_OK;
+  cudaError_t e = cudaMemsetAsync(T.key, 0xFF, 3 * cap * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(T.sum, 0, 3 * cap * 12 + 256, st);
+  if (e != cudaSuccess) s = cuda_status(e, "cudaMemsetAsync");
+  if (s == TC_OK && n) {
+    k_te_insert<<<grid_cap(n, 256), 256, 0, st>>>(trace, n, g->out_e, m, D, b0, T, total, d_err);
+    TC_LAUNCHED(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_status(e, "k_te_insert");
+  }
+  if (s == TC_OK) {
+    k_te_lookup<<<grid_cap(m, 256), 256, 0, st>>>(g->out_e, m, n, D, b0, T, total,
+                                                   reinterpret_cast<__nv_bfloat16*>(feat));
+    TC_LAUNCHED(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_status(e, "k_te_lookup");
+  }
+  cudaFreeAsync(buf, st);
+  return s;
 }
 
 tc_status launch_mlp_forward(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, uint64_t n, float* out,

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "tc_internal.cuh"
 
@@ -697,16 +699,21 @@ __device__ __forceinline__ void tile_scatter(uint32_t lo, uint32_t hi, const uin
                                              uint32_t* warp_tot, uint32_t* stage, uint16_t* stage_k) {
   cnt[threadIdx.x] = 0;
   __syncthreads();
-  uint32_t key[kBucketItems], rank[kBucketItems];
+  // key (16 bits) and rank within the tile (< kBucketTile) packed in one
+  // register per item; the ids are loaded up front with the keys
+  uint32_t kr[kBucketItems], id[kBucketItems];
 #pragma unroll
   for (int it = 0; it < kBucketItems; it++) {
     const uint32_t j = lo + (uint32_t)it * 256 + threadIdx.x;
-    key[it] = 0xFFFFFFFFu;
+    kr[it] = 0xFFFFFFFFu;
     if (j < hi) {
-      key[it] = __ldg(keys_in + j);
-      rank[it] = atomicAdd(&cnt[(key[it] >> shift) & 255u], 1u);
+      kr[it] = (uint32_t)__ldg(keys_in + j) << 16;
+      id[it] = ids_in ? __ldg(ids_in + j) : j;
     }
   }
+#pragma unroll
+  for (int it = 0; it < kBucketItems; it++)
+    if (kr[it] != 0xFFFFFFFFu) kr[it] |= atomicAdd(&cnt[((kr[it] >> 16) >> shift) & 255u], 1u);
   __syncthreads();
   {  // exclusive scan of the tile's digit counts
     const uint32_t v = cnt[threadIdx.x];
@@ -726,11 +733,11 @@ __device__ __forceinline__ void tile_scatter(uint32_t lo, uint32_t hi, const uin
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < kBucketItems; it++) {
-    if (key[it] != 0xFFFFFFFFu) {
-      const uint32_t j = lo + (uint32_t)it * 256 + threadIdx.x;
-      const uint32_t p = start[(key[it] >> shift) & 255u] + rank[it];
-      stage[p] = ids_in ? __ldg(ids_in + j) : j;
-      stage_k[p] = (uint16_t)key[it];
+    if (kr[it] != 0xFFFFFFFFu) {
+      const uint32_t key = kr[it] >> 16;
+      const uint32_t p = start[(key >> shift) & 255u] + (kr[it] & 0xFFFFu);
+      stage[p] = id[it];
+      stage_k[p] = (uint16_t)key;
     }
   }
   __syncthreads();
@@ -745,7 +752,7 @@ __device__ __forceinline__ void tile_scatter(uint32_t lo, uint32_t hi, const uin
 }
 
 // Pass A scatter: tile t of the chunk, by the high byte.
-__global__ void __launch_bounds__(256) k_key_scatter_a(uint64_t count, const uint16_t* __restrict__ keys,
+__global__ void __launch_bounds__(256, 6) k_key_scatter_a(uint64_t count, const uint16_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ offs, uint32_t tiles,
                                                        uint16_t* __restrict__ keys_out,
                                                        uint32_t* __restrict__ ids_out) {
@@ -811,7 +818,7 @@ __global__ void __launch_bounds__(256) k_key_hist_b(const uint16_t* __restrict__
   hist[(uint64_t)info->tile_base[seg] * kBuckets + (uint64_t)threadIdx.x * info->ntiles[seg] + t] = cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(256) k_key_scatter_b(const uint16_t* __restrict__ keys,
+__global__ void __launch_bounds__(256, 5) k_key_scatter_b(const uint16_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ ids,
                                                        const SegInfo* __restrict__ info,
                                                        const uint32_t* __restrict__ offs,
@@ -904,6 +911,49 @@ tc_status sort_sample_ids(const IndexHeader* hdr, uint64_t seed, uint64_t first,
   return s;
 }
 
+// Diagnostic timing of the sampling launches alone (tc_set_timing): event
+// pairs around each launch, summed when the caller asks.
+static thread_local bool t_timing = false;
+static thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events;
+
+struct SamplerTimer {
+  cudaStream_t st;
+  explicit SamplerTimer(cudaStream_t s) : st(s) {
+    if (!t_timing) return;
+    for (auto& e : t_events) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    t_events.clear();
+  }
+  void start() {
+    if (!t_timing) return;
+    std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+    if (cudaEventCreate(&e.first) != cudaSuccess) return;
+    if (cudaEventCreate(&e.second) != cudaSuccess) {
+      cudaEventDestroy(e.first);
+      return;
+    }
+    cudaEventRecord(e.first, st);
+    t_events.push_back(e);
+  }
+  void stop() {
+    if (t_timing && !t_events.empty()) cudaEventRecord(t_events.back().second, st);
+  }
+};
+
+void set_timing(bool on) { t_timing = on; }
+
+float last_sampler_ms() {
+  float total = 0.f;
+  for (auto& e : t_events) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(e.second) == cudaSuccess && cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess)
+      total += ms;
+  }
+  return total;
+}
+
 tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
                          const void* index, uint64_t k, uint64_t seed, uint64_t offset, uint64_t* trace,
                          SampleSums* d_sums, cudaStream_t st, const void* qindex, const uint16_t* h,
@@ -966,7 +1016,13 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
     TC_CUDA(cudaGetLastError());
     return TC_OK;
   };
-  if (k < kSortedMinSamples) return run(nullptr, 0, k);
+  SamplerTimer timer(st);
+  if (k < kSortedMinSamples) {
+    timer.start();
+    tc_status s = run(nullptr, 0, k);
+    timer.stop();
+    return s;
+  }
   // samples in chunks; each chunk is put in key order first
   const uint64_t chunk = k < kChunkSamples ? k : kChunkSamples;
   const size_t sbytes = sort_scratch_bytes(chunk);
@@ -977,7 +1033,9 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   for (uint64_t base = 0; base < k && s == TC_OK; base += chunk) {
     const uint64_t count = (k - base) < chunk ? (k - base) : chunk;
     s = sort_sample_ids(v.hdr, seed, offset + base, count, buf, order, st);
+    timer.start();
     if (s == TC_OK) s = run(order, base, count);
+    timer.stop();
   }
   cudaFreeAsync(buf, st);
   return s;

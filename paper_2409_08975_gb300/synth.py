@@ -224,7 +224,15 @@ def large(seed=1005):
 BATCH_DELTAS = (600, 3600, 86400)
 
 
-def batch(seed=1003, n_small=64):
+def small(seed=1007):
+    """Profiling case: the mid generator at n = 5e5, m = 1e7 (graph and index
+    about 1 GB, several times L2), path+chord, delta = 3600, k = 1e7."""
+    g = chung_lu(500_000, 10_000_000, gamma=2.1, max_deg=5e4, multi_frac=0.30, seed=seed)
+    g.update({"name": "small", "motif": PATH_CHORD, "delta": 3600, "k": 10_000_000})
+    return g
+
+
+def batch(seed=1003, n_small=64, big_m=50_000_000, k_range=(1e6, 1e8)):
     """Batched queries: a 50M-edge graph of the mid generator (n = 2.5M)
     queried with all 24 time-rank orders of the directed 4-cycle at each
     delta in BATCH_DELTAS, plus n_small graphs of 1e4 - 2e6 edges
@@ -234,7 +242,8 @@ def batch(seed=1003, n_small=64):
     graph."""
     import itertools
     rng = np.random.default_rng(seed)
-    graphs = [chung_lu(2_500_000, 50_000_000, gamma=2.1, max_deg=2.5e5, multi_frac=0.30, seed=seed)]
+    graphs = [chung_lu(big_m // 20, big_m, gamma=2.1, max_deg=2.5e5 * big_m / 50_000_000, multi_frac=0.30,
+                       seed=seed)]
     sizes = np.exp(rng.uniform(np.log(1e4), np.log(2e6), n_small)).astype(np.int64)
     for i, m_i in enumerate(sizes):
         n_i = int(max(1000, m_i // 20))
@@ -242,7 +251,7 @@ def batch(seed=1003, n_small=64):
                                multi_frac=0.30, seed=seed + 1 + i))
     orders = [[C4[j] for j in p] for p in itertools.permutations(range(4))]
     def k_draw():
-        return int(np.exp(rng.uniform(np.log(1e6), np.log(1e8))))
+        return int(np.exp(rng.uniform(np.log(k_range[0]), np.log(k_range[1]))))
     queries = []
     for o, edges in enumerate(orders):
         for d in BATCH_DELTAS:
@@ -253,4 +262,13 @@ def batch(seed=1003, n_small=64):
             "k": sum(q[3] for q in queries)}
 
 
-CONFIGS = {"tiny": tiny, "mid": mid, "learned": learned, "large": large, "batch": batch}
+def batch_small(seed=1008):
+    """Profiling case of the batch: a 1e7-edge big graph, 8 small graphs,
+    1e5 - 1e7 samples per query."""
+    cfg = batch(seed=seed, n_small=8, big_m=10_000_000, k_range=(1e5, 1e7))
+    cfg["name"] = "batch_small"
+    return cfg
+
+
+CONFIGS = {"tiny": tiny, "mid": mid, "learned": learned, "large": large, "batch": batch, "small": small,
+           "batch_small": batch_small}

@@ -87,6 +87,7 @@ def lib():
             "tc_mlp_get_params": [vp, vp],
             "tc_mlp_set_params": [vp, vp],
             "tc_edge_features": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp],
+            "tc_sample_features": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, u64, u64, u64, vp, vp],
             "tc_mlp_forward": [vp, vp, vp, u64, vp, vp],
             "tc_mlp_grad": [vp, vp, vp, vp, u64, vp, ctypes.POINTER(ctypes.c_float), vp],
             "tc_mlp_train": [vp, vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, u64, u64, ctypes.c_uint32,
@@ -110,6 +111,10 @@ def lib():
             f.restype = st
         L.tc_kernel_launches.argtypes = []
         L.tc_kernel_launches.restype = ctypes.c_uint64
+        L.tc_set_timing.argtypes = [ctypes.c_int32]
+        L.tc_set_timing.restype = st
+        L.tc_last_sampler_ms.argtypes = []
+        L.tc_last_sampler_ms.restype = ctypes.c_float
         L.tc_last_error.argtypes = []
         L.tc_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -135,6 +140,14 @@ def _ptr(t):
 
 def tc_kernel_launches():
     return int(lib().tc_kernel_launches())
+
+
+def tc_set_timing(enabled):
+    _check(lib().tc_set_timing(1 if enabled else 0), "tc_set_timing")
+
+
+def tc_last_sampler_ms():
+    return float(lib().tc_last_sampler_ms())
 
 
 def make_motif(edges, anchor=None, window=WINDOW_STRICT):
@@ -370,6 +383,14 @@ def tc_edge_features(g, motif, delta, weights, stream=None):
     _check(lib().tc_edge_features(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.index), _ptr(feat),
                                   _stream(stream)), "tc_edge_features")
     return feat[:g.m].view(torch.bfloat16)
+
+
+def tc_sample_features(g, motif, delta, weights, feat, n_samples, seed=0, offset=0, stream=None):
+    """Fill columns 12..15 of feat (bf16 rows [m, 16]) from n_samples plain samples."""
+    _check(lib().tc_sample_features(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix),
+                                    _ptr(weights.index), int(n_samples), int(seed), int(offset), _ptr(feat),
+                                    _stream(stream)), "tc_sample_features")
+    return feat
 
 
 def tc_mlp_forward(mlp, feat, rows=None, n=None, stream=None):

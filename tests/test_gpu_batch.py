@@ -161,3 +161,22 @@ def test_batch_edge_cases(tc, graphs):
     res = tc.Batch(qs, block_size=256, tile=2048).run()
     _same(res[0], res[1])
     _same(res[1], res[2])
+
+
+def test_chunked_sort_beyond_2_28_samples(tc, graphs):
+    # above 2^28 samples the sample ids are put in key order chunk by chunk;
+    # the sums must equal those of the two ranges run separately, single
+    # call and batch alike
+    g = graphs[2][0]
+    chunk = 1 << 28
+    k = chunk + 123_457
+    mot = tc.make_motif(C4)
+    w = tc.tc_path_weights(g, mot, 10_000)
+    full = tc.tc_sample_estimate(g, mot, 10_000, w, k, 21, 5)
+    a = tc.tc_sample_estimate(g, mot, 10_000, w, chunk, 21, 5)
+    b = tc.tc_sample_estimate(g, mot, 10_000, w, k - chunk, 21, 5 + chunk)
+    for key in ("sum_x", "sum_x2", "hits", "checked"):
+        assert full[key] == a[key] + b[key], key
+    r = tc.Batch([(g, C4, 10_000, k, 21, 5), (g, C4, 10_000, 70_000, 21, 5)], block_size=256, tile=32768).run()
+    for key in ("sum_x", "sum_x2", "hits", "checked"):
+        assert r[0][key] == full[key], key

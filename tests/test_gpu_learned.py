@@ -71,10 +71,29 @@ def test_features_within_one_bf16_step(tc):
     assert (diff == 0).mean() > 0.999
 
 
+def test_sample_features_match_oracle(tc):
+    # columns 12..15 from 50,000 plain samples, against the oracle's
+    # statistics of the same samples, within one bf16 step
+    n, src, dst, t = _graph_bursty()
+    g, og, mot, plan, w, feat = _setup(tc, n, src, dst, t, CHORD, 3600)
+    before = _f32(feat)[:, :12].copy()
+    tc.tc_sample_features(g, mot, 3600, w, feat, 50_000, seed=11, offset=3)
+    got = _f32(feat)
+    assert (got[:, :12] == before).all()
+    pre = oracle.prefix_sum(oracle.path_weights(og, plan, 3600)["w"])
+    exp = L.features_bf16(L.edge_features(og, plan, 3600), L.sample_features(og, plan, 3600, pre, 50_000, 11, 3))
+    diff = np.abs(got[:, 12:] - exp[:, 12:])
+    step = np.maximum(np.abs(exp[:, 12:]), 1e-30) * 2.0 ** -7
+    assert (diff <= step).all()
+    assert (diff == 0).mean() > 0.999
+    assert (got[:, 15] > 0).any() and (got[:, 15] == 0).any()
+
+
 def test_forward_and_gradient_match_fp64(tc):
     import torch
     n, src, dst, t = _graph_bursty()
     g, og, mot, plan, w, feat = _setup(tc, n, src, dst, t, CHORD, 3600)
+    tc.tc_sample_features(g, mot, 3600, w, feat, 50_000, seed=11)
     params = L.init_params(np.random.default_rng(9))
     flat = L.pack(params).astype(np.float32)
     mlp = tc.MLP(seed=1)
@@ -88,7 +107,7 @@ def test_forward_and_gradient_match_fp64(tc):
     z_ref, _ = L.mlp_forward(p32, x)
     assert np.abs(z_gpu - z_ref).max() < 2e-2
     assert np.abs(z_gpu - z_ref).mean() < 1e-3
-    y = (rng.random(5000) < 0.2).astype(np.float32)
+    y = np.where(rng.random(5000) < 0.8, 0, rng.integers(1, 6, 5000)).astype(np.float32)  # closure counts
     grad, loss = tc.tc_mlp_grad(mlp, feat, _dev(rows, torch.int32), _dev(y, torch.float32))
     gref, lref = L.mlp_backward(p32, x, y.astype(np.float64))
     gref_flat = L.pack(gref)
@@ -99,17 +118,22 @@ def test_forward_and_gradient_match_fp64(tc):
 
 def _trained(tc, setup, n_train, seed=3):
     g, og, mot, plan, w, feat = setup
+    delta = 3600 if og.n > 100 else 10_000
+    tc.tc_sample_features(g, mot, delta, w, feat, n_train, seed=seed + 1000)  # samples disjoint from training
     mlp = tc.MLP(seed=seed)
-    first, last = tc.tc_mlp_train(mlp, g, mot, 3600 if og.n > 100 else 10_000, w, feat, n_train, seed=seed,
-                                  batch=4096, lr=3e-3)
+    first, last = tc.tc_mlp_train(mlp, g, mot, delta, w, feat, n_train, seed=seed, batch=4096, lr=3e-3)
     return mlp, first, last
 
 
 def test_training_lowers_loss(tc):
     n, src, dst, t = _graph_bursty()
     setup = _setup(tc, n, src, dst, t, CHORD, 3600)
+    w1_init = L.unpack(tc.MLP(seed=3).get_params())["W1"]
     mlp, first, last = _trained(tc, setup, 400_000)
     assert last < 0.8 * first
+    # every input column, the sample statistics included, is trained
+    w1 = L.unpack(mlp.get_params())["W1"]
+    assert (np.abs(w1 - w1_init).max(axis=0) > 1e-3).all()
 
 
 def test_proposal_prefix_and_sampler_bit_exact(tc):
@@ -142,6 +166,7 @@ def test_proposal_unbiased_over_1000_seeds(tc):
     src, dst, t = small_random_graph(77, 6, 60, 60, dup_frac=0.3)
     g, og, mot, plan, w, feat = setup = _setup(tc, 6, src, dst, t, C4, 20)
     mlp = tc.MLP(seed=4)
+    tc.tc_sample_features(g, mot, 20, w, feat, 20_000, seed=5)
     tc.tc_mlp_train(mlp, g, mot, 20, w, feat, 20_000, seed=4, batch=512, lr=1e-2)
     prop = tc.tc_proposal_weights(mlp, g, mot, 20, w, feat, eps=0.05, scale=64)
     h = prop.h.cpu().numpy().view(np.uint16)

@@ -46,26 +46,75 @@ def test_features_literal_counts():
         assert list(f[i]) == exp, i
 
 
+def test_sample_features_literal():
+    # the four sample statistics recomputed by plain loops over the trace
+    src, dst, t = small_random_graph(33, 7, 120, 90, dup_frac=0.3)
+    t = t - 40  # negative times exercise the floor of the time bucket
+    g = oracle.build_csr(7, src, dst, t)
+    plan = oracle.compile_motif(CHORD)
+    delta = 9
+    pre = oracle.prefix_sum(oracle.path_weights(g, plan, delta)["w"])
+    n, seed, off = 3000, 4, 17
+    f = L.sample_features(g, plan, delta, pre, n, seed, off)
+    _, tr = oracle.sample_run(g, plan, delta, pre, n, seed, off, trace=True)
+    D = max(delta, 1)
+    tmin = int(t.min())
+
+    def keys(i):
+        e = int(g.out_perm[i])
+        u, v, te = int(src[e]), int(dst[e]), int(t[e])
+        b = (te // D - tmin // D) % (1 << 32)
+        return [(u, v), (u, b), (v, b)]
+
+    stats = [{}, {}, {}]
+    tot = 0
+    for i2, _, _, X in tr.astype(np.int64).tolist():
+        tot += X * X
+        for c, k in enumerate(keys(i2)):
+            cnt, s2 = stats[c].get(k, (0, 0))
+            stats[c][k] = (cnt + 1, s2 + X * X)
+    prior = tot / n
+    for i in range(g.m):
+        for c, k in enumerate(keys(i)):
+            cnt, s2 = stats[c].get(k, (0, 0))
+            assert f[i, c] == pytest.approx((s2 + prior) / (cnt + 1), rel=1e-15)
+            if c == 0:
+                assert f[i, 3] == cnt
+    assert (f[:, 3] > 0).any() and (f[:, 3] == 0).any()
+
+
+def test_closure_loss_is_bce_on_binary_labels_and_its_minimiser():
+    rng = np.random.default_rng(8)
+    z = rng.normal(0, 3, 500)
+    y = (rng.random(500) < 0.4).astype(np.float64)
+    g = 1.0 / (1.0 + np.exp(-z))
+    textbook = np.mean(-y * np.log(g) - (1 - y) * np.log(1 - g))
+    assert L.closure_loss(z, y) == pytest.approx(textbook, rel=1e-12)
+    # one shared logit: the loss is minimised at g = E[y] / (E[y] + P(y = 0))
+    y = rng.choice([0, 0, 0, 1, 2, 7], 4000).astype(np.float64)
+    target = y.mean() / (y.mean() + (y == 0).mean())
+    zs = np.linspace(-4, 4, 801)
+    best = zs[int(np.argmin([L.closure_loss(np.full(len(y), zz), y) for zz in zs]))]
+    assert abs(1.0 / (1.0 + np.exp(-best)) - target) < 0.005
+
+
 def test_backward_matches_finite_differences():
     rng = np.random.default_rng(5)
     params = L.init_params(rng)
-    x = np.zeros((40, 16))
-    x[:, :12] = rng.uniform(0, 3, (40, 12))
-    y = (rng.random(40) < 0.3).astype(np.float64)
+    x = rng.uniform(0, 3, (40, 16))  # 12 edge counts and 4 sample statistics
+    y = np.where(rng.random(40) < 0.6, 0.0, rng.integers(1, 6, 40)).astype(np.float64)  # closure counts
     grads, _ = L.mlp_backward(params, x, y, round_acts=False, quantized=False)
     h = 1e-6
     for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
         p = params[name]
         flat = p.reshape(-1)
         idx = rng.choice(flat.size, size=min(12, flat.size), replace=False)
-        if name == "W1":
-            idx = [i for i in idx if i % 16 < 12] or [0]
         for j in idx:
             old = flat[j]
             flat[j] = old + h
-            lp = L.bce_loss(L.mlp_forward(params, x, False, False)[0], y)
+            lp = L.closure_loss(L.mlp_forward(params, x, False, False)[0], y)
             flat[j] = old - h
-            lm = L.bce_loss(L.mlp_forward(params, x, False, False)[0], y)
+            lm = L.closure_loss(L.mlp_forward(params, x, False, False)[0], y)
             flat[j] = old
             fd = (lp - lm) / (2 * h)
             an = grads[name].reshape(-1)[j]
