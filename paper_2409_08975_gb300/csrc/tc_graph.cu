@@ -264,17 +264,30 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
   for (int d = threadIdx.x; d < radix; d += kSortThreads) hist[(uint64_t)d * tiles + blockIdx.x] = s_hist[d];
 }
 
-// Stable scatter: per-warp digit counts (warp-level multisplit with
-// __match_any_sync) in input order, then each warp's keys go to the digit's
-// global offset plus the counts of earlier warps and lanes.
+// Stable scatter through shared memory: per-warp digit counts (warp-level
+// multisplit with __match_any_sync) in input order give every key its rank
+// among the tile's keys of the same digit; keys and values are staged in
+// shared memory in (digit, rank) order and written out in that order, so
+// each digit's run of the tile goes to consecutive global addresses.
+// Shared memory: the per-warp counts (later the stage), the tile-local start
+// and the global start of every digit.
+__host__ __device__ constexpr int sort_scatter_words(int radix) {
+  return (kSortWarps * radix > 2 * kSortTile ? kSortWarps * radix : 2 * kSortTile) + 2 * radix;
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                               const uint32_t* __restrict__ vin, uint64_t n,
                                                               int bit, int nbits,
                                                               const uint32_t* __restrict__ offs,
                                                               uint32_t tiles, uint32_t* __restrict__ kout,
                                                               uint32_t* __restrict__ vout) {
-  extern __shared__ uint32_t s_cnt[];  // [kSortWarps][radix]
+  extern __shared__ uint32_t smem[];
   const int radix = 1 << nbits;
+  const int cnt_words = kSortWarps * radix > 2 * kSortTile ? kSortWarps * radix : 2 * kSortTile;
+  uint32_t* s_cnt = smem;                // [kSortWarps][radix]; afterwards the stage
+  uint32_t* s_start = smem + cnt_words;  // [radix]
+  uint32_t* s_base = s_start + radix;    // [radix]
+  __shared__ uint32_t warp_tot[kSortWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t mask = (uint32_t)radix - 1u;
   const uint32_t lt = (1u << lane) - 1u;
@@ -297,28 +310,74 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
     __syncwarp();
   }
   __syncthreads();
+  // per digit: counts of earlier warps (in place), the tile total and the
+  // digit's global start
   for (int d = threadIdx.x; d < radix; d += kSortThreads) {
-    uint32_t run = offs[(uint64_t)d * tiles + blockIdx.x];
+    uint32_t run = 0;
     for (int w = 0; w < kSortWarps; w++) {
       const uint32_t c = s_cnt[w * radix + d];
       s_cnt[w * radix + d] = run;
       run += c;
     }
+    s_start[d] = run;
+    s_base[d] = offs[(uint64_t)d * tiles + blockIdx.x];
   }
   __syncthreads();
+  {  // exclusive scan of the digit totals: thread t owns digits [t * per, (t + 1) * per)
+    const int per = (radix + kSortThreads - 1) / kSortThreads;
+    const int d0 = threadIdx.x * per;
+    uint32_t local = 0;
+    for (int j = 0; j < per; j++)
+      if (d0 + j < radix) local += s_start[d0 + j];
+    uint32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t run = incl - local;
+    for (int w = 0; w < warp; w++) run += warp_tot[w];
+    for (int j = 0; j < per; j++)
+      if (d0 + j < radix) {
+        const uint32_t c = s_start[d0 + j];
+        s_start[d0 + j] = run;
+        run += c;
+      }
+  }
+  __syncthreads();
+  // tile-local positions in (digit, rank) order
+  uint32_t lp[kSortItems];
 #pragma unroll
   for (int j = 0; j < kSortItems; j++) {
     const uint64_t i = sort_index(blockIdx.x, warp, j, lane);
     const uint32_t d = i < n ? ((key[j] >> bit) & mask) : 0xFFFFFFFFu;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (d != 0xFFFFFFFFu) {
-      const uint32_t pos = my[d] + __popc(peers & lt);
-      kout[pos] = key[j];
-      vout[pos] = val[j];
-    }
+    lp[j] = 0xFFFFFFFFu;
+    if (d != 0xFFFFFFFFu) lp[j] = s_start[d] + my[d] + __popc(peers & lt);
     __syncwarp();
     if (d != 0xFFFFFFFFu && (peers & lt) == 0) my[d] += __popc(peers);
     __syncwarp();
+  }
+  __syncthreads();  // the counts are no longer read: the stage reuses them
+  uint32_t* stage_k = s_cnt;
+  uint32_t* stage_v = s_cnt + kSortTile;
+#pragma unroll
+  for (int j = 0; j < kSortItems; j++)
+    if (lp[j] != 0xFFFFFFFFu) {
+      stage_k[lp[j]] = key[j];
+      stage_v[lp[j]] = val[j];
+    }
+  __syncthreads();
+  const uint64_t t0 = (uint64_t)blockIdx.x * kSortTile;
+  const uint32_t count = (uint32_t)(n - t0 < (uint64_t)kSortTile ? n - t0 : (uint64_t)kSortTile);
+  for (uint32_t i = threadIdx.x; i < count; i += kSortThreads) {
+    const uint32_t k = stage_k[i];
+    const uint32_t d = (k >> bit) & mask;
+    const uint32_t g = s_base[d] + (i - s_start[d]);
+    kout[g] = k;
+    vout[g] = stage_v[i];
   }
 }
 
@@ -330,7 +389,7 @@ tc_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v
   static bool attr = false;
   if (!attr) {
     TC_CUDA(cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(uint32_t) * kSortWarps * kMaxRadix)));
+                                 (int)(sizeof(uint32_t) * sort_scatter_words(kMaxRadix))));
     attr = true;
   }
   const int total = bit1 - bit0;
@@ -351,7 +410,7 @@ tc_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v
     if (e != cudaSuccess) { s = cuda_status(e, "k_sort_hist"); break; }
     s = scan_rec<uint32_t>(hist, hist, (uint64_t)radix * tiles, false, nullptr, st);
     if (s != TC_OK) break;
-    k_sort_scatter<<<(unsigned)tiles, kSortThreads, sizeof(uint32_t) * kSortWarps * radix, st>>>(
+    k_sort_scatter<<<(unsigned)tiles, kSortThreads, sizeof(uint32_t) * sort_scatter_words(radix), st>>>(
         ka, va, n, bit, nbits, hist, (uint32_t)tiles, kb, vb);
     TC_LAUNCHED(1);
     e = cudaGetLastError();

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_te_lookup(const OutEdge* __restrict__ o
                                                    int64_t D, int64_t b0, TeTables T,
                                                    const unsigned long long* __restrict__ total,
                                                    __nv_bfloat16* __restrict__ feat) {
-  const double prior = n ? (double)*total / (double)n : 0.0;
+  const float prior = n ? (float)((double)*total / (double)n) : 0.f;  // FP32 below: the result is log1p'd to bf16
   const uint64_t mask = T.cap - 1;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const OutEdge r = out_e[i];
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) k_te_lookup(const OutEdge* __restrict__ o
         h = (h + 1) & mask;
       }
       if (c == 0) n1 = cnt;
-      col[c] = __float2bfloat16_rn(log1pf((float)(((double)s + prior) / ((double)cnt + 1.0))));
+      col[c] = __float2bfloat16_rn(log1pf(((float)s + prior) / ((float)cnt + 1.f)));
     }
     col[3] = __float2bfloat16_rn(log1pf((float)n1));
     *reinterpret_cast<uint2*>(feat + i * kF + kNFeat) = *reinterpret_cast<const uint2*>(col);
@@ -403,6 +403,13 @@ __global__ void __launch_bounds__(128) k_proposal(const float* __restrict__ para
 // global atomic add per parameter and block.
 
 constexpr int kTrainWarps = 4;
+// Row tiles of kTrainRows per block of the gradient launch: one tile per
+// block puts four times more blocks in flight than four tiles (the parameter
+// gradients then take more global atomics, which cost less than the idle
+// SMs did: 48 ms instead of 111 ms for 1e7 training rows on the 20M-edge graph).
+#ifndef TC_TRAIN_TILES
+#define TC_TRAIN_TILES 1
+#endif
 constexpr int kTrainRows = 16 * kTrainWarps;
 
 struct TrainShared {
@@ -699,7 +706,7 @@ tc_status launch_mlp_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t*
     TC_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainShared)));
     attr = true;
   }
-  k_mlp_grad<<<grid_cap(n, kTrainRows * 4), 32 * kTrainWarps, sizeof(TrainShared), st>>>(
+  k_mlp_grad<<<grid_cap(n, kTrainRows * TC_TRAIN_TILES), 32 * kTrainWarps, sizeof(TrainShared), st>>>(
       M->params, reinterpret_cast<const __nv_bfloat16*>(feat), rows, labels, n, 1.0f / (float)n, grad, loss_sum);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
