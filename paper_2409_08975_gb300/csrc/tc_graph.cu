@@ -492,16 +492,19 @@ __global__ void k_offsets(const uint32_t* __restrict__ sorted, uint64_t len, int
 }
 
 __global__ void k_fill_out(const OutEdge* __restrict__ pack, const uint32_t* __restrict__ perm, uint64_t m,
-                           OutEdge* out_e, uint32_t* canon) {
+                           OutEdge* out_e, uint32_t* canon, int64_t tmin, uint32_t* __restrict__ out_t32) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t e = perm[i];
-    out_e[i] = pack[e];
+    const OutEdge r = pack[e];
+    out_e[i] = r;
     canon[e] = (uint32_t)i;
+    if (out_t32) out_t32[i] = (uint32_t)((uint64_t)r.t - (uint64_t)tmin);
   }
 }
 
 __global__ void k_fill_in(const OutEdge* __restrict__ pack, const uint32_t* __restrict__ perm,
-                          const uint32_t* __restrict__ canon, uint64_t m, InEdge* in_e, uint32_t* in_eid) {
+                          const uint32_t* __restrict__ canon, uint64_t m, InEdge* in_e, uint32_t* in_eid,
+                          int64_t tmin, uint32_t* __restrict__ in_t32) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t e = perm[i];
     const OutEdge r = pack[e];
@@ -511,6 +514,7 @@ __global__ void k_fill_in(const OutEdge* __restrict__ pack, const uint32_t* __re
     q.t = r.t;
     in_e[i] = q;
     in_eid[i] = canon[e];
+    if (in_t32) in_t32[i] = (uint32_t)((uint64_t)r.t - (uint64_t)tmin);
   }
 }
 
@@ -659,6 +663,11 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   TRY_S(dmalloc(&canon, M, st));
   const unsigned gr = grid_for(M);
   const uint64_t span = (uint64_t)g->tmax - (uint64_t)g->tmin;
+  g->out_t32 = g->in_t32 = nullptr;
+  if (M && span <= 0xFFFFFFFFull) {  // the list times as 32-bit offsets from tmin
+    TRY_S(dmalloc(&g->out_t32, M, st));
+    TRY_S(dmalloc(&g->in_t32, M, st));
+  }
   const int tbits = bitlen64(span);
   const int vbits = bitlen64((uint64_t)(n > 0 ? n - 1 : 0));
 
@@ -683,7 +692,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
     TC_LAUNCHED(1);
     TRY_C(cudaMemcpyAsync(va, permT, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
-    k_fill_out<<<gr, 256, 0, st>>>(pack, va, M, g->out_e, canon);
+    k_fill_out<<<gr, 256, 0, st>>>(pack, va, M, g->out_e, canon, g->tmin, g->out_t32);
     TC_LAUNCHED(1);
     TRY_C(cudaGetLastError(), "k_fill_out");
     TRY_C(cudaMemcpyAsync(g->perm, va, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
@@ -698,7 +707,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
     TC_LAUNCHED(1);
     TRY_C(cudaMemcpyAsync(va, permT, sizeof(uint32_t) * M, cudaMemcpyDeviceToDevice, st), "memcpy");
     TRY_S(radix_sort_pairs(ka, va, kb, vb, M, 0, vbits, st));
-    k_fill_in<<<gr, 256, 0, st>>>(pack, va, canon, M, g->in_e, g->in_eid);
+    k_fill_in<<<gr, 256, 0, st>>>(pack, va, canon, M, g->in_e, g->in_eid, g->tmin, g->in_t32);
     TC_LAUNCHED(1);
     TRY_C(cudaGetLastError(), "k_fill_in");
   }

@@ -130,6 +130,11 @@ struct tc_graph {
   uint32_t* pair_eid;
   tc::PairSlot* pair_hash;  // open addressing, linear probing, load <= 1/2
   uint64_t hash_mask;       // capacity - 1 (capacity a power of two)
+  // times of the out- and in-lists as t - tmin in 32 bits, when the time
+  // span fits (else NULL): the window searches probe 4-byte entries, eight
+  // per 32-byte sector
+  uint32_t* out_t32;
+  uint32_t* in_t32;
 };
 
 namespace tc {
@@ -239,32 +244,29 @@ __device__ __forceinline__ uint32_t search_time(uint32_t lo, uint32_t hi, int64_
 // Window of x's list (alpha < 0: in-list, else out-list) around time t
 // (beta < 0: before, else after; strict or closed at t) as positions [lo, hi).
 // The two bounds are searched independently so that their loads overlap.
+// Compact: the list times are read from the 32-bit arrays (t - tmin).
+template <bool Compact>
 __device__ __forceinline__ void window_range(const OutEdge* __restrict__ out_e,
                                              const uint32_t* __restrict__ out_off,
                                              const InEdge* __restrict__ in_e,
-                                             const uint32_t* __restrict__ in_off, int alpha, int beta,
-                                             int closed, int32_t x, int64_t t, int64_t delta,
+                                             const uint32_t* __restrict__ in_off,
+                                             const uint32_t* __restrict__ out_t32,
+                                             const uint32_t* __restrict__ in_t32, int64_t tmin, int alpha,
+                                             int beta, int closed, int32_t x, int64_t t, int64_t delta,
                                              uint32_t* lo, uint32_t* hi) {
-  if (alpha < 0) {
-    const uint32_t a = __ldg(in_off + x), b = __ldg(in_off + x + 1);
-    auto tt = [&](uint32_t p) { return in_e[p].t; };
-    if (beta < 0) {
-      *lo = search_time<true>(a, b, sat_sub(t, delta), tt);
-      *hi = closed ? search_time<false>(a, b, t, tt) : search_time<true>(a, b, t, tt);
-    } else {
-      *lo = closed ? search_time<true>(a, b, t, tt) : search_time<false>(a, b, t, tt);
-      *hi = search_time<false>(a, b, sat_add(t, delta), tt);
-    }
+  const bool in = alpha < 0;
+  const uint32_t a = __ldg((in ? in_off : out_off) + x), b = __ldg((in ? in_off : out_off) + x + 1);
+  const uint32_t* t32 = in ? in_t32 : out_t32;
+  auto tt = [&](uint32_t p) -> int64_t {
+    if (Compact) return (int64_t)__ldg(t32 + p) + tmin;
+    return in ? in_e[p].t : out_e[p].t;
+  };
+  if (beta < 0) {
+    *lo = search_time<true>(a, b, sat_sub(t, delta), tt);
+    *hi = closed ? search_time<false>(a, b, t, tt) : search_time<true>(a, b, t, tt);
   } else {
-    const uint32_t a = __ldg(out_off + x), b = __ldg(out_off + x + 1);
-    auto tt = [&](uint32_t p) { return out_e[p].t; };
-    if (beta < 0) {
-      *lo = search_time<true>(a, b, sat_sub(t, delta), tt);
-      *hi = closed ? search_time<false>(a, b, t, tt) : search_time<true>(a, b, t, tt);
-    } else {
-      *lo = closed ? search_time<true>(a, b, t, tt) : search_time<false>(a, b, t, tt);
-      *hi = search_time<false>(a, b, sat_add(t, delta), tt);
-    }
+    *lo = closed ? search_time<true>(a, b, t, tt) : search_time<false>(a, b, t, tt);
+    *hi = search_time<false>(a, b, sat_add(t, delta), tt);
   }
 }
 

@@ -26,16 +26,24 @@ namespace tc {
 
 // Edges per thread of the weight kernels, processed together so that the
 // loads of their independent searches overlap.
+// Window searches on the 32-bit time arrays when the graph has them.
+#ifndef TC_COMPACT_TIMES
+#define TC_COMPACT_TIMES 1
+#endif
+
 #ifndef TC_WEIGHTS_ILP
 #define TC_WEIGHTS_ILP 2
 #endif
 
+template <bool Compact>
 __global__ void __launch_bounds__(256) k_weights_dst(const OutEdge* __restrict__ out_e,
                                                      const uint32_t* __restrict__ out_off,
                                                      const InEdge* __restrict__ in_e,
                                                      const uint32_t* __restrict__ in_off,
-                                                     const uint32_t* __restrict__ in_eid, uint64_t m, Plan plan,
-                                                     int64_t delta, uint64_t* __restrict__ w) {
+                                                     const uint32_t* __restrict__ in_eid,
+                                                     const uint32_t* __restrict__ out_t32,
+                                                     const uint32_t* __restrict__ in_t32, int64_t tmin, uint64_t m,
+                                                     Plan plan, int64_t delta, uint64_t* __restrict__ w) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < m; p0 += stride * TC_WEIGHTS_ILP) {
     InEdge e[TC_WEIGHTS_ILP];
@@ -49,8 +57,8 @@ __global__ void __launch_bounds__(256) k_weights_dst(const OutEdge* __restrict__
     for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
       const uint64_t p = p0 + j * stride;
       if (p < m)
-        window_range(out_e, out_off, in_e, in_off, plan.alpha3, plan.beta3, plan.closed, e[j].dst, e[j].t, delta,
-                     &lo3[j], &hi3[j]);
+        window_range<Compact>(out_e, out_off, in_e, in_off, out_t32, in_t32, tmin, plan.alpha3, plan.beta3,
+                              plan.closed, e[j].dst, e[j].t, delta, &lo3[j], &hi3[j]);
     }
 #pragma unroll
     for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
@@ -60,11 +68,14 @@ __global__ void __launch_bounds__(256) k_weights_dst(const OutEdge* __restrict__
   }
 }
 
+template <bool Compact>
 __global__ void __launch_bounds__(256) k_weights_src(const OutEdge* __restrict__ out_e,
                                                      const uint32_t* __restrict__ out_off,
                                                      const InEdge* __restrict__ in_e,
-                                                     const uint32_t* __restrict__ in_off, uint64_t m, Plan plan,
-                                                     int64_t delta, EdgeRec* __restrict__ rec,
+                                                     const uint32_t* __restrict__ in_off,
+                                                     const uint32_t* __restrict__ out_t32,
+                                                     const uint32_t* __restrict__ in_t32, int64_t tmin, uint64_t m,
+                                                     Plan plan, int64_t delta, EdgeRec* __restrict__ rec,
                                                      uint64_t* __restrict__ w) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += stride * TC_WEIGHTS_ILP) {
@@ -81,8 +92,8 @@ __global__ void __launch_bounds__(256) k_weights_src(const OutEdge* __restrict__
       lo1[j] = 0;  // a wedge at v: the u side is the one-position dummy
       hi1[j] = 1;
       if (i < m && plan.alpha1 != 0)
-        window_range(out_e, out_off, in_e, in_off, plan.alpha1, plan.beta1, plan.closed, e[j].src, e[j].t, delta,
-                     &lo1[j], &hi1[j]);
+        window_range<Compact>(out_e, out_off, in_e, in_off, out_t32, in_t32, tmin, plan.alpha1, plan.beta1,
+                              plan.closed, e[j].src, e[j].t, delta, &lo1[j], &hi1[j]);
     }
 #pragma unroll
     for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
@@ -108,12 +119,23 @@ tc_status launch_weights(const tc_graph* g, const Plan& plan, int64_t delta, Edg
   const uint64_t m = (uint64_t)g->m;
   if (m == 0) return TC_OK;
   const unsigned blocks = (unsigned)((m + 256 * TC_WEIGHTS_ILP - 1) / (256 * TC_WEIGHTS_ILP));
+  const bool compact = TC_COMPACT_TIMES && g->out_t32 && g->in_t32;
   if (plan.alpha3 != 0) {  // a wedge at u has no v-side window
-    k_weights_dst<<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->in_eid, m, plan, delta, w);
+    if (compact)
+      k_weights_dst<true><<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->in_eid, g->out_t32,
+                                                  g->in_t32, g->tmin, m, plan, delta, w);
+    else
+      k_weights_dst<false><<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->in_eid, nullptr,
+                                                   nullptr, 0, m, plan, delta, w);
     TC_LAUNCHED(1);
     TC_CUDA(cudaGetLastError());
   }
-  k_weights_src<<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, m, plan, delta, rec, w);
+  if (compact)
+    k_weights_src<true><<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->out_t32, g->in_t32,
+                                                g->tmin, m, plan, delta, rec, w);
+  else
+    k_weights_src<false><<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, nullptr, nullptr, 0, m,
+                                                 plan, delta, rec, w);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;

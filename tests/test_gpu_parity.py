@@ -327,3 +327,20 @@ def test_host_entry_point_matches_device_path(tc):
     a = tc.tc_sample_estimate(g, mot, 10_000, w, 200_000, 3, 0)
     b = tc.tc_estimate_from_host(cfg["n"], cfg["src"], cfg["dst"], cfg["t"], mot, 10_000, 200_000, 3)
     assert a == b
+
+
+def test_weights_with_times_beyond_32_bits(tc):
+    # a time span of 2^40 s: the window searches read the 64-bit list times
+    # (the 32-bit offsets are only built when the span fits)
+    src, dst, t = small_random_graph(19, 9, 400, 300, dup_frac=0.3)
+    t = t * (1 << 32) - (1 << 40)
+    g, og = _build_both(tc, 9, src, dst, t)
+    for edges in (C4, CHORD, LATE_MID, [(0, 1), (0, 2), (1, 2)]):
+        for window in (0, 1):
+            plan = oracle.compile_motif(edges, closed=bool(window))
+            mot = tc.make_motif(edges, window=window)
+            for delta in (0, 3 << 32, 40 << 32):
+                ow = oracle.path_weights(og, plan, delta)
+                w = tc.tc_path_weights(g, mot, delta, want_w=True)
+                assert (_u64(w.w)[:og.m] == ow["w"]).all(), (edges, window, delta)
+                assert w.W == int(oracle.prefix_sum(ow["w"])[-1])
