@@ -253,7 +253,7 @@ tc_status compile_plan_checked(const tc_motif* motif, Plan* p) { return plan_of(
 
 static void free_graph_arrays(tc_graph* g) {
   void* ps[] = {g->out_off, g->out_e, g->perm, g->in_off, g->in_e, g->in_eid, g->pair_off,
-                g->pair_dst, g->pair_eoff, g->pair_t, g->pair_eid, g->pair_hash, g->out_t32, g->in_t32};
+                g->pair_dst, g->pair_eoff, g->pair_t, g->pair_eid, g->pair_hash, g->out_t32, g->in_t32, g->pair_t32};
   for (void* p : ps)
     if (p) cudaFree(p);
 }

@@ -521,13 +521,15 @@ __global__ void k_fill_in(const OutEdge* __restrict__ pack, const uint32_t* __re
 // pair order: destination, time and canonical id of each position
 __global__ void k_pair_gather(const OutEdge* __restrict__ pack, const uint32_t* __restrict__ perm,
                               const uint32_t* __restrict__ canon, uint64_t m, int32_t* __restrict__ pdst,
-                              int64_t* __restrict__ pair_t, uint32_t* __restrict__ pair_eid) {
+                              int64_t* __restrict__ pair_t, uint32_t* __restrict__ pair_eid, int64_t tmin,
+                              uint32_t* __restrict__ pair_t32) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t e = perm[i];
     const OutEdge r = pack[e];
     pdst[i] = r.dst;
     pair_t[i] = r.t;
     pair_eid[i] = canon[e];
+    if (pair_t32) pair_t32[i] = (uint32_t)((uint64_t)r.t - (uint64_t)tmin);
   }
 }
 
@@ -663,10 +665,11 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   TRY_S(dmalloc(&canon, M, st));
   const unsigned gr = grid_for(M);
   const uint64_t span = (uint64_t)g->tmax - (uint64_t)g->tmin;
-  g->out_t32 = g->in_t32 = nullptr;
+  g->out_t32 = g->in_t32 = g->pair_t32 = nullptr;
   if (M && span <= 0xFFFFFFFFull) {  // the list times as 32-bit offsets from tmin
     TRY_S(dmalloc(&g->out_t32, M, st));
     TRY_S(dmalloc(&g->in_t32, M, st));
+    TRY_S(dmalloc(&g->pair_t32, M, st));
   }
   const int tbits = bitlen64(span);
   const int vbits = bitlen64((uint64_t)(n > 0 ? n - 1 : 0));
@@ -724,7 +727,7 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
     TRY_S(dmalloc(&flags, M, st));
     TRY_S(dmalloc(&pidx, M + 1, st));
     TRY_S(dmalloc(&pdst, M, st));
-    k_pair_gather<<<gr, 256, 0, st>>>(pack, va, canon, M, pdst, g->pair_t, g->pair_eid);
+    k_pair_gather<<<gr, 256, 0, st>>>(pack, va, canon, M, pdst, g->pair_t, g->pair_eid, g->tmin, g->pair_t32);
     TC_LAUNCHED(1);
     TRY_C(cudaGetLastError(), "k_pair_gather");
     k_pair_flags<<<gr, 256, 0, st>>>(ka, pdst, M, flags);

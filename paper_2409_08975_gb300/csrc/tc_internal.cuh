@@ -135,6 +135,7 @@ struct tc_graph {
   // per 32-byte sector
   uint32_t* out_t32;
   uint32_t* in_t32;
+  uint32_t* pair_t32;  // pair-list times as t - tmin (same condition)
 };
 
 namespace tc {

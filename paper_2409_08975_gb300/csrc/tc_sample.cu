@@ -26,6 +26,11 @@ namespace tc {
 
 // Edges per thread of the weight kernels, processed together so that the
 // loads of their independent searches overlap.
+// Pair-list searches of the sampler on the 32-bit times when the graph has them.
+#ifndef TC_COMPACT_PAIRS
+#define TC_COMPACT_PAIRS 1
+#endif
+
 // Window searches on the 32-bit time arrays when the graph has them.
 #ifndef TC_COMPACT_TIMES
 #define TC_COMPACT_TIMES 1
@@ -277,6 +282,8 @@ struct SamplerArgs {
   const PairSlot* pair_hash;
   uint64_t hash_mask;
   const int64_t* pair_t;
+  const uint32_t* pair_t32;  // pair-list times as t - tmin, or NULL
+  int64_t tmin;
   const uint64_t* prefix;
   const IndexHeader* hdr;
   const EdgeRec* rec;
@@ -319,9 +326,15 @@ __device__ __forceinline__ bool pair_window(const SamplerArgs& A, int32_t x, int
     h = (h + 1) & A.hash_mask;
   }
   if (!found) return false;
-  auto tt = [&](uint32_t p) { return __ldg(A.pair_t + p); };
-  *a = search_time<false>(s, e, tlo, tt);
-  *b = hi_incl ? search_time<false>(*a, e, thi, tt) : search_time<true>(*a, e, thi, tt);
+  if (A.pair_t32) {  // 4-byte entries, eight per sector
+    auto tt = [&](uint32_t p) { return (int64_t)__ldg(A.pair_t32 + p) + A.tmin; };
+    *a = search_time<false>(s, e, tlo, tt);
+    *b = hi_incl ? search_time<false>(*a, e, thi, tt) : search_time<true>(*a, e, thi, tt);
+  } else {
+    auto tt = [&](uint32_t p) { return __ldg(A.pair_t + p); };
+    *a = search_time<false>(s, e, tlo, tt);
+    *b = hi_incl ? search_time<false>(*a, e, thi, tt) : search_time<true>(*a, e, thi, tt);
+  }
   return true;
 }
 
@@ -994,6 +1007,8 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   A.pair_hash = g->pair_hash;
   A.hash_mask = g->hash_mask;
   A.pair_t = g->pair_t;
+  A.pair_t32 = TC_COMPACT_PAIRS ? g->pair_t32 : nullptr;
+  A.tmin = g->tmin;
   A.prefix = prefix;
   A.hdr = v.hdr;
   A.rec = v.rec;
@@ -1074,6 +1089,8 @@ tc_status launch_path_sum(const tc_graph* g, const Plan& plan, int64_t delta, co
   A.pair_hash = g->pair_hash;
   A.hash_mask = g->hash_mask;
   A.pair_t = g->pair_t;
+  A.pair_t32 = TC_COMPACT_PAIRS ? g->pair_t32 : nullptr;
+  A.tmin = g->tmin;
   A.prefix = prefix;
   A.hdr = v.hdr;
   A.rec = v.rec;
@@ -1120,6 +1137,8 @@ void batch_query_record(void* h_rec, const tc_graph* g, const Plan& plan, int64_
   A.pair_hash = g->pair_hash;
   A.hash_mask = g->hash_mask;
   A.pair_t = g->pair_t;
+  A.pair_t32 = TC_COMPACT_PAIRS ? g->pair_t32 : nullptr;
+  A.tmin = g->tmin;
   A.prefix = prefix;
   A.hdr = v.hdr;
   A.rec = v.rec;
