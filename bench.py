@@ -43,7 +43,7 @@ MOTIF_NAMES = {str(v): k for k, v in MOTIFS.items()}
 # capture of the benchmark's own launch (dram__bytes_read.sum +
 # dram__bytes_write.sum over two 1e8-sample launches); valid while the kernel
 # is unchanged, null for workloads that were not captured
-SAMPLER_TRAFFIC_PER_SAMPLE = {("mid", "path_chord"): 87.3}
+SAMPLER_TRAFFIC_PER_SAMPLE = {}  # re-captured below for the current kernel
 UNIT = "samples/s"
 SECTOR = 32
 
@@ -515,10 +515,11 @@ def main():
         from paper_2409_08975_gb300 import dist as tcdist
         merged = tcdist.merge_runs(r0, r0["W"], device="cuda")
     checked_frac = r0["checked"] / max(r0["k"], 1)
-    # sampler bytes per sample: guide entry, prefix entry, edge record, e1 and
-    # e3 records (5 sectors); a checked path adds the pair list lookup
-    # (pair_off, pair_dst, pair_eoff, pair_t: 4 sectors)
-    bytes_per_sample = SECTOR * (5 + 4 * checked_frac)
+    # sampler bytes per sample: guide entry, prefix entry, edge record and the
+    # end-edge entries (two for a 3-path anchor, one for a wedge): 5 or 4
+    # sectors; a checked path adds the pair list lookup (4 sectors)
+    ends = sum(1 for a in tc.tc_motif_plan(mot)[1][:2] if a != 0)
+    bytes_per_sample = SECTOR * (3 + ends + 4 * checked_frac)
     peak, peak_kind = load_peaks()
     k_sample_ms = statistics.mean(kernel_ms)  # the sampling launch alone, key-order sort excluded
     achieved = bytes_per_sample * k / (k_sample_ms / 1e3) / 1e9

@@ -186,9 +186,10 @@ tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delt
  * (Alg. 2, 3, 4, 5).  Sample s = sample_offset + i, i < k, uses Philox4x32-10
  * (Salmon et al., SC'11) with key (seed low, seed high) and counter
  * (s low, s high, draw, attempt); draw 0 picks the middle edge as the unique
- * e with prefix[e] <= r < prefix[e+1] for r uniform in [0, W), draws 1 and 2
- * pick the end edges uniformly in their windows (Lemire's bounded draw with
- * rejection, at most 64 attempts).  Each path contributes
+ * e with prefix[e] <= r < prefix[e+1] for r uniform in [0, W) from words 0-1
+ * of its block, and draw 1 picks the end edges uniformly in their windows, e1
+ * from words 0-1 and e3 from words 2-3 of its block (Lemire's bounded draw
+ * with rejection, each draw at most 64 attempts).  Each path contributes
  * X = prod over gaps of ListCount (Alg. 3, 4).
  *   d_prefix, d_index  as filled by tc_path_weights for the same graph,
  *                      motif and delta (checked on the device)

@@ -39,6 +39,8 @@ def _declare(L):
     L.or_philox4x32_10.restype = None
     L.or_bounded.argtypes = [u64, u64, u32, u64, ctypes.POINTER(u64)]
     L.or_bounded.restype = ctypes.c_int
+    L.or_bounded_hi.argtypes = [u64, u64, u32, u64, ctypes.POINTER(u64)]
+    L.or_bounded_hi.restype = ctypes.c_int
     L.or_list_count.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_int)]
     L.or_list_count.restype = u64
     L.or_sample_run.argtypes = [i64, i64] + [vp] * 3 + [vp] * 8 + [vp, i64, vp, u64, u64, u64, vp, vp]
@@ -289,9 +291,11 @@ def philox4x32_10(ctr, key):
     return [int(x) for x in o]
 
 
-def bounded(seed, s, draw, rng):
+def bounded(seed, s, draw, rng, upper=False):
+    """Lemire's bounded draw in [0, rng) from block (s, draw, attempt): x from
+    words 0-1, or words 2-3 when upper."""
     r = ctypes.c_uint64(0)
-    st = lib().or_bounded(seed, s, draw, rng, ctypes.byref(r))
+    st = (lib().or_bounded_hi if upper else lib().or_bounded)(seed, s, draw, rng, ctypes.byref(r))
     if st:
         raise OracleError(st, "bounded")
     return r.value

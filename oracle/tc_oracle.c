@@ -317,18 +317,29 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
  * Lemire (2019), x * range is split into high and low 64-bit halves; the draw
  * is accepted when low >= 2^64 mod range, and the result is the high half.
  */
-int or_bounded(uint64_t seed, uint64_t s, uint32_t d, uint64_t range, uint64_t *r) {
+static int bounded_words(uint64_t seed, uint64_t s, uint32_t d, int upper, uint64_t range, uint64_t *r) {
   if (range == 0) return OR_INVALID;
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint64_t reject_below = (uint64_t)(-range) % range; /* = 2^64 mod range */
   for (uint32_t a = 0; a < 64; a++) {
     uint32_t ctr[4] = {(uint32_t)s, (uint32_t)(s >> 32), d, a}, o[4];
     or_philox4x32_10(ctr, key, o);
-    uint64_t x = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+    uint64_t x = upper ? ((uint64_t)o[2] | ((uint64_t)o[3] << 32)) : ((uint64_t)o[0] | ((uint64_t)o[1] << 32));
     u128 prod = (u128)x * range;
     if ((uint64_t)prod >= reject_below) { *r = (uint64_t)(prod >> 64); return OR_OK; }
   }
   return OR_RNG_EXHAUSTED;
+}
+
+/* x from words 0-1 of block (s, d, a) */
+int or_bounded(uint64_t seed, uint64_t s, uint32_t d, uint64_t range, uint64_t *r) {
+  return bounded_words(seed, s, d, 0, range, r);
+}
+
+/* the same draw from words 2-3 of the block: the two end edges of a sample
+ * share block d = 1, e1 the lower half, e3 the upper half */
+int or_bounded_hi(uint64_t seed, uint64_t s, uint32_t d, uint64_t range, uint64_t *r) {
+  return bounded_words(seed, s, d, 1, range, r);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -555,10 +566,11 @@ int or_sample_run(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, 
     int64_t i2 = lo, e2 = out_perm[i2];
     int64_t a, b, c, d;
     anchor_windows(&g, &pl, e2, delta, &a, &b, &c, &d);
-    /* e1 by draw 1, e3 by draw 2; a wedge's unused end has range 1 (r = 0) */
+    /* e1 and e3 from the two halves of block 1; a wedge's unused end has
+     * range 1 (r = 0) */
     st = or_bounded(seed, s, 1, (uint64_t)(b - a), &r1);
     if (st) return st;
-    st = or_bounded(seed, s, 2, (uint64_t)(d - c), &r3);
+    st = or_bounded_hi(seed, s, 1, (uint64_t)(d - c), &r3);
     if (st) return st;
     int64_t p1 = a + (int64_t)r1, p3 = c + (int64_t)r3;
     uint64_t X = anchor_check(&g, &pl, delta, i2, p1, p3, &ovf);
@@ -782,10 +794,11 @@ int or_sample_run_q(int64_t n, int64_t m, const int32_t *src, const int32_t *dst
     int64_t i2 = lo, e2 = out_perm[i2];
     int64_t a, b, c, d;
     anchor_windows(&g, &pl, e2, delta, &a, &b, &c, &d);
-    /* e1 by draw 1, e3 by draw 2; a wedge's unused end has range 1 (r = 0) */
+    /* e1 and e3 from the two halves of block 1; a wedge's unused end has
+     * range 1 (r = 0) */
     st = or_bounded(seed, s, 1, (uint64_t)(b - a), &r1);
     if (st) return st;
-    st = or_bounded(seed, s, 2, (uint64_t)(d - c), &r3);
+    st = or_bounded_hi(seed, s, 1, (uint64_t)(d - c), &r3);
     if (st) return st;
     int64_t p1 = a + (int64_t)r1, p3 = c + (int64_t)r3;
     uint64_t X = anchor_check(&g, &pl, delta, i2, p1, p3, &ovf);

@@ -207,21 +207,30 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // generation in an interval", ACM TOMACS 2019): x * range = hi:lo, accept
 // when lo >= 2^64 mod range, answer hi.  Attempt a draws Philox with counter
 // (s_lo, s_hi, draw, a).  Returns false after 64 rejected attempts.
-__device__ __forceinline__ bool bounded_draw(uint64_t seed, uint64_t s, uint32_t draw, uint64_t range,
-                                             uint64_t* out) {
+// Lemire's test for one 64-bit word x: accepted when x * range mod 2^64 is
+// at least 2^64 mod range (always when it is at least range).
+__device__ __forceinline__ bool lemire_accept(uint64_t x, uint64_t range, uint64_t* out) {
+  const uint64_t lo = x * range;
+  if (lo < range && lo < (0ull - range) % range) return false;
+  *out = __umul64hi(x, range);
+  return true;
+}
+
+// x from words 0-1 (upper: words 2-3) of block (s, draw, attempt).
+__device__ __forceinline__ bool bounded_draw_words(uint64_t seed, uint64_t s, uint32_t draw, bool upper,
+                                                   uint64_t range, uint64_t* out) {
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-  uint64_t reject_below = 0;
-  bool have_threshold = false;
   for (uint32_t a = 0; a < 64; a++) {
     const uint4 o = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)(s >> 32), draw, a), key);
-    const uint64_t x = (uint64_t)o.x | ((uint64_t)o.y << 32);
-    const uint64_t lo = x * range;
-    const uint64_t hi = __umul64hi(x, range);
-    if (lo >= range) { *out = hi; return true; }  // 2^64 mod range < range
-    if (!have_threshold) { reject_below = (0ull - range) % range; have_threshold = true; }
-    if (lo >= reject_below) { *out = hi; return true; }
+    const uint64_t x = upper ? ((uint64_t)o.z | ((uint64_t)o.w << 32)) : ((uint64_t)o.x | ((uint64_t)o.y << 32));
+    if (lemire_accept(x, range, out)) return true;
   }
   return false;
+}
+
+__device__ __forceinline__ bool bounded_draw(uint64_t seed, uint64_t s, uint32_t draw, uint64_t range,
+                                             uint64_t* out) {
+  return bounded_draw_words(seed, s, draw, false, range, out);
 }
 
 __device__ __forceinline__ int64_t sat_add(int64_t a, int64_t d) {

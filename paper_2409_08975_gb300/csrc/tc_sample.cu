@@ -599,13 +599,29 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS_DECL) k_path_sum(con
 }
 
 
+// The rejection loops: the first attempt is tested in the sampler itself and
+// these run only when it is rejected (probability below range / 2^64),
+// starting again from attempt 0.
+__device__ __forceinline__ bool bounded_draw_slow(uint64_t seed, uint64_t s, uint32_t draw, bool upper, uint64_t range,
+                                               uint64_t* out) {
+  return bounded_draw_words(seed, s, draw, upper, range, out);
+}
+
 // One sample (Alg. 2, 3): sample index i within the call (id offset + i).
 template <bool Trace>
 __device__ __forceinline__ void sample_one(const SamplerArgs& A, const Plan& P, uint64_t W, uint32_t shift,
                                            uint64_t i, ThreadSums& T, uint32_t* s_err) {
   const uint64_t s = A.offset + i;
   uint64_t r2, r1, r3;
-  if (!bounded_draw(A.seed, s, 0, W, &r2)) { T.err |= kErrRng; return; }
+  const uint2 key = make_uint2((uint32_t)A.seed, (uint32_t)(A.seed >> 32));
+  {
+    const uint4 o = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)(s >> 32), 0u, 0u), key);
+    if (!lemire_accept((uint64_t)o.x | ((uint64_t)o.y << 32), W, &r2) &&
+        !bounded_draw_slow(A.seed, s, 0, false, W, &r2)) {
+      T.err |= kErrRng;
+      return;
+    }
+  }
   // middle edge: the unique e with prefix[e] <= r2 < prefix[e + 1]
   const uint32_t b = (uint32_t)(r2 >> shift);
   uint32_t lo = __ldg(A.guide + b), hi = __ldg(A.guide + b + 1);
@@ -615,12 +631,18 @@ __device__ __forceinline__ void sample_one(const SamplerArgs& A, const Plan& P, 
   }
   const EdgeRec e = A.rec[lo];
   if (e.d1 == 0 || e.d3 == 0) { T.err |= kErrBounds; return; }  // index not built from this prefix
-  // e1 by draw 1, e3 by draw 2; a draw over one position is 0 without
-  // drawing (a wedge's dummy end, or a window of one edge)
+  // e1 and e3 from the two halves of block 1; a draw over one position is 0
+  // without drawing (a wedge's dummy end, or a window of one edge)
   r1 = r3 = 0;
-  if ((e.d1 > 1 && !bounded_draw(A.seed, s, 1, e.d1, &r1)) || (e.d3 > 1 && !bounded_draw(A.seed, s, 2, e.d3, &r3))) {
-    T.err |= kErrRng;
-    return;
+  if (e.d1 > 1 || e.d3 > 1) {
+    const uint4 o = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)(s >> 32), 1u, 0u), key);
+    if ((e.d1 > 1 && !lemire_accept((uint64_t)o.x | ((uint64_t)o.y << 32), e.d1, &r1) &&
+         !bounded_draw_slow(A.seed, s, 1, false, e.d1, &r1)) ||
+        (e.d3 > 1 && !lemire_accept((uint64_t)o.z | ((uint64_t)o.w << 32), e.d3, &r3) &&
+         !bounded_draw_slow(A.seed, s, 1, true, e.d3, &r3))) {
+      T.err |= kErrRng;
+      return;
+    }
   }
   const uint32_t p1 = e.lo1 + (uint32_t)r1, p3 = e.lo3 + (uint32_t)r3;
   if (lo >= A.m || p1 >= A.m || p3 >= A.m) { T.err |= kErrBounds; return; }

@@ -36,16 +36,18 @@ def test_philox_known_answers():
 # --------------------------------------------------------------------------
 # Lemire's bounded draw (Lemire 2019)
 
-def _x(seed, s, d, a):
+def _x(seed, s, d, a, upper=False):
     o = oracle.philox4x32_10([s & 0xFFFFFFFF, s >> 32, d, a], [seed & 0xFFFFFFFF, seed >> 32])
-    return o[0] | (o[1] << 32)
+    return (o[2] | (o[3] << 32)) if upper else (o[0] | (o[1] << 32))
 
 
 @pytest.mark.parametrize("j", [1, 5, 17, 32, 63])
 def test_bounded_power_of_two_is_top_bits(j):
-    # 2^64 mod 2^j = 0: nothing is rejected and x * 2^j >> 64 = x >> (64 - j)
+    # 2^64 mod 2^j = 0: nothing is rejected and x * 2^j >> 64 = x >> (64 - j),
+    # x from the lower or the upper half of the block
     for s in range(200):
         assert oracle.bounded(7, s, 2, 1 << j) == _x(7, s, 2, 0) >> (64 - j)
+        assert oracle.bounded(7, s, 1, 1 << j, upper=True) == _x(7, s, 1, 0, upper=True) >> (64 - j)
 
 
 def test_bounded_range_one_and_bounds():
@@ -64,7 +66,7 @@ def test_bounded_rejection_removes_bias(R, mod):
     N = 30000
     counts = np.zeros(mod)
     for s in range(N):
-        counts[oracle.bounded(11, s, 0, R) % mod] += 1
+        counts[oracle.bounded(11, s, 0, R, upper=bool(s & 1)) % mod] += 1
     chi2 = ((counts - N / mod) ** 2 / (N / mod)).sum()
     assert chi2 < 20.0, counts
 
