@@ -508,7 +508,9 @@ def main():
         ex = tc.tc_exact_count(g, mot, delta, wts)
         ev[1].record(stream)
         torch.cuda.synchronize()
-        exact = {"C": ex["sum_x"], "paths": ex["k"], "ms": ev[0].elapsed_time(ev[1]),
+        ex_ms = ev[0].elapsed_time(ev[1])
+        exact = {"C": ex["sum_x"], "paths": ex["k"], "ms": ex_ms,
+                 "paths_per_s": ex["k"] / (ex_ms / 1e3) if ex_ms > 0 else None,
                  "rel_error_plain": abs(r0["estimate"] - ex["sum_x"]) / max(ex["sum_x"], 1)}
     merged = None
     if world > 1:  # the one exchange: exact integer sums of the last step over ranks
