@@ -333,10 +333,13 @@ def run_batch(args, rank, world, local):
     launches = tc.tc_kernel_launches() - launches0
     clk = clocks.stop()
     total_ms = start.elapsed_time(end)
+    merged = None
     if world > 1:
         tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(tt.item())
+        from paper_2409_08975_gb300 import dist as tcdist  # the one exchange: exact per-query sums
+        merged = tcdist.merge_batch(res, device="cuda")
     ms_per_step = total_ms / args.steps
     value = world * k_total / (ms_per_step / 1e3)
     sampler_ms = statistics.median(samp)
@@ -393,7 +396,8 @@ def run_batch(args, rank, world, local):
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": None,
             "csr_build_ms": csr_ms, "batch": dict(info, create_s=create_s, sampling_ms_median=sampler_ms),
             "estimates": [{"W": r["W"], "k": r["k"], "estimate": r["estimate"], "std_err": r["std_err"]}
-                          for r in res[:8]],
+                          for r in (merged or res)[:8]],
+            "merged_over_ranks": merged is not None,
         }))
     for g in graphs:
         g.destroy()

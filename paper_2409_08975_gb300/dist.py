@@ -36,6 +36,24 @@ def merge_runs(local, W, group=None, device="cpu"):
     return {"sum_x": sx, "sum_x2": sx2, "hits": hits, "k": k, "W": int(W), "estimate": est, "std_err": se}
 
 
+def merge_batch(local, group=None, device="cpu"):
+    """Merge this rank's per-query runs (a list of {sum_x, sum_x2, hits, k,
+    W}, as tc_batch_run returns) into per-query global estimates with one
+    all-reduce; every rank must hold the same queries (W is per query and
+    the same on every rank)."""
+    vals = []
+    for r in local:
+        vals += [r["sum_x"], r["sum_x2"], r["hits"], r["k"]]
+    tot = allreduce_exact(vals, group, device) if vals else []
+    out = []
+    for j, r in enumerate(local):
+        sx, sx2, hits, k = tot[4 * j:4 * j + 4]
+        est, se = tc.estimate_from_sums(sx, sx2, k, r["W"])
+        out.append({"sum_x": sx, "sum_x2": sx2, "hits": hits, "k": k, "W": int(r["W"]), "estimate": est,
+                    "std_err": se})
+    return out
+
+
 def rank_range(k_total, rank, world):
     """Sample-id range [offset, offset + count) of a rank."""
     base, extra = divmod(int(k_total), int(world))

@@ -42,6 +42,51 @@ def _worker(rank, world, port, queue):
     dist.destroy_process_group()
 
 
+def _batch_worker(rank, world, port, queue):
+    # every rank answers the same two queries over its own id range
+    # [rank * k, (rank + 1) * k), as the batched benchmark does
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2409_08975_gb300 import dist as tcdist
+    g, plan, pre = _graph()
+    plan2 = oracle.compile_motif([(0, 1), (0, 2), (1, 2)])
+    pre2 = oracle.prefix_sum(oracle.path_weights(g, plan2, 10)["w"])
+    local = []
+    for pl, delta, pr, k in ((plan, 20, pre, 3000), (plan2, 10, pre2, 1700)):
+        sums, _ = oracle.sample_run(g, pl, delta, pr, k, SEED, rank * k)
+        local.append(dict(sums, W=int(pr[-1])))
+    merged = tcdist.merge_batch(local)
+    if rank == 0:
+        queue.put(merged)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_batch_runs_merge_per_query(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    merged = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    g, plan, pre = _graph()
+    plan2 = oracle.compile_motif([(0, 1), (0, 2), (1, 2)])
+    pre2 = oracle.prefix_sum(oracle.path_weights(g, plan2, 10)["w"])
+    for m, (pl, delta, pr, k) in zip(merged, ((plan, 20, pre, 3000), (plan2, 10, pre2, 1700))):
+        single, _ = oracle.sample_run(g, pl, delta, pr, world * k, SEED, 0)
+        for key in ("sum_x", "sum_x2", "hits", "k"):
+            assert m[key] == single[key], key
+        est, _ = oracle.estimate(single["sum_x"], single["sum_x2"], world * k, int(pr[-1]))
+        assert m["estimate"] == pytest.approx(est, rel=1e-12)
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
