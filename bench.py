@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--train-samples", type=int, default=10_000_000)
+    ap.add_argument("--objective", default="both", choices=["closure", "variance", "both"],
+                    help="training objective of the learned proposal (both: one comparison each, "
+                         "the closure loss under 'learned', the variance objective under 'learned_variance')")
     ap.add_argument("--motif", default=None, choices=sorted(MOTIFS),
                     help="another motif on the workload's graph (default: the workload's own)")
     ap.add_argument("--workload", default="mid", choices=["mid", "learned", "large", "batch", "small", "batch_small"],
@@ -223,7 +226,8 @@ def run_reference(args, rank, world):
     }))
 
 
-def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weights_ms, n_train, stream):
+def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weights_ms, n_train, stream,
+                       objective="closure"):
     """Learned proposal q ~ w (eps + g) against the plain q ~ w on the same
     graph: features, training on n_train plain samples and the proposal are
     timed once; then k samples with the proposal.  Relative error at a fixed
@@ -244,7 +248,7 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
     _, sfeat_ms = timed(lambda: tc.tc_sample_features(g, mot, delta, wts, feat, n_train, seed=777))
     mlp = tc.MLP(seed=1)
     losses, train_ms = timed(lambda: tc.tc_mlp_train(mlp, g, mot, delta, wts, feat, n_train, seed=12345,
-                                                     batch=16384, lr=3e-3))
+                                                     batch=16384, lr=3e-3, objective=objective))
     prop, prop_ms = timed(lambda: tc.tc_proposal_weights(mlp, g, mot, delta, wts, feat))
     runs = []
     for i in range(4):
@@ -262,7 +266,7 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
     tp = t_1pct(var_plain, plain_sampler_ms / k)
     tl = t_1pct(var_learned, q_ms / k)
     mlp.destroy()
-    return {"train_samples": n_train, "train_ms": train_ms, "features_ms": feat_ms,
+    return {"objective": objective, "train_samples": n_train, "train_ms": train_ms, "features_ms": feat_ms,
             "sample_features_ms": sfeat_ms, "proposal_ms": prop_ms,
             "loss_first_batch": losses[0], "loss_last_batch": losses[1],
             "sampler_ms": q_ms, "samples_per_s": k / (q_ms / 1e3), "estimate": c, "std_err": rq["std_err"],
@@ -565,10 +569,16 @@ def main():
         e2e = {"value": world * k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * m, "d2h_bytes_per_step": 92,
                "ms_per_step": e2e_s * 1e3}
 
-    learned = None if (args.no_learned or rank != 0) else learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
-                                                              args.train_samples, stream)
-    if learned and exact:
-        learned["rel_error"] = abs(learned["estimate"] - exact["C"]) / max(exact["C"], 1)
+    comparisons = {}
+    if not args.no_learned and rank == 0:
+        objectives = ["closure", "variance"] if args.objective == "both" else [args.objective]
+        for obj in objectives:
+            comparisons[obj] = learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
+                                                  args.train_samples, stream, obj)
+            if exact:
+                comparisons[obj]["rel_error"] = abs(comparisons[obj]["estimate"] - exact["C"]) / max(exact["C"], 1)
+    learned = comparisons.get("closure", comparisons.get("variance"))
+    learned_variance = comparisons.get("variance") if len(comparisons) == 2 else None
 
     base = None
     if rank == 0 and not args.no_cpu_baseline and args.workload == "mid":
@@ -583,6 +593,7 @@ def main():
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_dict(cfg, k, world),
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "cpu_baseline": base, "csr_build_ms": csr_ms, "weights": weights, "learned": learned,
+            "learned_variance": learned_variance,
             "estimate": {"W": r0["W"], "estimate": r0["estimate"], "std_err": r0["std_err"], "hits": r0["hits"],
                          "checked": r0["checked"]},
             "merged_over_ranks": merged, "exact": exact,

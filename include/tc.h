@@ -351,6 +351,26 @@ tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, in
                        uint64_t n_samples, uint64_t seed, uint32_t batch, float lr, float* h_losses,
                        void* stream);
 
+/*
+ * Training objectives.  TC_OBJECTIVE_CLOSURE: the closure loss above.
+ * TC_OBJECTIVE_VARIANCE: the estimator's own variance -- with h = eps + g
+ * for the proposal's eps, a sample drawn from q ~ w h has second moment
+ * proportional to Q * sum over paths of X^2 / h, estimated over a batch of
+ * plain samples by mean(h) * mean(X^2 / h); minimising it drives h towards
+ * sqrt(E[X^2 | e]), the variance-optimal per-edge proposal.
+ * tc_mlp_grad_ex / tc_mlp_train_ex: as tc_mlp_grad / tc_mlp_train with the
+ * objective and eps (> 0 for the variance objective); for the variance
+ * objective h_loss and h_losses receive the objective's value.
+ */
+#define TC_OBJECTIVE_CLOSURE 0
+#define TC_OBJECTIVE_VARIANCE 1
+tc_status tc_mlp_grad_ex(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, const float* d_labels,
+                         uint64_t n, int32_t objective, float eps, float* d_grad, float* h_loss, void* stream);
+tc_status tc_mlp_train_ex(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, int64_t delta,
+                          const uint64_t* d_prefix, const void* d_index, const uint16_t* d_feat,
+                          uint64_t n_samples, uint64_t seed, uint32_t batch, float lr, int32_t objective,
+                          float eps, float* h_losses, void* stream);
+
 /* Bytes of a proposal index (header and guide table) for graph g. */
 tc_status tc_proposal_index_bytes(const tc_graph* g, size_t* h_bytes);
 

@@ -178,10 +178,33 @@ def closure_loss(z3, y):
     return float(np.mean(np.where(y > 0, y * np.logaddexp(0.0, -z3), np.logaddexp(0.0, z3))))
 
 
-def mlp_backward(params, x, y, round_acts=True, quantized=True):
-    """Gradients of closure_loss(mlp_forward(x), y) with respect to the FP32
-    parameters (the bf16 roundings are treated as identity in the chain rule,
-    as in the library's backward)."""
+def variance_loss(z3, X, eps):
+    """Estimator-variance objective over a batch of plain samples (paths drawn
+    with probability w_e / W, closure counts X): with h = eps + sigmoid(z3),
+    the second moment of one importance-weighted sample under q ~ w h is
+    (Q / W) * E_plain[X^2 / h] with Q / W = E_plain[h]; the objective is the
+    batch estimate mean(h) * mean(X^2 / h).  Its minimiser over per-edge h is
+    h proportional to sqrt(E[X^2 | e]) (Cauchy-Schwarz)."""
+    h = eps + 1.0 / (1.0 + np.exp(-np.asarray(z3, np.float64)))
+    X = np.asarray(X, np.float64)
+    return float(np.mean(h) * np.mean(X * X / h))
+
+
+def variance_dz(z3, X, eps):
+    """d variance_loss / d z3 for each row: with A = mean(h), B = mean(X^2/h)
+    and g' = g (1 - g), (B - A X^2 / h^2) g' / n."""
+    g = 1.0 / (1.0 + np.exp(-np.asarray(z3, np.float64)))
+    h = eps + g
+    X = np.asarray(X, np.float64)
+    A, Bm = np.mean(h), np.mean(X * X / h)
+    return (Bm - A * X * X / (h * h)) * g * (1.0 - g) / len(X)
+
+
+def mlp_backward(params, x, y, round_acts=True, quantized=True, objective="closure", eps=0.05):
+    """Gradients of closure_loss(mlp_forward(x), y) -- or, for objective
+    "variance", of variance_loss(mlp_forward(x), y, eps) -- with respect to
+    the FP32 parameters (the bf16 roundings are treated as identity in the
+    chain rule, as in the library's backward)."""
     z3, (xb, z1, a1, z2, a2) = mlp_forward(params, x, round_acts, quantized)
     B = len(y)
     if quantized:
@@ -191,8 +214,11 @@ def mlp_backward(params, x, y, round_acts=True, quantized=True):
         W2 = np.asarray(params["W2"], np.float64)
         W3 = np.asarray(params["W3"], np.float64)
     y = np.asarray(y, np.float64)
-    g3 = 1.0 / (1.0 + np.exp(-z3))
-    dz3 = np.where(y > 0, -y * (1.0 - g3), g3) / B
+    if objective == "variance":
+        dz3 = variance_dz(z3, y, eps)
+    else:
+        g3 = 1.0 / (1.0 + np.exp(-z3))
+        dz3 = np.where(y > 0, -y * (1.0 - g3), g3) / B
     g = {"W3": a2.T @ dz3, "b3": np.array([dz3.sum()])}
     dz2 = np.outer(dz3, W3) * (z2 > 0)
     g["W2"] = dz2.T @ a1
@@ -200,7 +226,7 @@ def mlp_backward(params, x, y, round_acts=True, quantized=True):
     dz1 = (dz2 @ W2) * (z1 > 0)
     g["W1"] = dz1.T @ xb
     g["b1"] = dz1.sum(0)
-    return g, closure_loss(z3, y)
+    return g, (variance_loss(z3, y, eps) if objective == "variance" else closure_loss(z3, y))
 
 
 def proposal_h(g, eps, scale):

@@ -659,23 +659,38 @@ tc_status tc_mlp_forward(const tc_mlp* mlp, const uint16_t* d_feat, const uint32
 
 tc_status tc_mlp_grad(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, const float* d_labels,
                       uint64_t n, float* d_grad, float* h_loss, void* stream) {
+  return tc_mlp_grad_ex(mlp, d_feat, d_rows, d_labels, n, TC_OBJECTIVE_CLOSURE, 0.f, d_grad, h_loss, stream);
+}
+
+tc_status tc_mlp_grad_ex(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, const float* d_labels,
+                         uint64_t n, int32_t objective, float eps, float* d_grad, float* h_loss, void* stream) {
   if (!mlp || !d_grad || (n && (!d_feat || !d_labels))) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
+  if (objective != TC_OBJECTIVE_CLOSURE && objective != TC_OBJECTIVE_VARIANCE)
+    return set_error(TC_ERR_INVALID_ARG, "unknown training objective");
+  if (objective == TC_OBJECTIVE_VARIANCE && !(eps > 0.f)) return set_error(TC_ERR_INVALID_ARG, "eps must be > 0");
+  const bool var = objective == TC_OBJECTIVE_VARIANCE;
   cudaStream_t st = S(stream);
-  float* loss = nullptr;
-  TC_CUDA(pool_malloc(&loss, sizeof(float), st));
+  float* buf = nullptr;  // loss, spare float, then (variance) logits and dloss/dz
+  TC_CUDA(pool_malloc(&buf, sizeof(float) * (2 + (var ? 2 * (n ? n : 1) : 0)), st));
+  float* loss = buf;
   tc_status s = TC_OK;
   cudaError_t e = cudaMemsetAsync(d_grad, 0, sizeof(float) * TC_MLP_PARAMS, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, sizeof(float) * 2, st);
   if (e != cudaSuccess) s = cuda_status(e, "memset");
-  if (s == TC_OK) s = launch_mlp_grad(mlp, d_feat, d_rows, d_labels, n, d_grad, loss, st);
+  if (s == TC_OK) {
+    if (var)
+      s = launch_variance_grad(mlp, d_feat, d_rows, d_labels, n, eps, d_grad, loss, buf + 2, buf + 2 + n, buf + 1, st);
+    else
+      s = launch_mlp_grad(mlp, d_feat, d_rows, d_labels, n, d_grad, loss, st);
+  }
   float hl = 0.f;
   if (s == TC_OK) {
     e = cudaMemcpyAsync(&hl, loss, sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = cuda_status(e, "tc_mlp_grad");
   }
-  cudaFreeAsync(loss, st);
-  if (s == TC_OK && h_loss) *h_loss = n ? hl / (float)n : 0.f;
+  cudaFreeAsync(buf, st);
+  if (s == TC_OK && h_loss) *h_loss = var ? hl : (n ? hl / (float)n : 0.f);
   return s;
 }
 
@@ -683,6 +698,17 @@ tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, in
                        const uint64_t* d_prefix, const void* d_index, const uint16_t* d_feat,
                        uint64_t n_samples, uint64_t seed, uint32_t batch, float lr, float* h_losses,
                        void* stream) {
+  return tc_mlp_train_ex(mlp, g, motif, delta, d_prefix, d_index, d_feat, n_samples, seed, batch, lr,
+                         TC_OBJECTIVE_CLOSURE, 0.f, h_losses, stream);
+}
+
+tc_status tc_mlp_train_ex(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, int64_t delta,
+                          const uint64_t* d_prefix, const void* d_index, const uint16_t* d_feat,
+                          uint64_t n_samples, uint64_t seed, uint32_t batch, float lr, int32_t objective,
+                          float eps, float* h_losses, void* stream) {
+  if (objective != TC_OBJECTIVE_CLOSURE && objective != TC_OBJECTIVE_VARIANCE)
+    return set_error(TC_ERR_INVALID_ARG, "unknown training objective");
+  if (objective == TC_OBJECTIVE_VARIANCE && !(eps > 0.f)) return set_error(TC_ERR_INVALID_ARG, "eps must be > 0");
   TC_TRY(check_graph(g));
   Plan plan;
   TC_TRY(plan_of(motif, &plan));
@@ -695,9 +721,13 @@ tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, in
   uint32_t* rows = nullptr;
   float* labels = nullptr;
   float* losses = nullptr;
+  float* zbuf = nullptr;  // variance objective: logits, dloss/dz and a spare float of a batch
   SampleSums* sums = nullptr;
   tc_status s = TC_OK;
+  const bool var = objective == TC_OBJECTIVE_VARIANCE;
+  const uint64_t bmax = batch < n_samples ? batch : n_samples;
   cudaError_t e = pool_malloc(&trace, 32 * n_samples, st);
+  if (e == cudaSuccess && var) e = pool_malloc(&zbuf, sizeof(float) * (2 * bmax + 1), st);
   if (e == cudaSuccess) e = pool_malloc(&rows, 4 * n_samples, st);
   if (e == cudaSuccess) e = pool_malloc(&labels, 4 * n_samples, st);
   if (e == cudaSuccess) e = pool_malloc(&losses, sizeof(float) * steps, st);
@@ -710,7 +740,11 @@ tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, in
   if (s == TC_OK) s = launch_trace_to_rows(trace, n_samples, rows, labels, st);
   for (uint64_t b = 0; b < steps && s == TC_OK; b++) {
     const uint64_t lo = b * batch, nb = (n_samples - lo) < batch ? (n_samples - lo) : batch;
-    s = launch_mlp_grad(mlp, d_feat, rows + lo, labels + lo, nb, mlp_grad_buffer(mlp), losses + b, st);
+    if (var)
+      s = launch_variance_grad(mlp, d_feat, rows + lo, labels + lo, nb, eps, mlp_grad_buffer(mlp), losses + b, zbuf,
+                               zbuf + bmax, zbuf + 2 * bmax, st);
+    else
+      s = launch_mlp_grad(mlp, d_feat, rows + lo, labels + lo, nb, mlp_grad_buffer(mlp), losses + b, st);
     if (s == TC_OK) s = mlp_adam(mlp, lr, st);
   }
   SampleSums hs;
@@ -722,13 +756,13 @@ tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, in
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = cuda_status(e, "tc_mlp_train");
   }
-  for (void* p : {(void*)trace, (void*)rows, (void*)labels, (void*)losses, (void*)sums})
+  for (void* p : {(void*)trace, (void*)rows, (void*)labels, (void*)losses, (void*)sums, (void*)zbuf})
     if (p) cudaFreeAsync(p, st);
   if (s == TC_OK && hs.err) s = device_status(hs.err, "tc_mlp_train");
   if (s == TC_OK && h_losses) {
     const uint64_t last_n = n_samples - (steps - 1) * (uint64_t)batch;
-    h_losses[0] = first / (float)(batch < n_samples ? batch : n_samples);
-    h_losses[1] = last / (float)last_n;
+    h_losses[0] = var ? first : first / (float)(batch < n_samples ? batch : n_samples);
+    h_losses[1] = var ? last : last / (float)last_n;
   }
   return s;
 }

@@ -322,7 +322,13 @@ tc_status launch_features(const tc_graph* g, const EdgeRec* rec, int64_t delta, 
 tc_status launch_mlp_forward(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, uint64_t n, float* out,
                              cudaStream_t st);
 tc_status launch_mlp_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, const float* labels,
-                          uint64_t n, float* grad, float* loss_sum, cudaStream_t st);
+                          uint64_t n, float* grad, float* loss_sum, cudaStream_t st, bool given_dz = false);
+// Gradient of the estimator-variance objective (z, dz: n floats of scratch;
+// *loss receives the objective, loss_scratch one float the gradient kernel
+// may touch).
+tc_status launch_variance_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, const float* X,
+                               uint64_t n, float eps, float* grad, float* loss, float* z, float* dz,
+                               float* loss_scratch, cudaStream_t st);
 tc_status mlp_adam(tc_mlp* M, float lr, cudaStream_t st);
 float* mlp_grad_buffer(tc_mlp* M);
 tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint64_t n, int64_t delta,

@@ -423,12 +423,58 @@ struct TrainShared {
   float loss[kTrainWarps];
 };
 
+// Estimator-variance objective over a batch of n rows: with h_i = eps + g_i,
+// g_i = sigmoid(z_i), the per-sample second moment of the estimate under the
+// proposal is proportional to L = mean(h) * mean(X_i^2 / h_i) (the batch's
+// paths come from the plain sampler, so mean(h) estimates Q / W).  Writes
+// dL/dz_i into dz and L into *loss; sums in FP64.
+__global__ void __launch_bounds__(1024) k_variance_dz(const float* __restrict__ z, const float* __restrict__ X,
+                                                      uint64_t n, float eps, float* __restrict__ dz,
+                                                      float* __restrict__ loss) {
+  __shared__ double s_a[32], s_b[32];
+  __shared__ double s_A, s_B;
+  double a = 0.0, b = 0.0;
+  for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double h = (double)eps + (double)sigmoidf_(z[i]);
+    const double x = X[i];
+    a += h;
+    b += x * x / h;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_a[threadIdx.x >> 5] = a;
+    s_b[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      ta += s_a[w];
+      tb += s_b[w];
+    }
+    s_A = ta / (double)n;
+    s_B = tb / (double)n;
+    *loss = (float)(s_A * s_B);
+  }
+  __syncthreads();
+  const double A = s_A, B = s_B;
+  for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double g = sigmoidf_(z[i]);
+    const double h = (double)eps + g;
+    const double x = X[i];
+    dz[i] = (float)(g * (1.0 - g) * (B - A * x * x / (h * h)) / (double)n);
+  }
+}
+
 __global__ void __launch_bounds__(32 * kTrainWarps) k_mlp_grad(const float* __restrict__ params,
                                                               const __nv_bfloat16* __restrict__ feat,
                                                               const uint32_t* __restrict__ rows,
                                                               const float* __restrict__ labels, uint64_t n,
                                                               float inv_batch, float* __restrict__ grad,
-                                                              float* __restrict__ loss_sum) {
+                                                              float* __restrict__ loss_sum, int given_dz) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainShared& S = *reinterpret_cast<TrainShared*>(smem_raw);
   load_mlp_shared(S.net, params);
@@ -452,14 +498,15 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_mlp_grad(const float* __re
     // binary cross-entropy when y is 0 or 1); dloss/dz = -y (1 - g) or g
     const float ya = va ? labels[ia] : 0.f, yb = vb ? labels[ib] : 0.f;
     auto dloss = [](float z, float y) { return y > 0.f ? -y * (1.f - sigmoidf_(z)) : sigmoidf_(z); };
-    const float dza = va ? dloss(T.z3g, ya) * inv_batch : 0.f;
-    const float dzb = vb ? dloss(T.z3g8, yb) * inv_batch : 0.f;
+    // given_dz: the labels are dloss/dz already (the variance objective)
+    const float dza = va ? (given_dz ? ya : dloss(T.z3g, ya) * inv_batch) : 0.f;
+    const float dzb = vb ? (given_dz ? yb : dloss(T.z3g8, yb) * inv_batch) : 0.f;
     if (q == 0) {
       S.dz3[ra] = dza;
       S.dz3[rb] = dzb;
       auto softplus = [](float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); };
       auto loss = [&](float z, float y) { return y > 0.f ? y * softplus(-z) : softplus(z); };
-      loss_acc += (va ? loss(T.z3g, ya) : 0.f) + (vb ? loss(T.z3g8, yb) : 0.f);
+      if (!given_dz) loss_acc += (va ? loss(T.z3g, ya) : 0.f) + (vb ? loss(T.z3g8, yb) : 0.f);
     }
     // inputs and activations of the rows (bf16 values held as FP32)
     {
@@ -699,7 +746,7 @@ tc_status launch_mlp_forward(const tc_mlp* M, const uint16_t* feat, const uint32
 // grad (device, kNParams) += gradient of the mean BCE over rows; *loss_sum
 // (device) += summed per-row loss.
 tc_status launch_mlp_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, const float* labels,
-                          uint64_t n, float* grad, float* loss_sum, cudaStream_t st) {
+                          uint64_t n, float* grad, float* loss_sum, cudaStream_t st, bool given_dz) {
   if (!n) return TC_OK;
   static bool attr = false;
   if (!attr) {
@@ -707,10 +754,22 @@ tc_status launch_mlp_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t*
     attr = true;
   }
   k_mlp_grad<<<grid_cap(n, kTrainRows * TC_TRAIN_TILES), 32 * kTrainWarps, sizeof(TrainShared), st>>>(
-      M->params, reinterpret_cast<const __nv_bfloat16*>(feat), rows, labels, n, 1.0f / (float)n, grad, loss_sum);
+      M->params, reinterpret_cast<const __nv_bfloat16*>(feat), rows, labels, n, 1.0f / (float)n, grad, loss_sum,
+      given_dz ? 1 : 0);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
+}
+
+tc_status launch_variance_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, const float* X,
+                               uint64_t n, float eps, float* grad, float* loss, float* z, float* dz,
+                               float* loss_scratch, cudaStream_t st) {
+  if (!n) return TC_OK;
+  TC_TRY(launch_mlp_forward(M, feat, rows, n, z, st));
+  k_variance_dz<<<1, 1024, 0, st>>>(z, X, n, eps, dz, loss);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return launch_mlp_grad(M, feat, rows, dz, n, grad, loss_scratch, st, true);
 }
 
 tc_status mlp_adam(tc_mlp* M, float lr, cudaStream_t st) {

@@ -92,6 +92,10 @@ def lib():
             "tc_mlp_grad": [vp, vp, vp, vp, u64, vp, ctypes.POINTER(ctypes.c_float), vp],
             "tc_mlp_train": [vp, vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, u64, u64, ctypes.c_uint32,
                              ctypes.c_float, vp, vp],
+            "tc_mlp_grad_ex": [vp, vp, vp, vp, u64, ctypes.c_int32, ctypes.c_float, vp,
+                               ctypes.POINTER(ctypes.c_float), vp],
+            "tc_mlp_train_ex": [vp, vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, u64, u64, ctypes.c_uint32,
+                                ctypes.c_float, ctypes.c_int32, ctypes.c_float, vp, vp],
             "tc_proposal_index_bytes": [vp, ctypes.POINTER(sz)],
             "tc_proposal_weights": [vp, vp, ctypes.POINTER(tc_motif), i64, vp, vp, ctypes.c_float, ctypes.c_uint32,
                                     vp, vp, vp, ctypes.POINTER(u64), vp],
@@ -401,21 +405,27 @@ def tc_mlp_forward(mlp, feat, rows=None, n=None, stream=None):
     return out[:n]
 
 
-def tc_mlp_grad(mlp, feat, rows, labels, stream=None):
+OBJECTIVES = {"closure": 0, "variance": 1}
+
+
+def tc_mlp_grad(mlp, feat, rows, labels, objective="closure", eps=0.05, stream=None):
     n = int(labels.numel())
     grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
     loss = ctypes.c_float(0.0)
-    _check(lib().tc_mlp_grad(mlp.handle, _ptr(feat), _ptr(rows), _ptr(labels), n, _ptr(grad), ctypes.byref(loss),
-                             _stream(stream)), "tc_mlp_grad")
+    _check(lib().tc_mlp_grad_ex(mlp.handle, _ptr(feat), _ptr(rows), _ptr(labels), n, OBJECTIVES[objective],
+                                float(eps), _ptr(grad), ctypes.byref(loss), _stream(stream)), "tc_mlp_grad")
     return grad, loss.value
 
 
-def tc_mlp_train(mlp, g, motif, delta, weights, feat, n_samples, seed=0, batch=16384, lr=2e-3, stream=None):
-    """Returns the mean loss of the first and the last batch."""
+def tc_mlp_train(mlp, g, motif, delta, weights, feat, n_samples, seed=0, batch=16384, lr=2e-3, objective="closure",
+                 eps=0.05, stream=None):
+    """Returns the loss of the first and the last batch (the mean closure
+    loss, or the variance objective)."""
     losses = np.zeros(2, np.float32)
-    _check(lib().tc_mlp_train(mlp.handle, g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix),
-                              _ptr(weights.index), _ptr(feat), int(n_samples), int(seed), int(batch), float(lr),
-                              losses.ctypes.data_as(ctypes.c_void_p), _stream(stream)), "tc_mlp_train")
+    _check(lib().tc_mlp_train_ex(mlp.handle, g.handle, ctypes.byref(motif), int(delta), _ptr(weights.prefix),
+                                 _ptr(weights.index), _ptr(feat), int(n_samples), int(seed), int(batch), float(lr),
+                                 OBJECTIVES[objective], float(eps), losses.ctypes.data_as(ctypes.c_void_p),
+                                 _stream(stream)), "tc_mlp_train")
     return float(losses[0]), float(losses[1])
 
 

@@ -116,12 +116,39 @@ def test_forward_and_gradient_match_fp64(tc):
     assert abs(loss - lref) < 1e-3
 
 
-def _trained(tc, setup, n_train, seed=3):
+def test_variance_objective_gradient_matches_fp64(tc):
+    import torch
+    n, src, dst, t = _graph_bursty()
+    g, og, mot, plan, w, feat = _setup(tc, n, src, dst, t, CHORD, 3600)
+    tc.tc_sample_features(g, mot, 3600, w, feat, 50_000, seed=11)
+    params = L.init_params(np.random.default_rng(19))
+    flat = L.pack(params).astype(np.float32)
+    mlp = tc.MLP(seed=1)
+    mlp.set_params(flat)
+    p32 = L.unpack(flat.astype(np.float64))
+    rng = np.random.default_rng(12)
+    for nrows in (5000, 77):        # several tiles, and one ragged tile
+        rows = rng.integers(0, g.m, nrows).astype(np.int32)
+        x = _f32(feat)[rows]
+        y = np.where(rng.random(nrows) < 0.8, 0, rng.integers(1, 6, nrows)).astype(np.float32)
+        grad, loss = tc.tc_mlp_grad(mlp, feat, _dev(rows, torch.int32), _dev(y, torch.float32),
+                                    objective="variance", eps=0.05)
+        gref, lref = L.mlp_backward(p32, x, y.astype(np.float64), objective="variance", eps=0.05)
+        gref_flat = L.pack(gref)
+        gg = grad.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(gg - gref_flat) <= 1e-2 * np.linalg.norm(gref_flat), nrows
+        assert loss == pytest.approx(lref, rel=1e-3)
+    with pytest.raises(tc.TcError):
+        tc.tc_mlp_grad(mlp, feat, _dev(rows, torch.int32), _dev(y, torch.float32), objective="variance", eps=0.0)
+
+
+def _trained(tc, setup, n_train, seed=3, objective="closure"):
     g, og, mot, plan, w, feat = setup
     delta = 3600 if og.n > 100 else 10_000
     tc.tc_sample_features(g, mot, delta, w, feat, n_train, seed=seed + 1000)  # samples disjoint from training
     mlp = tc.MLP(seed=seed)
-    first, last = tc.tc_mlp_train(mlp, g, mot, delta, w, feat, n_train, seed=seed, batch=4096, lr=3e-3)
+    first, last = tc.tc_mlp_train(mlp, g, mot, delta, w, feat, n_train, seed=seed, batch=4096, lr=3e-3,
+                                  objective=objective)
     return mlp, first, last
 
 
@@ -179,12 +206,13 @@ def test_proposal_unbiased_over_1000_seeds(tc):
     assert abs(np.mean(ests) - C) <= 2.576 * math.sqrt(float(var) / k / 1000)
 
 
-def test_trained_network_reduces_variance(tc):
+@pytest.mark.parametrize("objective", ["closure", "variance"])
+def test_trained_network_reduces_variance(tc, objective):
     # exact per-sample variances from all paths: plain W sum C_P^2 - C^2,
     # learned Q sum C_P^2 / h_P - C^2, after training on plain samples
     n, src, dst, t = _graph_bursty()
     g, og, mot, plan, w, feat = setup = _setup(tc, n, src, dst, t, CHORD, 3600)
-    mlp, _, _ = _trained(tc, setup, 400_000)
+    mlp, _, _ = _trained(tc, setup, 400_000, objective=objective)
     prop = tc.tc_proposal_weights(mlp, g, mot, 3600, w, feat)
     h = prop.h.cpu().numpy().view(np.uint16)
     ps = oracle.path_sum(og, plan, 3600)

@@ -185,3 +185,88 @@ def test_proposal_unbiased_over_1000_seeds_and_exact_variance():
     assert abs(np.mean(ests) - C) <= 2.576 * sd_mean
     sd_run = math.sqrt(float(var) / k)
     assert 0.8 * sd_run < np.std(ests) < 1.2 * sd_run
+
+
+def test_variance_objective_by_hand_and_its_minimiser():
+    # two rows, eps 0.5, z = 0: h = 1 for both; X = 2, 0 -> mean(h) 1,
+    # mean(X^2 / h) 2; dL/dz = (B - A X^2 / h^2) g (1 - g) / n = (2 - 4) / 8, 2 / 8
+    z = np.zeros(2)
+    X = np.array([2.0, 0.0])
+    assert L.variance_loss(z, X, 0.5) == pytest.approx(2.0, rel=1e-15)
+    assert np.allclose(L.variance_dz(z, X, 0.5), [-0.25, 0.25], rtol=1e-15)
+    # rows in groups with one free h per group: by Cauchy-Schwarz the minimum
+    # (sum_e sqrt(n_e S_e))^2 / n^2 is reached at h_e proportional to
+    # sqrt(S_e / n_e) (S_e = sum of X^2 over the group), where dL/dz sums to
+    # zero within every group; any other h gives more
+    rng = np.random.default_rng(4)
+    groups = rng.integers(0, 6, 3000)
+    X = np.where(rng.random(3000) < 0.5, 0.0, rng.integers(1, 9, 3000)).astype(np.float64)
+    n_e = np.bincount(groups, minlength=6).astype(np.float64)
+    S_e = np.bincount(groups, weights=X * X, minlength=6)
+    eps = 0.05
+    r = np.sqrt(S_e / n_e)
+    h_star = 0.9 * r / r.max()
+    g = (h_star - eps)[groups]
+    assert (g > 0).all() and (g < 1).all()
+    z = np.log(g / (1 - g))
+    best = L.variance_loss(z, X, eps)
+    assert best == pytest.approx(np.sum(np.sqrt(n_e * S_e)) ** 2 / 3000 ** 2, rel=1e-12)
+    dz = L.variance_dz(z, X, eps)
+    assert np.abs(np.bincount(groups, weights=dz, minlength=6)).max() < 1e-15 * 3000
+    for _ in range(20):
+        gz = np.clip(g * np.exp(rng.normal(0, 0.2, 6))[groups], 1e-3, 1 - 1e-3)
+        assert L.variance_loss(np.log(gz / (1 - gz)), X, eps) > best
+
+
+def test_variance_objective_over_all_paths_is_the_exact_variance():
+    # over the multiset of all W paths (each path a row of its middle edge),
+    # W^2 mean(h) mean(X^2 / h) - C^2 is the proposal's exact per-sample
+    # variance Q sum_P C_P^2 / h_P - C^2; the objective only needs per edge
+    # w_e rows of h_e and the sum of X^2, so one row carries sqrt(sum X^2)
+    src, dst, t, g = _graph()
+    plan = oracle.compile_motif(C4)
+    delta = 20
+    w = oracle.path_weights(g, plan, delta)["w"].astype(np.int64)
+    assert g.m < 65_535
+    per_edge = np.arange(1, g.m + 1, dtype=np.uint16)       # distinct h: one bin per edge
+    lo, S1e, S2e = L.path_sum_q(g, plan, delta, per_edge)
+    S2e = np.array(S2e, dtype=np.float64)[per_edge.astype(np.int64) - lo]
+    C = oracle.brute_force_count(src, dst, t, C4, delta)
+    rng = np.random.default_rng(6)
+    h = rng.integers(1, 60, g.m).astype(np.uint16)
+    Q = int(L.qprefix(w.astype(np.uint64), h)[-1])
+    h_lo, _, S2 = L.path_sum_q(g, plan, delta, h)
+    exact = float(L.exact_variance_q(Q, C, h_lo, S2))
+    rows_h, rows_x = [], []
+    for e in range(g.m):
+        if w[e]:
+            rows_h += [h[e]] * int(w[e])
+            rows_x += [np.sqrt(S2e[e])] + [0.0] * (int(w[e]) - 1)
+    gg = np.array(rows_h, np.float64) / 64.0                 # eps 0: h scaled into (0, 1)
+    z = np.log(gg / (1 - gg))
+    W = int(w.sum())
+    assert len(rows_h) == W and C > 0
+    obj = L.variance_loss(z, np.array(rows_x), 0.0)
+    assert W * W * obj - C * C == pytest.approx(exact, rel=1e-9)
+
+
+def test_variance_backward_matches_finite_differences():
+    rng = np.random.default_rng(15)
+    params = L.init_params(rng)
+    x = rng.uniform(0, 3, (40, 16))
+    y = np.where(rng.random(40) < 0.6, 0.0, rng.integers(1, 6, 40)).astype(np.float64)
+    grads, loss = L.mlp_backward(params, x, y, round_acts=False, quantized=False, objective="variance", eps=0.05)
+    assert loss == L.variance_loss(L.mlp_forward(params, x, False, False)[0], y, 0.05)
+    h = 1e-6
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        flat = params[name].reshape(-1)
+        for j in rng.choice(flat.size, size=min(12, flat.size), replace=False):
+            old = flat[j]
+            flat[j] = old + h
+            lp = L.variance_loss(L.mlp_forward(params, x, False, False)[0], y, 0.05)
+            flat[j] = old - h
+            lm = L.variance_loss(L.mlp_forward(params, x, False, False)[0], y, 0.05)
+            flat[j] = old
+            fd = (lp - lm) / (2 * h)
+            an = grads[name].reshape(-1)[j]
+            assert abs(fd - an) <= 1e-7 + 1e-5 * abs(fd), (name, j, fd, an)
