@@ -226,13 +226,28 @@ def run_reference(args, rank, world):
     }))
 
 
+BUDGET_SEEDS = (1, 2, 3, 4, 5)
+
+
+def run_errors(tc, g, mot, delta, wts, C, k, prop=None):
+    """|C_hat - C| / C of independent runs of k samples, one per seed of
+    BUDGET_SEEDS, with the plain proposal or the learned one (prop)."""
+    errs = []
+    for s in BUDGET_SEEDS:
+        r = (tc.tc_sample_estimate(g, mot, delta, wts, k, seed=s) if prop is None
+             else tc.tc_sample_estimate_q(g, mot, delta, wts, prop, k, seed=s))
+        errs.append(abs(r["estimate"] - C) / C)
+    return errs
+
+
 def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weights_ms, n_train, stream,
-                       objective="closure"):
+                       objective="closure", exact_C=None, plain_errors=None):
     """Learned proposal q ~ w (eps + g) against the plain q ~ w on the same
     graph: features, training on n_train plain samples and the proposal are
     timed once; then k samples with the proposal.  Relative error at a fixed
     GPU time follows from the per-sample variance (k SE^2) and the GPU time
-    per sample of each sampler."""
+    per sample of each sampler; with the exact count C, also as the mean
+    relative error of five seeds' runs at the GPU time of k plain samples."""
     import torch
 
     def timed(fn):
@@ -265,6 +280,17 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
 
     tp = t_1pct(var_plain, plain_sampler_ms / k)
     tl = t_1pct(var_learned, q_ms / k)
+    budget = None
+    if exact_C and plain_errors:
+        # the paper's metric: mean relative error over seeds at one GPU-time
+        # budget, that of k plain samples; the learned sampler gets as many
+        # samples as fit in it
+        k_l = max(2, int(k * plain_sampler_ms / q_ms))
+        errs = run_errors(tc, g, mot, delta, wts, exact_C, k_l, prop)
+        budget = {"budget_ms": plain_sampler_ms, "seeds": list(BUDGET_SEEDS), "k_plain": k, "k_learned": k_l,
+                  "rel_error_plain": statistics.mean(plain_errors), "rel_error_learned": statistics.mean(errs),
+                  "rel_error_ratio_learned_over_plain": statistics.mean(errs) / max(statistics.mean(plain_errors),
+                                                                                    1e-300)}
     mlp.destroy()
     return {"objective": objective, "train_samples": n_train, "train_ms": train_ms, "features_ms": feat_ms,
             "sample_features_ms": sfeat_ms, "proposal_ms": prop_ms,
@@ -273,7 +299,8 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
             "plain_estimate": plain["estimate"], "plain_std_err": plain["std_err"],
             "variance_ratio_learned_over_plain": var_learned / var_plain,
             "time_to_1pct_ms_plain": tp, "time_to_1pct_ms_learned": tl, "time_ratio_learned_over_plain": tl / tp,
-            "time_ratio_with_setup": (tl + feat_ms + sfeat_ms + train_ms + prop_ms) / (tp + weights_ms)}
+            "time_ratio_with_setup": (tl + feat_ms + sfeat_ms + train_ms + prop_ms) / (tp + weights_ms),
+            "fixed_budget": budget}
 
 
 def config_dict(cfg, k, world):
@@ -570,11 +597,15 @@ def main():
                "ms_per_step": e2e_s * 1e3}
 
     comparisons = {}
+    plain_errors = None
+    if exact and exact["C"] and not args.no_learned and rank == 0:
+        plain_errors = run_errors(tc, g, mot, delta, wts, exact["C"], k)
     if not args.no_learned and rank == 0:
         objectives = ["closure", "variance"] if args.objective == "both" else [args.objective]
         for obj in objectives:
             comparisons[obj] = learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
-                                                  args.train_samples, stream, obj)
+                                                  args.train_samples, stream, obj,
+                                                  exact["C"] if exact else None, plain_errors)
             if exact:
                 comparisons[obj]["rel_error"] = abs(comparisons[obj]["estimate"] - exact["C"]) / max(exact["C"], 1)
     learned = comparisons.get("closure", comparisons.get("variance"))
