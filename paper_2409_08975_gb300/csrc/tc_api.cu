@@ -735,7 +735,7 @@ tc_status tc_mlp_train_ex(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif,
   if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, sizeof(SampleSums), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(losses, 0, sizeof(float) * steps, st);
   if (e != cudaSuccess) s = cuda_status(e, "tc_mlp_train allocation");
-  // training paths from the plain sampler: rows = middle edges, labels = [X > 0]
+  // training paths from the plain sampler: rows = middle edges, labels = closure counts X
   if (s == TC_OK) s = launch_sampler(g, plan, delta, d_prefix, d_index, n_samples, seed, 0, trace, sums, st);
   if (s == TC_OK) s = launch_trace_to_rows(trace, n_samples, rows, labels, st);
   for (uint64_t b = 0; b < steps && s == TC_OK; b++) {

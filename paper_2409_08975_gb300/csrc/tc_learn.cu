@@ -395,9 +395,12 @@ __global__ void __launch_bounds__(128) k_proposal(const float* __restrict__ para
 }
 
 // ---------------------------------------------------------------------------
-// Gradient of the mean binary cross-entropy over a batch.  Each warp runs the
-// forward of a 16-row tile on the tensor cores and back-propagates in FP32:
-//   dz3 = (sigmoid(z3) - y) / B, dz2 = dz3 W3 * [z2 > 0], dz1 = W2^T dz2 * [z1 > 0];
+// Gradient of the mean closure loss over a batch (the binary cross-entropy
+// when every label is 0 or 1), or of any loss whose dloss/dz3 per row is
+// given.  Each warp runs the forward of a 16-row tile on the tensor cores and
+// back-propagates in FP32:
+//   dz3 = (-y (1 - g) if y > 0 else g) / B with g = sigmoid(z3) (or the given
+//   dz3), dz2 = dz3 W3 * [z2 > 0], dz1 = W2^T dz2 * [z1 > 0];
 // the per-row vectors go to shared memory, where the block accumulates the
 // parameter gradients (each thread owns a fixed set of parameters) before one
 // global atomic add per parameter and block.
@@ -743,8 +746,9 @@ tc_status launch_mlp_forward(const tc_mlp* M, const uint16_t* feat, const uint32
   return TC_OK;
 }
 
-// grad (device, kNParams) += gradient of the mean BCE over rows; *loss_sum
-// (device) += summed per-row loss.
+// grad (device, kNParams) += gradient of the mean closure loss over rows;
+// *loss_sum (device) += summed per-row loss.  given_dz: labels hold dloss/dz3
+// per row and no loss is summed.
 tc_status launch_mlp_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, const float* labels,
                           uint64_t n, float* grad, float* loss_sum, cudaStream_t st, bool given_dz) {
   if (!n) return TC_OK;
