@@ -270,3 +270,52 @@ def test_variance_backward_matches_finite_differences():
             fd = (lp - lm) / (2 * h)
             an = grads[name].reshape(-1)[j]
             assert abs(fd - an) <= 1e-7 + 1e-5 * abs(fd), (name, j, fd, an)
+
+
+def _adam(params, grad_fn, n_rows, batch, lr):
+    """Plain Adam (beta 0.9 / 0.999, eps 1e-8) over consecutive row batches."""
+    flat = L.pack(params).astype(np.float64)
+    m1, m2 = np.zeros_like(flat), np.zeros_like(flat)
+    losses = []
+    for step, lo in enumerate(range(0, n_rows, batch), start=1):
+        g, loss = grad_fn(L.unpack(flat.astype(np.float32).astype(np.float64)), lo, min(lo + batch, n_rows))
+        losses.append(loss)
+        gf = L.pack(g)
+        m1 = 0.9 * m1 + 0.1 * gf
+        m2 = 0.999 * m2 + 0.001 * gf * gf
+        flat -= lr * (m1 / (1 - 0.9 ** step)) / (np.sqrt(m2 / (1 - 0.999 ** step)) + 1e-8)
+    return L.unpack(flat.astype(np.float32).astype(np.float64)), losses
+
+
+@pytest.mark.parametrize("objective", ["closure", "variance"])
+def test_oracle_pipeline_reduces_the_exact_variance(objective):
+    # the whole learned method on the CPU: features and sample statistics,
+    # training on the plain sampler's paths with the oracle's gradients,
+    # integer h, and the exact per-sample variance Q sum_P C_P^2 / h_P - C^2
+    # against the plain W sum_P C_P^2 - C^2 over all paths
+    from paper_2409_08975_gb300 import synth
+    c = synth.scaled_mid(3000, 60_000, seed=21)
+    g = oracle.build_csr(c["n"], c["src"], c["dst"], c["t"])
+    plan = oracle.compile_motif(CHORD)
+    delta = 3600
+    w = oracle.path_weights(g, plan, delta)["w"]
+    pre = oracle.prefix_sum(w)
+    x = L.features_bf16(L.edge_features(g, plan, delta),
+                        L.sample_features(g, plan, delta, pre, 400_000, 1003)).astype(np.float64)
+    _, tr = oracle.sample_run(g, plan, delta, pre, 400_000, 3, trace=True)
+    rows, X = tr[:, 0].astype(np.int64), tr[:, 3].astype(np.float64)
+
+    def grad(p, lo, hi):
+        return L.mlp_backward(p, x[rows[lo:hi]], X[lo:hi], objective=objective, eps=0.05)
+
+    params, losses = _adam(L.init_params(np.random.default_rng(3)), grad, len(rows), 4096, 3e-3)
+    assert np.mean(losses[-10:]) < np.mean(losses[:10])
+    z, _ = L.mlp_forward(params, x)
+    h = L.proposal_h((1.0 / (1.0 + np.exp(-z))).astype(np.float32), 0.05, 1024)
+    ps = oracle.path_sum(g, plan, delta)
+    C, W = ps["C"], int(pre[-1])
+    var_plain = Fraction(W) * ps["sum_x2"] - C * C
+    h_lo, S1, S2 = L.path_sum_q(g, plan, delta, h)
+    assert sum(S1) == C
+    ratio = float(L.exact_variance_q(int(L.qprefix(w, h)[-1]), C, h_lo, S2) / var_plain)
+    assert ratio < 0.75, ratio        # 0.58-0.60 over three initialisations for either objective
