@@ -1,8 +1,11 @@
 """Pins of the learned-proposal oracle (no GPU): bf16 rounding against
 torch's conversion, features against literal counting, the FP64 backward
-against central finite differences, and the proposal sampler against the
-plain sampler (h = 1) and the unbiasedness of Claim 2 with the exact variance
-Q sum_P C_P^2 / h_P - C^2."""
+(closure loss and variance objective) against central finite differences,
+the variance objective against hand values, its Cauchy-Schwarz minimiser and
+the exact variance over all paths, the proposal sampler against the plain
+sampler (h = 1) and the unbiasedness of Claim 2 with the exact variance
+Q sum_P C_P^2 / h_P - C^2, and the whole method run on the oracle lowering
+that variance."""
 import math
 from fractions import Fraction
 
