@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--train-samples", type=int, default=10_000_000)
+    ap.add_argument("--stats-samples", type=int, default=None,
+                    help="plain samples behind the sample-statistics features (default: --train-samples)")
     ap.add_argument("--objective", default="both", choices=["closure", "variance", "both"],
                     help="training objective of the learned proposal (both: one comparison each, "
                          "the closure loss under 'learned', the variance objective under 'learned_variance')")
@@ -241,7 +243,7 @@ def run_errors(tc, g, mot, delta, wts, C, k, prop=None):
 
 
 def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weights_ms, n_train, stream,
-                       objective="closure", exact_C=None, plain_errors=None):
+                       objective="closure", exact_C=None, plain_errors=None, n_stats=None):
     """Learned proposal q ~ w (eps + g) against the plain q ~ w on the same
     graph: features, training on n_train plain samples and the proposal are
     timed once; then k samples with the proposal.  Relative error at a fixed
@@ -260,7 +262,8 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
 
     feat, feat_ms = timed(lambda: tc.tc_edge_features(g, mot, delta, wts))
     # sample statistics from n_train plain samples of another seed than the training paths
-    _, sfeat_ms = timed(lambda: tc.tc_sample_features(g, mot, delta, wts, feat, n_train, seed=777))
+    n_stats = n_stats or n_train
+    _, sfeat_ms = timed(lambda: tc.tc_sample_features(g, mot, delta, wts, feat, n_stats, seed=777))
     mlp = tc.MLP(seed=1)
     losses, train_ms = timed(lambda: tc.tc_mlp_train(mlp, g, mot, delta, wts, feat, n_train, seed=12345,
                                                      batch=16384, lr=3e-3, objective=objective))
@@ -292,7 +295,7 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
                   "rel_error_ratio_learned_over_plain": statistics.mean(errs) / max(statistics.mean(plain_errors),
                                                                                     1e-300)}
     mlp.destroy()
-    return {"objective": objective, "train_samples": n_train, "train_ms": train_ms, "features_ms": feat_ms,
+    return {"objective": objective, "train_samples": n_train, "stats_samples": n_stats, "train_ms": train_ms, "features_ms": feat_ms,
             "sample_features_ms": sfeat_ms, "proposal_ms": prop_ms,
             "loss_first_batch": losses[0], "loss_last_batch": losses[1],
             "sampler_ms": q_ms, "samples_per_s": k / (q_ms / 1e3), "estimate": c, "std_err": rq["std_err"],
@@ -605,7 +608,7 @@ def main():
         for obj in objectives:
             comparisons[obj] = learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
                                                   args.train_samples, stream, obj,
-                                                  exact["C"] if exact else None, plain_errors)
+                                                  exact["C"] if exact else None, plain_errors, args.stats_samples)
             if exact:
                 comparisons[obj]["rel_error"] = abs(comparisons[obj]["estimate"] - exact["C"]) / max(exact["C"], 1)
     learned = comparisons.get("closure", comparisons.get("variance"))
