@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--train-samples", type=int, default=10_000_000)
     ap.add_argument("--stats-samples", type=int, default=None,
                     help="plain samples behind the sample-statistics features (default: --train-samples)")
+    ap.add_argument("--eps", type=float, default=0.05, help="the learned proposal's mixture weight: q ~ w (eps + g)")
     ap.add_argument("--objective", default="both", choices=["closure", "variance", "both"],
                     help="training objective of the learned proposal (both: one comparison each, "
                          "the closure loss under 'learned', the variance objective under 'learned_variance')")
@@ -243,7 +244,7 @@ def run_errors(tc, g, mot, delta, wts, C, k, prop=None):
 
 
 def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weights_ms, n_train, stream,
-                       objective="closure", exact_C=None, plain_errors=None, n_stats=None):
+                       objective="closure", exact_C=None, plain_errors=None, n_stats=None, eps=0.05):
     """Learned proposal q ~ w (eps + g) against the plain q ~ w on the same
     graph: features, training on n_train plain samples and the proposal are
     timed once; then k samples with the proposal.  Relative error at a fixed
@@ -266,8 +267,8 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
     _, sfeat_ms = timed(lambda: tc.tc_sample_features(g, mot, delta, wts, feat, n_stats, seed=777))
     mlp = tc.MLP(seed=1)
     losses, train_ms = timed(lambda: tc.tc_mlp_train(mlp, g, mot, delta, wts, feat, n_train, seed=12345,
-                                                     batch=16384, lr=3e-3, objective=objective))
-    prop, prop_ms = timed(lambda: tc.tc_proposal_weights(mlp, g, mot, delta, wts, feat))
+                                                     batch=16384, lr=3e-3, objective=objective, eps=eps))
+    prop, prop_ms = timed(lambda: tc.tc_proposal_weights(mlp, g, mot, delta, wts, feat, eps=eps))
     runs = []
     for i in range(4):
         r, ms = timed(lambda: tc.tc_sample_estimate_q(g, mot, delta, wts, prop, k, seed=0, offset=(50 + i) * k))
@@ -295,7 +296,7 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
                   "rel_error_ratio_learned_over_plain": statistics.mean(errs) / max(statistics.mean(plain_errors),
                                                                                     1e-300)}
     mlp.destroy()
-    return {"objective": objective, "train_samples": n_train, "stats_samples": n_stats, "train_ms": train_ms, "features_ms": feat_ms,
+    return {"objective": objective, "eps": eps, "train_samples": n_train, "stats_samples": n_stats, "train_ms": train_ms, "features_ms": feat_ms,
             "sample_features_ms": sfeat_ms, "proposal_ms": prop_ms,
             "loss_first_batch": losses[0], "loss_last_batch": losses[1],
             "sampler_ms": q_ms, "samples_per_s": k / (q_ms / 1e3), "estimate": c, "std_err": rq["std_err"],
@@ -608,7 +609,8 @@ def main():
         for obj in objectives:
             comparisons[obj] = learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
                                                   args.train_samples, stream, obj,
-                                                  exact["C"] if exact else None, plain_errors, args.stats_samples)
+                                                  exact["C"] if exact else None, plain_errors, args.stats_samples,
+                                                  args.eps)
             if exact:
                 comparisons[obj]["rel_error"] = abs(comparisons[obj]["estimate"] - exact["C"]) / max(exact["C"], 1)
     learned = comparisons.get("closure", comparisons.get("variance"))
