@@ -352,15 +352,21 @@ tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, in
                        void* stream);
 
 /*
- * Training objectives.  TC_OBJECTIVE_CLOSURE: the closure loss above.
+ * Training objectives (the paper has no learned part; the estimator whose
+ * variance the second objective targets is that of Claim 2 with the
+ * proposal's weights).  TC_OBJECTIVE_CLOSURE: the closure loss above.
  * TC_OBJECTIVE_VARIANCE: the estimator's own variance -- with h = eps + g
  * for the proposal's eps, a sample drawn from q ~ w h has second moment
  * proportional to Q * sum over paths of X^2 / h, estimated over a batch of
  * plain samples by mean(h) * mean(X^2 / h); minimising it drives h towards
  * sqrt(E[X^2 | e]), the variance-optimal per-edge proposal.
  * tc_mlp_grad_ex / tc_mlp_train_ex: as tc_mlp_grad / tc_mlp_train with the
- * objective and eps (> 0 for the variance objective); for the variance
- * objective h_loss and h_losses receive the objective's value.
+ * objective and eps (> 0 for the variance objective, else
+ * TC_ERR_INVALID_ARG, as is an unknown objective); d_labels (grad) and the
+ * sampled paths (train) carry the closure counts X.  For the variance
+ * objective h_loss and h_losses receive the objective's value over the
+ * rows or batch (not a per-row mean).  Device buffers are borrowed; the
+ * calls allocate their scratch from the library's pool on the stream.
  */
 #define TC_OBJECTIVE_CLOSURE 0
 #define TC_OBJECTIVE_VARIANCE 1
