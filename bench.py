@@ -262,7 +262,7 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
         return out, a.elapsed_time(b)
 
     feat, feat_ms = timed(lambda: tc.tc_edge_features(g, mot, delta, wts))
-    # sample statistics from n_train plain samples of another seed than the training paths
+    # sample statistics from n_stats plain samples (default n_train) of another seed than the training paths
     n_stats = n_stats or n_train
     _, sfeat_ms = timed(lambda: tc.tc_sample_features(g, mot, delta, wts, feat, n_stats, seed=777))
     mlp = tc.MLP(seed=1)
@@ -296,8 +296,8 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
                   "rel_error_ratio_learned_over_plain": statistics.mean(errs) / max(statistics.mean(plain_errors),
                                                                                     1e-300)}
     mlp.destroy()
-    return {"objective": objective, "eps": eps, "train_samples": n_train, "stats_samples": n_stats, "train_ms": train_ms, "features_ms": feat_ms,
-            "sample_features_ms": sfeat_ms, "proposal_ms": prop_ms,
+    return {"objective": objective, "eps": eps, "train_samples": n_train, "stats_samples": n_stats,
+            "train_ms": train_ms, "features_ms": feat_ms, "sample_features_ms": sfeat_ms, "proposal_ms": prop_ms,
             "loss_first_batch": losses[0], "loss_last_batch": losses[1],
             "sampler_ms": q_ms, "samples_per_s": k / (q_ms / 1e3), "estimate": c, "std_err": rq["std_err"],
             "plain_estimate": plain["estimate"], "plain_std_err": plain["std_err"],
