@@ -1,5 +1,8 @@
 """Pins of the learned-proposal oracle (no GPU): bf16 rounding against
-torch's conversion, features against literal counting, the FP64 backward
+torch's conversion, features against literal counting, the forward against a
+hand-worked two-row network and against torch.nn linear layers loaded from
+the packed parameter layout (plain FP64, and with torch's bf16 rounding of
+weights, inputs and hidden activations), the FP64 backward
 (closure loss and variance objective) against central finite differences,
 the variance objective against hand values, its Cauchy-Schwarz minimiser and
 the exact variance over all paths, the proposal sampler against the plain
@@ -122,6 +125,86 @@ def test_backward_matches_finite_differences():
             fd = (lp - lm) / (2 * h)
             an = grads[name].reshape(-1)[j]
             assert abs(fd - an) <= 1e-6 + 1e-5 * abs(fd), (name, j, fd, an)
+
+
+def _hand_params():
+    """A network whose logits two rows work out by hand (every value is a
+    small dyadic fraction, exact in bf16 and FP64)."""
+    p = {"W1": np.zeros((64, 16)), "b1": np.zeros(64), "W2": np.zeros((64, 64)), "b2": np.zeros(64),
+         "W3": np.zeros(64), "b3": np.array([0.125])}
+    # W1 is [out][in]: hidden unit j = sum_i W1[j][i] x_i + b1[j]
+    p["W1"][0, 0], p["W1"][1, 1], p["W1"][2, 0], p["W1"][2, 15] = 1.0, -2.0, 0.5, 1.0
+    p["b1"][0], p["b1"][1], p["b1"][3] = 0.25, 1.0, -1.0
+    p["W2"][0, 0], p["W2"][1, 1], p["W2"][1, 2], p["W2"][5, 1] = 1.0, 1.0, 2.0, -1.0
+    p["b2"][5] = 0.5
+    p["W3"][0], p["W3"][1], p["W3"][5] = 1.0, -0.5, 2.0
+    return p
+
+
+@pytest.mark.parametrize("quantized,round_acts", [(False, False), (True, True)])
+def test_forward_by_hand(quantized, round_acts):
+    """Row a = (x0 = 2, x1 = 1, x15 = 3):
+       hidden 1: z = (2 + 1/4, -2 + 1, 1 + 3, -1) -> ReLU (9/4, 0, 4, 0)
+       hidden 2: unit 0 = 9/4, unit 1 = 0 + 2 * 4 = 8, unit 5 = -0 + 1/2 = 1/2
+       logit: 9/4 - 8/2 + 2 * 1/2 + 1/8 = -5/8.
+    Row b = (x1 = 1/4): hidden 1 (1/4, 1/2, 0, 0); hidden 2 unit 0 = 1/4,
+       unit 1 = 1/2, unit 5 = -1/2 + 1/2 = 0; logit 1/4 - 1/4 + 0 + 1/8 = 1/8.
+    A transposed W1, a dropped bias or a missing ReLU changes either logit."""
+    x = np.zeros((2, 16))
+    x[0, 0], x[0, 1], x[0, 15] = 2.0, 1.0, 3.0
+    x[1, 1] = 0.25
+    z3, _ = L.mlp_forward(_hand_params(), x, round_acts=round_acts, quantized=quantized)
+    assert z3.tolist() == [-0.625, 0.125]
+    # the same network through the packed layout the library reads
+    z3p, _ = L.mlp_forward(L.unpack(L.pack(_hand_params())), x, round_acts=round_acts, quantized=quantized)
+    assert z3p.tolist() == [-0.625, 0.125]
+
+
+def _torch_net(flat, dtype):
+    """torch.nn layers loaded from the packed layout W1[64][16], b1, W2[64][64],
+    b2, W3[64], b3 (nn.Linear stores its weight as [out][in])."""
+    net = torch.nn.Sequential(torch.nn.Linear(16, 64), torch.nn.ReLU(), torch.nn.Linear(64, 64), torch.nn.ReLU(),
+                              torch.nn.Linear(64, 1)).to(dtype)
+    f = torch.as_tensor(np.asarray(flat, np.float64))
+    o = 0
+    with torch.no_grad():
+        for layer, shape in ((net[0], (64, 16)), (net[2], (64, 64)), (net[4], (1, 64))):
+            n_w = shape[0] * shape[1]
+            layer.weight.copy_(f[o:o + n_w].reshape(shape))
+            o += n_w
+            layer.bias.copy_(f[o:o + shape[0]])
+            o += shape[0]
+    assert o == L.N_PARAMS
+    return net
+
+
+def test_forward_matches_torch_linear_layers():
+    rng = np.random.default_rng(8)
+    params = L.init_params(rng)
+    x = rng.uniform(0, 4, (300, 16))
+    net = _torch_net(L.pack(params), torch.float64)
+    with torch.no_grad():
+        ref = net(torch.as_tensor(x)).numpy()[:, 0]
+    z3, _ = L.mlp_forward(params, x, round_acts=False, quantized=False)
+    np.testing.assert_allclose(z3, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_quantized_forward_matches_torch_bf16_rounding():
+    """bf16 weights and inputs, FP32 biases, hidden activations rounded to
+    bf16 after the ReLU: the same network written with torch's own bfloat16
+    conversion, the products and sums in FP64."""
+    rng = np.random.default_rng(9)
+    params = L.init_params(rng)
+    x = rng.uniform(0, 4, (300, 16))
+    bf = lambda a: torch.as_tensor(np.asarray(a, np.float64)).to(torch.float32).to(torch.bfloat16).to(torch.float64)
+    f32 = lambda a: torch.as_tensor(np.asarray(a, np.float64)).to(torch.float32).to(torch.float64)
+    W1, W2, W3 = bf(params["W1"]), bf(params["W2"]), bf(params["W3"])
+    b1, b2, b3 = f32(params["b1"]), f32(params["b2"]), f32(params["b3"])
+    a1 = torch.relu(bf(x) @ W1.T + b1).to(torch.bfloat16).to(torch.float64)
+    a2 = torch.relu(a1 @ W2.T + b2).to(torch.bfloat16).to(torch.float64)
+    ref = (a2 @ W3 + b3[0]).numpy()
+    z3, _ = L.mlp_forward(params, x, round_acts=True, quantized=True)
+    np.testing.assert_allclose(z3, ref, rtol=1e-12, atol=1e-12)
 
 
 def test_pack_roundtrip_and_size():
