@@ -154,6 +154,16 @@ tc_status tc_graph_info_get(const tc_graph* g, tc_graph_info* h_info);
 tc_status tc_graph_copy(const tc_graph* g, int32_t which, void* d_dst, void* stream);
 
 /*
+ * Canonical edge order (Sec. III: out-lists sorted by time): d_perm[i]
+ * receives the input index of the edge at canonical position i, as int64
+ * (m entries, caller-owned device memory).  Every per-edge array of this
+ * ABI (w, prefix, trace positions) is indexed in this order.  The same
+ * permutation as uint32 is TC_ARRAY_EDGE_PERM of tc_graph_copy.
+ * Errors: TC_ERR_INVALID_ARG (NULL graph or d_perm with m > 0), TC_ERR_CUDA.
+ */
+tc_status tc_graph_edge_order(const tc_graph* g, int64_t* d_perm, void* stream);
+
+/*
  * Bytes of device memory a sampling index needs for graph g: per canonical
  * edge a 32-byte record {int32 u, int32 v, int64 t, uint32 lo1, uint32 d1,
  * uint32 lo3, uint32 d3} (the edge and both window ranges of Alg. 2), a
@@ -201,6 +211,20 @@ tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delt
 tc_status tc_sample_estimate(const tc_graph* g, const tc_motif* motif, int64_t delta,
                              const uint64_t* d_prefix, const void* d_index, uint64_t k, uint64_t seed,
                              uint64_t sample_offset, tc_estimate* h_out, void* stream);
+
+/*
+ * The estimate of Alg. 5 from exact sums: C_hat = sum_x * W / k by exact
+ * 128-bit integer division, q + r / k in FP64, and its standard error
+ * W * sqrt(s^2 / k) with s^2 = (sum_x2 - sum_x^2 / k) / (k - 1) in FP64
+ * (NaN for k = 1; estimate and error 0 for k = 0 or W = 0).  The same
+ * arithmetic tc_sample_estimate applies to one run; this entry point forms
+ * it for sums added up over runs on disjoint sample-id ranges of one seed
+ * (for example one range per GPU).  sum_x2 is 128 bits (lo, hi).  h_out
+ * receives W, k and the sums as given, hits = checked = 0, the estimate and
+ * its error.  Host only.  Errors: TC_ERR_INVALID_ARG (h_out NULL).
+ */
+tc_status tc_estimate_from_sums(uint64_t sum_x, uint64_t sum_x2_lo, uint64_t sum_x2_hi, uint64_t k, uint64_t W,
+                                tc_estimate* h_out);
 
 /*
  * Same sampling as tc_sample_estimate for `count` samples, writing per sample

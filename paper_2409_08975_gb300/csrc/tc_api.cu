@@ -377,6 +377,25 @@ tc_status tc_graph_copy(const tc_graph* g, int32_t which, void* d_dst, void* str
   return TC_OK;
 }
 
+tc_status tc_graph_edge_order(const tc_graph* g, int64_t* d_perm, void* stream) {
+  TC_TRY(check_graph(g));
+  if (!d_perm && g->m > 0) return set_error(TC_ERR_INVALID_ARG, "d_perm is NULL");
+  return launch_widen_u32(g->perm, (uint64_t)g->m, d_perm, S(stream));
+}
+
+tc_status tc_estimate_from_sums(uint64_t sum_x, uint64_t sum_x2_lo, uint64_t sum_x2_hi, uint64_t k, uint64_t W,
+                                tc_estimate* h_out) {
+  if (!h_out) return set_error(TC_ERR_INVALID_ARG, "out is NULL");
+  std::memset(h_out, 0, sizeof(*h_out));
+  h_out->W = W;
+  h_out->k = k;
+  h_out->sum_x = sum_x;
+  h_out->sum_x2_lo = sum_x2_lo;
+  h_out->sum_x2_hi = sum_x2_hi;
+  finish_estimate(h_out);
+  return TC_OK;
+}
+
 tc_status tc_sample_index_bytes(const tc_graph* g, size_t* h_bytes) {
   TC_TRY(check_graph(g));
   if (!h_bytes) return set_error(TC_ERR_INVALID_ARG, "bytes is NULL");

@@ -769,4 +769,21 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   return done(TC_OK);
 }
 
+// Canonical position -> input index widened to int64 (tc_graph_edge_order).
+__global__ void k_widen_u32(const uint32_t* __restrict__ in, uint64_t n, int64_t* __restrict__ out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (int64_t)in[i];
+}
+
+tc_status launch_widen_u32(const uint32_t* in, uint64_t n, int64_t* out, cudaStream_t st) {
+  if (n == 0) return TC_OK;
+  uint64_t blocks = (n + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  k_widen_u32<<<(unsigned)blocks, 256, 0, st>>>(in, n, out);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
 }  // namespace tc

@@ -299,6 +299,8 @@ tc_status scan_u64_in_scratch(const uint64_t* in, uint64_t* out, uint64_t n, boo
 tc_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint64_t n, int bit0,
                            int bit1, cudaStream_t st);
 
+tc_status launch_widen_u32(const uint32_t* in, uint64_t n, int64_t* out, cudaStream_t st);
+
 tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t,
                       cudaStream_t st, tc_graph* g);
 

@@ -4,7 +4,8 @@ Samples are keyed by id, so ranks that draw disjoint id ranges of one seed
 produce partial integer sums whose total is the single-run result.  The only
 exchange is an all-reduce of those integers; values up to 128 bits are split
 into 32-bit limbs so that int64 tensor sums stay exact for any world size
-below 2^31.
+below 2^31.  The estimate of the merged sums is formed by the library
+(tc_estimate_from_sums), the same arithmetic as a single run's.
 """
 import torch
 import torch.distributed as dist
@@ -32,7 +33,7 @@ def merge_runs(local, W, group=None, device="cpu"):
     """Merge this rank's run {sum_x, sum_x2, hits, k} into the global
     estimate of Alg. 5 (C_hat = sum_x * W / k) and its standard error."""
     sx, sx2, hits, k = allreduce_exact([local["sum_x"], local["sum_x2"], local["hits"], local["k"]], group, device)
-    est, se = tc.estimate_from_sums(sx, sx2, k, W)
+    est, se = tc.tc_estimate_from_sums(sx, sx2, k, W)
     return {"sum_x": sx, "sum_x2": sx2, "hits": hits, "k": k, "W": int(W), "estimate": est, "std_err": se}
 
 
@@ -48,7 +49,7 @@ def merge_batch(local, group=None, device="cpu"):
     out = []
     for j, r in enumerate(local):
         sx, sx2, hits, k = tot[4 * j:4 * j + 4]
-        est, se = tc.estimate_from_sums(sx, sx2, k, r["W"])
+        est, se = tc.tc_estimate_from_sums(sx, sx2, k, r["W"])
         out.append({"sum_x": sx, "sum_x2": sx2, "hits": hits, "k": k, "W": int(r["W"]), "estimate": est,
                     "std_err": se})
     return out

@@ -72,6 +72,8 @@ def lib():
             "tc_graph_destroy": [vp],
             "tc_graph_info_get": [vp, ctypes.POINTER(tc_graph_info)],
             "tc_graph_copy": [vp, i32, vp, vp],
+            "tc_graph_edge_order": [vp, vp, vp],
+            "tc_estimate_from_sums": [u64, u64, u64, u64, u64, ctypes.POINTER(tc_estimate)],
             "tc_sample_index_bytes": [vp, ctypes.POINTER(sz)],
             "tc_path_weights": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, vp, ctypes.POINTER(u64), vp],
             "tc_sample_estimate": [vp, ctypes.POINTER(tc_motif), i64, vp, vp, u64, u64, u64,
@@ -228,6 +230,13 @@ def tc_build_temporal_csr(n, src, dst, t, stream=None):
     return Graph(h)
 
 
+def tc_graph_edge_order(g, stream=None):
+    """int64 CUDA tensor: input index of the edge at each canonical position."""
+    out = torch.empty(max(g.m, 1), dtype=torch.int64, device="cuda")
+    _check(lib().tc_graph_edge_order(g.handle, _ptr(out), _stream(stream)), "tc_graph_edge_order")
+    return out[:g.m]
+
+
 def tc_sample_index_bytes(g):
     b = ctypes.c_size_t()
     _check(lib().tc_sample_index_bytes(g.handle, ctypes.byref(b)), "tc_sample_index_bytes")
@@ -322,19 +331,15 @@ def tc_prefix_sum_noalloc(w, m, prefix, want_W=True, stream=None):
     return W.value if want_W else None
 
 
-def estimate_from_sums(sum_x, sum_x2, k, W):
-    """Merge helper for partial runs over disjoint sample ranges: the same
-    host formula as the library (Alg. 5), applied to summed integers."""
-    import math
-    if k == 0 or W == 0:
-        return 0.0, 0.0
-    q, r = divmod(int(sum_x) * int(W), int(k))
-    est = float(q) + float(r) / float(k)
-    if k < 2:
-        return est, float("nan")
-    sx, sx2, kf = float(sum_x), float(sum_x2), float(k)
-    s2 = max((sx2 - sx * sx / kf) / (kf - 1.0), 0.0)
-    return est, float(W) * math.sqrt(s2 / kf)
+def tc_estimate_from_sums(sum_x, sum_x2, k, W):
+    """Alg. 5's estimate and standard error from exact sums (for example the
+    sums of runs over disjoint sample-id ranges, added up), formed by the
+    library; sum_x2 is a Python int below 2^128.  Host only."""
+    sum_x2 = int(sum_x2)
+    e = tc_estimate()
+    _check(lib().tc_estimate_from_sums(int(sum_x), sum_x2 & 0xFFFFFFFFFFFFFFFF, sum_x2 >> 64, int(k), int(W),
+                                       ctypes.byref(e)), "tc_estimate_from_sums")
+    return e.estimate, e.std_err
 
 
 # ---------------------------------------------------------------------------

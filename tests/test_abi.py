@@ -78,3 +78,28 @@ def test_null_arguments_rejected(libtc):
     assert libtc.tc_path_weights(None, ctypes.byref(m), 5, None, None, None, None, None) == 1
     est = tc.tc_estimate()
     assert libtc.tc_sample_estimate(None, ctypes.byref(m), 5, None, None, 1, 0, 0, ctypes.byref(est), None) == 1
+
+
+def test_estimate_from_sums_matches_the_oracle(libtc):
+    """Alg. 5's final step through the ABI (host only) against the oracle's
+    exact-rational form, including sums of squares above 2^64 and the
+    degenerate k = 0, k = 1 and W = 0 cases."""
+    import math
+    import random
+    from paper_2409_08975_gb300 import tc
+    import oracle
+    rng = random.Random(3)
+    cases = [(0, 0, 0, 5), (7, 49, 1, 9), (0, 0, 10, 0), (3, 9, 2, 1 << 63)]
+    for _ in range(200):
+        k = rng.randrange(2, 1 << 40)
+        sx = rng.randrange(0, 1 << 63)
+        sx2 = rng.randrange(sx, 1 << 127)
+        cases.append((sx, sx2, k, rng.randrange(1, 1 << 64)))
+    for sx, sx2, k, W in cases:
+        est, se = tc.tc_estimate_from_sums(sx, sx2, k, W)
+        ref, rse = oracle.estimate(sx, sx2, k, W)
+        assert est == ref, (sx, sx2, k, W)
+        if math.isnan(rse):
+            assert math.isnan(se)
+        else:
+            assert se == pytest.approx(rse, rel=1e-12, abs=0.0)

@@ -1,6 +1,7 @@
-"""Two ranks on CPU (gloo) draw disjoint sample-id ranges of one seed with
-the oracle; the exact integer all-reduce of paper_2409_08975_gb300.dist gives
-the single-run sums and estimate."""
+"""Two and three ranks on CPU (gloo) draw disjoint sample-id ranges of one
+seed with the oracle; the exact integer all-reduce of
+paper_2409_08975_gb300.dist gives the single-run sums, and the library's
+tc_estimate_from_sums (host arithmetic, no GPU needed) the estimate."""
 import os
 import socket
 
@@ -64,8 +65,14 @@ def _batch_worker(rank, world, port, queue):
     dist.destroy_process_group()
 
 
+def _built():
+    from paper_2409_08975_gb300 import _build
+    _build.build()  # once, before the ranks load the library
+
+
 @pytest.mark.parametrize("world", [2, 3])
 def test_batch_runs_merge_per_query(world):
+    _built()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -95,6 +102,7 @@ def _free_port():
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_disjoint_ranges_merge_to_single_run(world):
+    _built()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
