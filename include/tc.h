@@ -264,8 +264,10 @@ tc_status tc_estimate_from_host(int64_t n, int64_t m, const int32_t* h_src, cons
  * TC_ERR_INVALID_ARG.  Every call shares that array: calls whose work
  * overlaps on the GPU (different streams, or several host threads) race and
  * must be serialised by the caller.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Overflow of W is detected on the device and reported
+ * array's device address (cudaGetSymbolAddress) and keeps it for that
+ * device's current context; the first call after a device reset (a new
+ * context) looks it up again.  Make the first call on a device before any
+ * stream capture.  Overflow of W is detected on the device and reported
  * only when h_W is requested.
  */
 #define TC_NOALLOC_MAX_EDGES (1ull << 28)

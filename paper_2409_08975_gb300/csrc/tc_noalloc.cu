@@ -2,6 +2,7 @@
 // allocation, for callers that cannot allocate device memory (see tc.h).
 // Its scratch (the scan's per-tile sums and an error word) is one file-scope
 // device array that every device loading this library holds until exit.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,24 +26,69 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned long long* g_scratch_addr[kMaxDevices] = {};
+
+// The looked-up address per device, valid for the context it was looked up
+// in: a device reset destroys that context and unloads the module, so the
+// address is looked up again whenever the current context differs.
+struct ScratchAddr {
+  unsigned long long ctx_id;
+  unsigned long long* ptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
+
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context (driver entry points
+// reached through the runtime, so the library does not link libcuda).
+tc_status current_context_id(int dev, unsigned long long* id) {
+  static ctx_get_current_fn get_current = nullptr;
+  static ctx_get_id_fn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || !f1)
+      return tc::set_error(TC_ERR_CUDA, "cuCtxGetCurrent entry point unavailable");
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess || !f2)
+      return tc::set_error(TC_ERR_CUDA, "cuCtxGetId entry point unavailable");
+    get_current = (ctx_get_current_fn)f1;
+    get_id = (ctx_get_id_fn)f2;
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) {
+    // no context current yet: make the device's primary context current
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return tc::cuda_status(e, "cudaSetDevice");
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return tc::set_error(TC_ERR_CUDA, "no current CUDA context");
+  }
+  if (get_id(ctx, id) != CUDA_SUCCESS) return tc::set_error(TC_ERR_CUDA, "cuCtxGetId failed");
+  return TC_OK;
+}
 
 // Device address of the scratch array on the current device.  The name
 // g_noalloc_scratch in host code is only a host-side stand-in, so the
-// address is looked up once per device with that device current.
+// address is looked up with that device current: once per device and
+// context (again after a device reset).
 tc_status scratch_on_current_device(unsigned long long** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return tc::cuda_status(e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return tc::set_error(TC_ERR_INVALID_ARG, "device index beyond 63");
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  unsigned long long ctx_id = 0;
+  TC_TRY(current_context_id(dev, &ctx_id));
+  ScratchAddr& a = g_scratch_addr[dev];
+  if (!a.ptr || a.ctx_id != ctx_id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return tc::cuda_status(e, "cudaGetSymbolAddress");
-    g_scratch_addr[dev] = (unsigned long long*)p;
+    a.ptr = (unsigned long long*)p;
+    a.ctx_id = ctx_id;
   }
-  *out = g_scratch_addr[dev];
+  *out = a.ptr;
   return TC_OK;
 }
 

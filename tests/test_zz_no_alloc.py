@@ -67,3 +67,31 @@ def test_noalloc_rejects_beyond_maximum(tc):
     assert e.value.status == 1
     assert "TC_NOALLOC_MAX_EDGES" in str(e.value)
     assert out.cpu().tolist() == [0, 0, 0, 0]
+
+
+def test_noalloc_two_scan_levels_match_cumsum(tc):
+    """More than 2048 x 2048 weights: the scan's second level of tile sums
+    sits after the first in the static array."""
+    import torch
+    m = 5_000_003
+    g = torch.Generator(device="cpu").manual_seed(4)
+    w = torch.randint(0, 1 << 20, (m,), generator=g, dtype=torch.int64).cuda()
+    ref = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+    ref[1:] = torch.cumsum(w, 0)
+    out = torch.full((m + 1,), -1, dtype=torch.int64, device="cuda")
+    for _ in range(2):  # twice in a row on the same array
+        W = tc.tc_prefix_sum_noalloc(w, m, out)
+        torch.cuda.synchronize()
+        assert W == int(ref[-1])
+        assert torch.equal(out, ref)
+
+
+def test_noalloc_reports_overflow(tc):
+    import torch
+    w = torch.tensor([1 << 62, 1 << 62, 1 << 62, 1 << 62], dtype=torch.int64, device="cuda")
+    out = torch.empty(5, dtype=torch.int64, device="cuda")
+    with pytest.raises(tc.TcError) as e:
+        tc.tc_prefix_sum_noalloc(w, 4, out)
+    assert e.value.status == 3
+    # the error word starts from zero again on the next call
+    assert tc.tc_prefix_sum_noalloc(w, 2, out) == 1 << 63
