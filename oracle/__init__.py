@@ -18,6 +18,8 @@ Contents (each function names the passage it follows):
                              (proof of Claim 2: equals the exact count C)
   * ``exact_count``       -- chronological backtracking count of M-matches (Def. 2)
   * ``brute_force_count`` -- literal Def. 2 over all edge tuples (tiny graphs)
+  * ``set_threads``       -- OpenMP threads of the loops above (default 1:
+                             serial; integer results identical)
   * ``estimate``          -- C_hat = (sum X / k) * W (Alg. 5) and its standard error
   * ``learned``           -- features, FP64 network, proposal sampler (learned proposal)
 

@@ -49,6 +49,15 @@ def _declare(L):
     L.or_path_sum.restype = ctypes.c_int
     L.or_exact_count.argtypes = [i64, i64] + [vp] * 3 + [vp] * 8 + [i32, vp, vp, i64, ctypes.POINTER(u64)]
     L.or_exact_count.restype = ctypes.c_int
+    L.or_set_threads.argtypes = [ctypes.c_int]
+    L.or_set_threads.restype = ctypes.c_int
+
+
+def set_threads(n):
+    """Threads of the oracle's parallel loops (weights, sampler, path sum,
+    backtracking count); 1 (the default) runs them serially.  Results do not
+    depend on it.  Returns the number in use (1 without OpenMP)."""
+    return int(lib().or_set_threads(int(n)))
 
 
 class OracleError(RuntimeError):

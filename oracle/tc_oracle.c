@@ -27,10 +27,19 @@
  * rejects ties among anchor edges.
  *
  * Status codes: 0 ok, 3 overflow, 6 RNG attempts exhausted, 1 invalid.
+ *
+ * Threads: serial by default.  or_set_threads(n > 1) runs the per-edge loop
+ * of the weights, the per-sample loop of the sampler, the per-middle-edge
+ * loop of the path sum and the first-edge loop of the backtracking count on
+ * n OpenMP threads.  Every iteration is independent and every sum is an
+ * integer, so the results are identical to the serial ones.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef unsigned __int128 u128;
 
@@ -38,6 +47,19 @@ typedef unsigned __int128 u128;
 #define OR_INVALID 1
 #define OR_OVERFLOW 3
 #define OR_RNG_EXHAUSTED 6
+
+static int or_threads = 1;
+
+/* Threads of the parallel loops (1 = serial); returns the number in use. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  or_threads = n > 1 ? n : 1;
+#else
+  (void)n;
+  or_threads = 1;
+#endif
+  return or_threads;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Sorting into the three list orders (Sec. III: lists sorted by timestamp). */
@@ -263,6 +285,7 @@ int or_path_weights(int64_t n, int64_t m, const int32_t *src, const int32_t *dst
   or_graph g = {n, m, src, dst, t, out_perm, out_off, in_perm, in_off, 0, 0, 0, 0};
   or_plan pl;
   read_plan(plan_arr, &pl);
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1)
   for (int64_t i = 0; i < m; i++) {
     int64_t e = out_perm[i];
     int64_t a, b, c, d;
@@ -533,6 +556,39 @@ static uint64_t anchor_check(const or_graph *g, const or_plan *pl, int64_t delta
 }
 
 /*
+ * One sample (Alg. 2, then Alg. 3): sample id s draws the middle edge and the
+ * two end edges; *X receives CheckMotif of the path and (i2, p1, p3) its
+ * canonical middle edge and end-edge list positions.  Returns a status.
+ */
+static int sample_one(const or_graph *g, const or_plan *pl, int64_t delta, const uint64_t *prefix,
+                      uint64_t W, uint64_t seed, uint64_t s, int64_t *i2_out, int64_t *p1_out,
+                      int64_t *p3_out, uint64_t *X, int *ovf) {
+  uint64_t r2, r1, r3;
+  int st = or_bounded(seed, s, 0, W, &r2);
+  if (st) return st;
+  /* middle edge: the unique i2 with prefix[i2] <= r2 < prefix[i2+1] */
+  int64_t lo = 0, hi = g->m; /* invariant: prefix[lo] <= r2 < prefix[hi] */
+  while (hi - lo > 1) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (prefix[mid] <= r2) lo = mid; else hi = mid;
+  }
+  int64_t i2 = lo, e2 = g->out_perm[i2];
+  int64_t a, b, c, d;
+  anchor_windows(g, pl, e2, delta, &a, &b, &c, &d);
+  /* e1 and e3 from the two halves of block 1; a wedge's unused end has
+   * range 1 (r = 0) */
+  st = or_bounded(seed, s, 1, (uint64_t)(b - a), &r1);
+  if (st) return st;
+  st = or_bounded_hi(seed, s, 1, (uint64_t)(d - c), &r3);
+  if (st) return st;
+  *i2_out = i2;
+  *p1_out = a + (int64_t)r1;
+  *p3_out = c + (int64_t)r3;
+  *X = anchor_check(g, pl, delta, i2, *p1_out, *p3_out, ovf);
+  return OR_OK;
+}
+
+/*
  * Sample + CheckMotif for sample ids offset .. offset+k-1 (Alg. 2, Alg. 5's
  * loop).  prefix has m+1 entries (prefix[m] = W).  Optional trace[4*k]
  * receives (i2, p1, p3, X) per sample.  sums[0..4] = (sum X, sum X^2 low,
@@ -551,41 +607,46 @@ int or_sample_run(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, 
   uint64_t W = prefix[m];
   uint64_t sx = 0, hits = 0;
   u128 sx2 = 0;
-  int ovf = 0;
+  int ovf = 0, status = OR_OK;
   if (W == 0) { sums[0] = sums[1] = sums[2] = sums[3] = 0; sums[4] = k; return OR_OK; }
-  for (uint64_t i = 0; i < k; i++) {
-    uint64_t s = offset + i, r2, r1, r3;
-    int st = or_bounded(seed, s, 0, W, &r2);
-    if (st) return st;
-    /* middle edge: the unique i2 with prefix[i2] <= r2 < prefix[i2+1] */
-    int64_t lo = 0, hi = m; /* invariant: prefix[lo] <= r2 < prefix[hi] */
-    while (hi - lo > 1) {
-      int64_t mid = lo + (hi - lo) / 2;
-      if (prefix[mid] <= r2) lo = mid; else hi = mid;
+#pragma omp parallel num_threads(or_threads) if (or_threads > 1)
+  {
+    uint64_t tsx = 0, thits = 0;
+    u128 tsx2 = 0;
+    int tovf = 0, tst = OR_OK;
+#pragma omp for schedule(static)
+    for (uint64_t i = 0; i < k; i++) {
+      if (tst) continue;
+      int64_t i2, p1, p3;
+      uint64_t X;
+      int st = sample_one(&g, &pl, delta, prefix, W, seed, offset + i, &i2, &p1, &p3, &X, &tovf);
+      if (st) { tst = st; continue; }
+      if (trace) {
+        trace[4 * i + 0] = (uint64_t)i2; trace[4 * i + 1] = (uint64_t)p1;
+        trace[4 * i + 2] = (uint64_t)p3; trace[4 * i + 3] = X;
+      }
+      uint64_t s1 = tsx + X;
+      if (s1 < tsx) tovf = 1;
+      tsx = s1;
+      u128 x2 = (u128)X * X, s2 = tsx2 + x2;
+      if (s2 < tsx2) tovf = 1;
+      tsx2 = s2;
+      thits += X > 0;
     }
-    int64_t i2 = lo, e2 = out_perm[i2];
-    int64_t a, b, c, d;
-    anchor_windows(&g, &pl, e2, delta, &a, &b, &c, &d);
-    /* e1 and e3 from the two halves of block 1; a wedge's unused end has
-     * range 1 (r = 0) */
-    st = or_bounded(seed, s, 1, (uint64_t)(b - a), &r1);
-    if (st) return st;
-    st = or_bounded_hi(seed, s, 1, (uint64_t)(d - c), &r3);
-    if (st) return st;
-    int64_t p1 = a + (int64_t)r1, p3 = c + (int64_t)r3;
-    uint64_t X = anchor_check(&g, &pl, delta, i2, p1, p3, &ovf);
-    if (trace) {
-      trace[4 * i + 0] = (uint64_t)i2; trace[4 * i + 1] = (uint64_t)p1;
-      trace[4 * i + 2] = (uint64_t)p3; trace[4 * i + 3] = X;
+#pragma omp critical
+    {
+      uint64_t s1 = sx + tsx;
+      if (s1 < sx) ovf = 1;
+      sx = s1;
+      u128 s2 = sx2 + tsx2;
+      if (s2 < sx2) ovf = 1;
+      sx2 = s2;
+      hits += thits;
+      ovf |= tovf;
+      if (tst && !status) status = tst;
     }
-    uint64_t s1 = sx + X;
-    if (s1 < sx) ovf = 1;
-    sx = s1;
-    u128 x2 = (u128)X * X, s2 = sx2 + x2;
-    if (s2 < sx2) ovf = 1;
-    sx2 = s2;
-    hits += X > 0;
   }
+  if (status) return status;
   sums[0] = sx; sums[1] = (uint64_t)sx2; sums[2] = (uint64_t)(sx2 >> 64); sums[3] = hits; sums[4] = k;
   return ovf ? OR_OVERFLOW : OR_OK;
 }
@@ -609,17 +670,31 @@ int or_path_sum(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, co
   uint64_t sx = 0, paths = 0;
   u128 sx2 = 0;
   int ovf = 0;
-  for (int64_t i2 = 0; i2 < m; i2++) {
-    int64_t e2 = out_perm[i2];
-    int64_t a, b, c, d;
-    anchor_windows(&g, &pl, e2, delta, &a, &b, &c, &d);
-    for (int64_t p1 = a; p1 < b; p1++)
-      for (int64_t p3 = c; p3 < d; p3++) {
-        uint64_t X = anchor_check(&g, &pl, delta, i2, p1, p3, &ovf);
-        sx += X;
-        sx2 += (u128)X * X;
-        paths++;
-      }
+#pragma omp parallel num_threads(or_threads) if (or_threads > 1)
+  {
+    uint64_t tsx = 0, tpaths = 0;
+    u128 tsx2 = 0;
+    int tovf = 0;
+#pragma omp for schedule(dynamic, 1024)
+    for (int64_t i2 = 0; i2 < m; i2++) {
+      int64_t e2 = out_perm[i2];
+      int64_t a, b, c, d;
+      anchor_windows(&g, &pl, e2, delta, &a, &b, &c, &d);
+      for (int64_t p1 = a; p1 < b; p1++)
+        for (int64_t p3 = c; p3 < d; p3++) {
+          uint64_t X = anchor_check(&g, &pl, delta, i2, p1, p3, &tovf);
+          tsx += X;
+          tsx2 += (u128)X * X;
+          tpaths++;
+        }
+    }
+#pragma omp critical
+    {
+      sx += tsx;
+      sx2 += tsx2;
+      paths += tpaths;
+      ovf |= tovf;
+    }
   }
   out[0] = sx; out[1] = (uint64_t)sx2; out[2] = (uint64_t)(sx2 >> 64); out[3] = paths;
   return ovf ? OR_OVERFLOW : OR_OK;
@@ -703,12 +778,50 @@ int or_exact_count(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
   qsort(tperm, (size_t)m, sizeof(int64_t), cmp_time);
   int ms[16], md[16];
   for (int i = 0; i < r; i++) { ms[i] = msrc[i]; md[i] = mdst[i]; }
-  bt_state S;
-  memset(&S, 0, sizeof S);
-  S.g = &g; S.tperm = tperm; S.r = r; S.msrc = ms; S.mdst = md; S.delta = delta;
-  *count = m ? bt(&S, 0, 0, INT64_MIN) : 0;
+  uint64_t total = 0;
+  int ovf = 0;
+  if (or_threads <= 1) {
+    bt_state S;
+    memset(&S, 0, sizeof S);
+    S.g = &g; S.tperm = tperm; S.r = r; S.msrc = ms; S.mdst = md; S.delta = delta;
+    total = m ? bt(&S, 0, 0, INT64_MIN) : 0;
+    ovf = S.ovf;
+  } else {
+    /* the first motif edge's loop of bt() split over threads: iteration p
+     * maps motif edge 0 to the p-th edge in time order and counts the
+     * completions of that partial match */
+#pragma omp parallel num_threads(or_threads)
+    {
+      bt_state S;
+      memset(&S, 0, sizeof S);
+      S.g = &g; S.tperm = tperm; S.r = r; S.msrc = ms; S.mdst = md; S.delta = delta;
+      uint64_t part = 0;
+#pragma omp for schedule(dynamic, 256)
+      for (int64_t p = 0; p < m; p++) {
+        int64_t e = tperm[p];
+        int64_t gs = g.src[e], gd = g.dst[e];
+        if (gs == gd) continue;
+        S.mapped[ms[0]] = 1; S.phi[ms[0]] = gs;
+        S.mapped[md[0]] = 1; S.phi[md[0]] = gd;
+        uint64_t c = bt(&S, 1, g.t[e], g.t[e]);
+        S.mapped[ms[0]] = 0;
+        S.mapped[md[0]] = 0;
+        uint64_t s2 = part + c;
+        if (s2 < part) S.ovf = 1;
+        part = s2;
+      }
+#pragma omp critical
+      {
+        uint64_t s2 = total + part;
+        if (s2 < total) ovf = 1;
+        total = s2;
+        ovf |= S.ovf;
+      }
+    }
+  }
+  *count = total;
   free(tperm);
-  return S.ovf ? OR_OVERFLOW : OR_OK;
+  return ovf ? OR_OVERFLOW : OR_OK;
 }
 
 /* ------------------------------------------------------------------------ */

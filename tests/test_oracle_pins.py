@@ -352,3 +352,30 @@ def test_estimate_exact_integer_division():
         assert c == pytest.approx(float(Fraction(sx * W, k)), rel=1e-15)
     # standard error of a constant sample is zero
     assert oracle.estimate(30, 90, 10, 4)[1] == 0.0
+
+
+def test_threaded_oracle_equals_serial():
+    """The OpenMP loops (weights, sampler with trace, path sum, backtracking
+    count) give the serial results exactly."""
+    from _graphs import small_random_graph
+    src, dst, t = small_random_graph(91, 9, 400, 300, dup_frac=0.3)
+    g = oracle.build_csr(9, src, dst, t)
+    plan = oracle.compile_motif(C4)
+    res = []
+    try:
+        for threads in (1, 4):
+            assert oracle.set_threads(threads) in (1, threads)
+            pw = oracle.path_weights(g, plan, 40)
+            pre = oracle.prefix_sum(pw["w"])
+            sums, tr = oracle.sample_run(g, plan, 40, pre, 5000, 3, 11, trace=True)
+            res.append((pw["w"].copy(), pw["lo1"].copy(), pw["d3"].copy(), sums, tr.copy(),
+                        oracle.path_sum(g, plan, 40), oracle.exact_count(g, C4, 40)))
+    finally:
+        oracle.set_threads(1)
+    a, b = res
+    for x, y in zip(a, b):
+        if isinstance(x, np.ndarray):
+            assert np.array_equal(x, y)
+        else:
+            assert x == y
+    assert a[5]["C"] == a[6] > 0
