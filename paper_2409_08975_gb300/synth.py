@@ -224,6 +224,30 @@ def large(seed=1005):
 BATCH_DELTAS = (600, 3600, 86400)
 
 
+def time_slice(g, j, parts=100):
+    """Contiguous time slice j of `parts` of graph g, each holding about
+    1 / parts of the edges: with t_(i) the i-th smallest time and m edges,
+    the edges with t_(j m / parts) <= t < t_((j + 1) m / parts) (no upper
+    bound for the last slice), in input order, with the vertices that occur
+    renumbered 0..n'-1 in increasing order of their ids (which keeps every
+    list order).  Returns a graph dict with the slice's time bounds."""
+    t = g["t"]
+    m = len(t)
+    k0, k1 = j * m // parts, (j + 1) * m // parts
+    ks = [k0] + ([k1] if j + 1 < parts else [])
+    part = np.partition(t, ks)
+    lo = int(part[k0])
+    hi = int(part[k1]) if j + 1 < parts else None
+    sel = np.flatnonzero((t >= lo) & (t < hi)) if hi is not None else np.flatnonzero(t >= lo)
+    src, dst = g["src"][sel], g["dst"][sel]
+    verts, inv = np.unique(np.concatenate([src, dst]), return_inverse=True)
+    out = {k: v for k, v in g.items() if k not in ("src", "dst", "t", "n")}
+    out.update({"name": "%s_slice%d_of%d" % (g.get("name", "graph"), j, parts), "n": int(max(len(verts), 1)),
+                "src": inv[:len(sel)].astype(np.int32), "dst": inv[len(sel):].astype(np.int32),
+                "t": t[sel].copy(), "t_lo": lo, "t_hi": hi, "m_parent": m})
+    return out
+
+
 def small(seed=1007):
     """Profiling case: the mid generator at n = 5e5, m = 1e7 (graph and index
     about 1 GB, several times L2), path+chord, delta = 3600, k = 1e7."""

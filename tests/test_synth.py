@@ -88,3 +88,28 @@ def test_batch_queries_shape():
     assert len(orders) == 24 and all(sorted(o) == sorted(synth.C4) for o in orders)
     assert all(1e3 <= q[3] <= 1e4 for q in cfg["queries"])
     assert cfg["k"] == sum(q[3] for q in cfg["queries"])
+
+
+def test_time_slices_partition_the_graph():
+    """Contiguous time slices of about 1 / parts of the edges each: every edge
+    falls in exactly one slice, inside its time bounds, and renumbering keeps
+    the vertex order."""
+    g = synth.scaled_mid(20_000, 300_000, seed=5)
+    parts = 10
+    total = 0
+    seen = np.zeros(len(g["t"]), np.int64)
+    for j in range(parts):
+        s = synth.time_slice(g, j, parts)
+        m = len(s["src"])
+        total += m
+        assert abs(m - len(g["t"]) / parts) <= 0.05 * len(g["t"]) / parts
+        assert (s["t"] >= s["t_lo"]).all()
+        if s["t_hi"] is not None:
+            assert (s["t"] < s["t_hi"]).all()
+        sel = np.flatnonzero((g["t"] >= s["t_lo"]) & ((g["t"] < s["t_hi"]) if s["t_hi"] is not None else True))
+        seen[sel] += 1
+        assert np.array_equal(s["t"], g["t"][sel])
+        ids = np.unique(np.concatenate([g["src"][sel], g["dst"][sel]]))
+        assert np.array_equal(ids[s["src"]], g["src"][sel]) and np.array_equal(ids[s["dst"]], g["dst"][sel])
+        assert s["n"] == len(ids)
+    assert total == len(g["t"]) and (seen == 1).all()
