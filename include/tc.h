@@ -381,6 +381,8 @@ tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, in
  * Training objectives (the paper has no learned part; the estimator whose
  * variance the second objective targets is that of Claim 2 with the
  * proposal's weights).  TC_OBJECTIVE_CLOSURE: the closure loss above.
+ * TC_OBJECTIVE_BCE: the binary cross-entropy of g against the closure
+ * outcome 1[X > 0] (the closure loss on labels clipped to 1).
  * TC_OBJECTIVE_VARIANCE: the estimator's own variance -- with h = eps + g
  * for the proposal's eps, a sample drawn from q ~ w h has second moment
  * proportional to Q * sum over paths of X^2 / h, estimated over a batch of
@@ -396,6 +398,7 @@ tc_status tc_mlp_train(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, in
  */
 #define TC_OBJECTIVE_CLOSURE 0
 #define TC_OBJECTIVE_VARIANCE 1
+#define TC_OBJECTIVE_BCE 2
 tc_status tc_mlp_grad_ex(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, const float* d_labels,
                          uint64_t n, int32_t objective, float eps, float* d_grad, float* h_loss, void* stream);
 tc_status tc_mlp_train_ex(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif, int64_t delta,

@@ -684,23 +684,28 @@ tc_status tc_mlp_grad(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t*
 tc_status tc_mlp_grad_ex(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, const float* d_labels,
                          uint64_t n, int32_t objective, float eps, float* d_grad, float* h_loss, void* stream) {
   if (!mlp || !d_grad || (n && (!d_feat || !d_labels))) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
-  if (objective != TC_OBJECTIVE_CLOSURE && objective != TC_OBJECTIVE_VARIANCE)
+  if (objective != TC_OBJECTIVE_CLOSURE && objective != TC_OBJECTIVE_VARIANCE && objective != TC_OBJECTIVE_BCE)
     return set_error(TC_ERR_INVALID_ARG, "unknown training objective");
   if (objective == TC_OBJECTIVE_VARIANCE && !(eps > 0.f)) return set_error(TC_ERR_INVALID_ARG, "eps must be > 0");
-  const bool var = objective == TC_OBJECTIVE_VARIANCE;
+  const bool var = objective == TC_OBJECTIVE_VARIANCE, bce = objective == TC_OBJECTIVE_BCE;
   cudaStream_t st = S(stream);
-  float* buf = nullptr;  // loss, spare float, then (variance) logits and dloss/dz
-  TC_CUDA(pool_malloc(&buf, sizeof(float) * (2 + (var ? 2 * (n ? n : 1) : 0)), st));
+  // loss, spare float, then (variance) logits and dloss/dz or (BCE) the clipped labels
+  float* buf = nullptr;
+  TC_CUDA(pool_malloc(&buf, sizeof(float) * (2 + (var ? 2 * (n ? n : 1) : (bce ? (n ? n : 1) : 0))), st));
   float* loss = buf;
   tc_status s = TC_OK;
   cudaError_t e = cudaMemsetAsync(d_grad, 0, sizeof(float) * TC_MLP_PARAMS, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, sizeof(float) * 2, st);
   if (e != cudaSuccess) s = cuda_status(e, "memset");
   if (s == TC_OK) {
-    if (var)
+    if (var) {
       s = launch_variance_grad(mlp, d_feat, d_rows, d_labels, n, eps, d_grad, loss, buf + 2, buf + 2 + n, buf + 1, st);
-    else
+    } else if (bce) {
+      s = launch_clip_labels(d_labels, n, buf + 2, st);
+      if (s == TC_OK) s = launch_mlp_grad(mlp, d_feat, d_rows, buf + 2, n, d_grad, loss, st);
+    } else {
       s = launch_mlp_grad(mlp, d_feat, d_rows, d_labels, n, d_grad, loss, st);
+    }
   }
   float hl = 0.f;
   if (s == TC_OK) {
@@ -725,7 +730,7 @@ tc_status tc_mlp_train_ex(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif,
                           const uint64_t* d_prefix, const void* d_index, const uint16_t* d_feat,
                           uint64_t n_samples, uint64_t seed, uint32_t batch, float lr, int32_t objective,
                           float eps, float* h_losses, void* stream) {
-  if (objective != TC_OBJECTIVE_CLOSURE && objective != TC_OBJECTIVE_VARIANCE)
+  if (objective != TC_OBJECTIVE_CLOSURE && objective != TC_OBJECTIVE_VARIANCE && objective != TC_OBJECTIVE_BCE)
     return set_error(TC_ERR_INVALID_ARG, "unknown training objective");
   if (objective == TC_OBJECTIVE_VARIANCE && !(eps > 0.f)) return set_error(TC_ERR_INVALID_ARG, "eps must be > 0");
   TC_TRY(check_graph(g));
@@ -756,7 +761,7 @@ tc_status tc_mlp_train_ex(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif,
   if (e != cudaSuccess) s = cuda_status(e, "tc_mlp_train allocation");
   // training paths from the plain sampler: rows = middle edges, labels = closure counts X
   if (s == TC_OK) s = launch_sampler(g, plan, delta, d_prefix, d_index, n_samples, seed, 0, trace, sums, st);
-  if (s == TC_OK) s = launch_trace_to_rows(trace, n_samples, rows, labels, st);
+  if (s == TC_OK) s = launch_trace_to_rows(trace, n_samples, rows, labels, st, objective == TC_OBJECTIVE_BCE);
   for (uint64_t b = 0; b < steps && s == TC_OK; b++) {
     const uint64_t lo = b * batch, nb = (n_samples - lo) < batch ? (n_samples - lo) : batch;
     if (var)

@@ -335,7 +335,9 @@ tc_status mlp_adam(tc_mlp* M, float lr, cudaStream_t st);
 float* mlp_grad_buffer(tc_mlp* M);
 tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint64_t n, int64_t delta,
                                  uint16_t* feat, uint32_t* d_err, cudaStream_t st);
-tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st);
+tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st,
+                               bool clip = false);
+tc_status launch_clip_labels(const float* labels, uint64_t n, float* out, cudaStream_t st);
 tc_status launch_proposal(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
                           float scale, uint16_t* h, uint64_t* q, cudaStream_t st);
 int guide_bits(uint64_t m);

@@ -622,12 +622,21 @@ __global__ void k_mlp_init(float* __restrict__ p, uint64_t seed) {
 
 // Training rows from a trace of the plain sampler: row = middle edge,
 // label = the closure count X.
+// Training rows and labels from a trace: the middle edge and its closure
+// count X, or the closure outcome 1[X > 0] (clip).
 __global__ void k_trace_to_rows(const uint64_t* __restrict__ trace, uint64_t n, uint32_t* __restrict__ rows,
-                                float* __restrict__ labels) {
+                                float* __restrict__ labels, bool clip) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     rows[i] = (uint32_t)trace[4 * i];
-    labels[i] = (float)trace[4 * i + 3];
+    const uint64_t X = trace[4 * i + 3];
+    labels[i] = clip ? (X ? 1.f : 0.f) : (float)X;
   }
+}
+
+// labels_out[i] = 1[labels[i] > 0] (the closure outcome of a count).
+__global__ void k_clip_labels(const float* __restrict__ labels, uint64_t n, float* __restrict__ out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = labels[i] > 0.f ? 1.f : 0.f;
 }
 
 static unsigned grid_cap(uint64_t items, int per_block) {
@@ -788,9 +797,18 @@ tc_status mlp_adam(tc_mlp* M, float lr, cudaStream_t st) {
 
 float* mlp_grad_buffer(tc_mlp* M) { return M->grad; }
 
-tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st) {
+tc_status launch_clip_labels(const float* labels, uint64_t n, float* out, cudaStream_t st) {
   if (!n) return TC_OK;
-  k_trace_to_rows<<<grid_cap(n, 256), 256, 0, st>>>(trace, n, rows, labels);
+  k_clip_labels<<<grid_cap(n, 256), 256, 0, st>>>(labels, n, out);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st,
+                               bool clip) {
+  if (!n) return TC_OK;
+  k_trace_to_rows<<<grid_cap(n, 256), 256, 0, st>>>(trace, n, rows, labels, clip);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;

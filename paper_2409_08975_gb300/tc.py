@@ -410,7 +410,7 @@ def tc_mlp_forward(mlp, feat, rows=None, n=None, stream=None):
     return out[:n]
 
 
-OBJECTIVES = {"closure": 0, "variance": 1}
+OBJECTIVES = {"closure": 0, "variance": 1, "bce": 2}
 
 
 def tc_mlp_grad(mlp, feat, rows, labels, objective="closure", eps=0.05, stream=None):

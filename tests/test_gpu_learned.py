@@ -114,6 +114,14 @@ def test_forward_and_gradient_match_fp64(tc):
     gg = grad.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(gg - gref_flat) <= 1e-2 * np.linalg.norm(gref_flat)
     assert abs(loss - lref) < 1e-3
+    # the binary cross-entropy on the closure outcome 1[X > 0]: the oracle's
+    # closure loss on labels clipped to 1
+    grad, loss = tc.tc_mlp_grad(mlp, feat, _dev(rows, torch.int32), _dev(y, torch.float32), objective="bce")
+    gref, lref = L.mlp_backward(p32, x, np.minimum(y, 1).astype(np.float64))
+    gref_flat = L.pack(gref)
+    gg = grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - gref_flat) <= 1e-2 * np.linalg.norm(gref_flat)
+    assert abs(loss - lref) < 1e-3
 
 
 def test_variance_objective_gradient_matches_fp64(tc):
@@ -206,7 +214,7 @@ def test_proposal_unbiased_over_1000_seeds(tc):
     assert abs(np.mean(ests) - C) <= 2.576 * math.sqrt(float(var) / k / 1000)
 
 
-@pytest.mark.parametrize("objective", ["closure", "variance"])
+@pytest.mark.parametrize("objective", ["closure", "variance", "bce"])
 def test_trained_network_reduces_variance(tc, objective):
     # exact per-sample variances from all paths: plain W sum C_P^2 - C^2,
     # learned Q sum C_P^2 / h_P - C^2, after training on plain samples
