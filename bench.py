@@ -3,15 +3,21 @@
 A step is one pass of the whole hot path over the resident graph: path
 weights and their exact prefix sum with the sampling index (Claim 1, Alg. 1),
 then k sampled 3-paths with CheckMotif / ListCount and the reduction of the
-estimate (Alg. 2-5).  The workload is the 20M-edge Chung-Lu graph (n = 1M,
-power-law exponent 2.1, maximum degree ~1e5, 30% multi-edges, bursty times
-over 1e8 s) with the path+chord motif a->b, b->c, c->d, a->d (in that time
-order), delta = 3600 s and k = 1e8 samples per step.
+estimate (Alg. 2-5).  The default workload is the large transaction-like
+graph: n = 1e8 vertices, m = 3e8 edges, top in/out degree about 1e6, pair
+multiplicities Zipf(1.8), times over 1e8 s with daily periodicity, the
+directed 4-cycle (M4-0) with delta = 3600 s and k = 1e9 samples per step.
 
-Printed: one JSON line with samples/s (device, graph resident), the same
-metric end to end through tc_estimate_from_host with pinned host buffers, the
-roofline of the dominant kernel (the sampler), the oracle's CPU rate and the
-SM clocks seen during the timed region.
+Printed: one JSON line with samples/s (device, graph resident); the same
+metric end to end through tc_estimate_from_host with pinned host buffers;
+the roofline of the dominant kernel (the sampler) and of the weights and
+prefix (the paper's algorithmic bytes per edge), each from CUDA events the
+library records around its launches; the oracle's rate on all host cores (a
+bounded sample: a 1% time slice of the graph); the exact count of that slice
+by the oracle's enumerator beside the GPU's; the relative error of the
+estimate against the GPU's exact count of the whole graph; the learned
+proposals against the plain one at a fixed GPU-time budget; and the SM
+clocks seen during the timed region.
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 Under torchrun each rank runs the full path on its own GPU over its own
@@ -20,6 +26,7 @@ sample-id range (weak scaling); the integer sums merge exactly afterwards.
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -39,38 +46,45 @@ MOTIFS = {  # name -> edges in time-rank order
     "cyclic_triangle": [(0, 1), (1, 2), (2, 0)],        # 3-vertex: a->b, b->c, c->a
 }
 MOTIF_NAMES = {str(v): k for k, v in MOTIFS.items()}
-# DRAM bytes (read + write) per sample of the sampler kernel, from one ncu
-# capture of the benchmark's own launch (dram__bytes_read.sum +
-# dram__bytes_write.sum over two 1e8-sample launches); valid while the kernel
-# is unchanged, null for workloads that were not captured
-SAMPLER_TRAFFIC_PER_SAMPLE = {("mid", "path_chord"): 79.3}
+# DRAM bytes (read + write) per unit of a kernel, from one ncu capture of the
+# benchmark's own launches (dram__bytes_read.sum + dram__bytes_write.sum);
+# valid while the kernel is unchanged, null for workloads not captured
+SAMPLER_TRAFFIC_PER_SAMPLE = {}
+WEIGHTS_TRAFFIC_PER_EDGE = {}
 UNIT = "samples/s"
 SECTOR = 32
+LEARNED_VARIANTS = ("closure", "variance", "as_written")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--samples", type=int, default=None, help="samples per step (default: the config's k)")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--exact-max-paths", type=float, default=2e11,
+    ap.add_argument("--exact-max-paths", type=float, default=1e12,
                     help="run the exhaustive exact count when W is at most this")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle's timing on the host cores and the slice check that uses it")
+    ap.add_argument("--cpu-samples", type=int, default=2_000_000,
+                    help="samples of the oracle's timed sampler run (all host cores)")
+    ap.add_argument("--learned", default=",".join(LEARNED_VARIANTS),
+                    help="learned proposals to compare with the plain one (comma list of %s; '' for none): "
+                         "closure = 16 inputs (12 edge counts and 4 sample statistics) trained on the closure "
+                         "count; variance = the same inputs trained on the estimator's variance; as_written = "
+                         "the 12 edge counts alone trained by binary cross-entropy on the closure outcome "
+                         "1[X > 0]" % ", ".join(LEARNED_VARIANTS))
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--train-samples", type=int, default=10_000_000)
     ap.add_argument("--stats-samples", type=int, default=None,
                     help="plain samples behind the sample-statistics features (default: --train-samples)")
     ap.add_argument("--eps", type=float, default=0.05, help="the learned proposal's mixture weight: q ~ w (eps + g)")
-    ap.add_argument("--objective", default="both", choices=["closure", "variance", "both"],
-                    help="training objective of the learned proposal (both: one comparison each, "
-                         "the closure loss under 'learned', the variance objective under 'learned_variance')")
     ap.add_argument("--motif", default=None, choices=sorted(MOTIFS),
                     help="another motif on the workload's graph (default: the workload's own)")
-    ap.add_argument("--workload", default="mid", choices=["mid", "learned", "large", "batch", "small", "batch_small"],
-                    help="mid: the 20M-edge graph (default); learned: n=2e7, m=1e8; large: n=1e8, m=3e8")
+    ap.add_argument("--workload", default="large", choices=["large", "mid", "learned", "batch", "small", "batch_small"],
+                    help="large: n=1e8, m=3e8 (default); mid: the 20M-edge graph; learned: n=2e7, m=1e8")
     return ap.parse_args()
 
 
@@ -146,7 +160,7 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def workload(name="mid"):
+def workload(name="large"):
     from paper_2409_08975_gb300 import synth
     return synth.CONFIGS[name]()
 
@@ -166,31 +180,85 @@ WORKLOADS = {
              "plus 64 graphs of 1e4-2e6 edges (log-uniform) with one query each; 1e6-1e8 samples per query "
              "(log-uniform), ~2.5e9 samples per step",
 }
+SLICE_PARTS = 100  # the oracle's bounded sample of a graph above SLICE_MIN_EDGES: one 1% time slice
+SLICE_MIN_EDGES = 50_000_000
 
 
-def cpu_baseline(cfg, k_total, sample_k=300_000):
-    """The oracle as it stands on the host cores: weights and prefix over the
-    whole graph timed in full, the sampler timed on sample_k samples and
-    scaled to k_total samples per step."""
+def host_info():
+    """Host cores and CPU model (lscpu), for the CPU baseline."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cores": os.cpu_count() or 1, "model": model, "arch": platform.machine()}
+
+
+def oracle_sample(cfg):
+    """The graph the oracle runs on: the whole graph, or for graphs above
+    SLICE_MIN_EDGES its first 1% time slice (a contiguous bounded sample of
+    the same workload: same generator, same delta windows)."""
+    from paper_2409_08975_gb300 import synth
+    m = len(cfg["src"])
+    if m <= SLICE_MIN_EDGES:
+        return dict(cfg, t_lo=None, t_hi=None, m_parent=m), 1.0
+    s = synth.time_slice(cfg, 0, SLICE_PARTS)
+    return s, m / len(s["src"])
+
+
+def cpu_baseline(cfg, k_total, sample_k, exact=True):
+    """The oracle as it stands, on all host cores (OpenMP; the sums are
+    integers, so the results equal the serial ones), on a bounded sample of
+    the workload: weights and prefix over the sample graph timed in full and
+    scaled to the whole graph's edge count; the sampler timed on sample_k
+    samples and scaled to k_total samples per step; and, timed apart, the
+    exact count of the sample graph by the oracle's enumerator (chronological
+    backtracking over the motif's edges, Def. 2)."""
     import oracle
-    og = oracle.build_csr(cfg["n"], cfg["src"], cfg["dst"], cfg["t"], sort="lexsort")
-    plan = oracle.compile_motif(cfg["motif"])
-    t0 = time.perf_counter()
-    w = oracle.path_weights(og, plan, cfg["delta"])["w"]
-    pre = oracle.prefix_sum(w)
-    t_prep = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.sample_run(og, plan, cfg["delta"], pre, sample_k, 0, 0)
-    t_samp = time.perf_counter() - t0
+    info = host_info()
+    sg, scale = oracle_sample(cfg)
+    threads = oracle.set_threads(info["cores"])
+    try:
+        og = oracle.build_csr(sg["n"], sg["src"], sg["dst"], sg["t"], sort="lexsort")
+        plan = oracle.compile_motif(cfg["motif"])
+        t0 = time.perf_counter()
+        w = oracle.path_weights(og, plan, cfg["delta"])["w"]
+        pre = oracle.prefix_sum(w)
+        t_prep = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.sample_run(og, plan, cfg["delta"], pre, sample_k, 0, 0)
+        t_samp = time.perf_counter() - t0
+        ex = None
+        if exact:
+            t0 = time.perf_counter()
+            C = oracle.exact_count(og, cfg["motif"], cfg["delta"])
+            ex = {"C": int(C), "W": int(pre[-1]), "edges": int(og.m), "n": int(og.n), "t_lo": sg["t_lo"],
+                  "t_hi": sg["t_hi"], "s": time.perf_counter() - t0, "threads": threads}
+    finally:
+        oracle.set_threads(1)
     per = t_samp / sample_k
-    value = k_total / (t_prep + per * k_total)
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "serial C oracle: weights+prefix over all %d edges timed in full (%.2f s); sampler timed "
-                      "on %d samples (%.2f s) and scaled to k=%d per step" % (og.m, t_prep, sample_k, t_samp,
-                                                                               k_total)}, og, plan, pre
+    step_s = t_prep * scale + per * k_total
+    where = ("the whole graph (%d edges)" % og.m if scale == 1.0 else
+             "its first 1%% time slice (%d of %d edges, t in [%d, %d))" % (og.m, len(cfg["src"]), sg["t_lo"],
+                                                                           sg["t_hi"]))
+    base = {"value": k_total / step_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "host": info,
+            "sample": "C oracle, %d OpenMP threads, on %s: weights+prefix %.3f s, scaled x%.1f to all edges; sampler "
+                      "%d samples in %.3f s, scaled to k=%d per step; extrapolated step %.1f s" % (
+                          threads, where, t_prep, scale, sample_k, t_samp, k_total, step_s),
+            "weights_s_sample": t_prep, "edge_scale": scale, "sampler_s": t_samp, "sampler_samples": sample_k,
+            "step_s_extrapolated": step_s}
+    return base, ex, sg
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle on all host cores (rank 0 only), each
+    step a bounded sample of sampler work on the oracle's sample graph (the
+    whole graph, or its first 1% time slice for the large graph)."""
     if rank != 0:
         return
     cfg = workload(args.workload)
@@ -201,12 +269,15 @@ def run_reference(args, rank, world):
     elif args.motif:
         cfg["motif"], cfg["motif_override"] = MOTIFS[args.motif], args.motif
     import oracle
-    og = oracle.build_csr(cfg["n"], cfg["src"], cfg["dst"], cfg["t"], sort="lexsort")
+    info = host_info()
+    sg, scale = oracle_sample(cfg)
+    threads = oracle.set_threads(info["cores"])
+    og = oracle.build_csr(sg["n"], sg["src"], sg["dst"], sg["t"], sort="lexsort")
     plan = oracle.compile_motif(cfg["motif"])
     t0 = time.perf_counter()
     pre = oracle.prefix_sum(oracle.path_weights(og, plan, cfg["delta"])["w"])
     t_prep = time.perf_counter() - t0
-    step_k = 100_000
+    step_k = 200_000
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -214,17 +285,22 @@ def run_reference(args, rank, world):
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
+    oracle.set_threads(1)
     per = sum(times) / (len(times) * step_k)
-    step_s = t_prep + per * k
+    step_s = t_prep * scale + per * k
     value = k / step_s
-    sample = ("serial C oracle on the host: weights+prefix over all %d edges once (%.2f s), each step %d samples "
-              "(%.3f s mean), scaled to k=%d samples per step" % (og.m, t_prep, step_k, per * step_k, k))
+    where = "the whole graph" if scale == 1.0 else "its first 1%% time slice (%d edges)" % og.m
+    sample = ("C oracle, %d OpenMP threads, on %s: weights+prefix %.3f s scaled x%.1f to all edges; each measured "
+              "step %d samples (%.3f s mean), scaled to k=%d samples per step" % (threads, where, t_prep, scale,
+                                                                                 step_k, per * step_k, k))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "ms_per_step_extrapolated": True,
+        "measured_step_ms": statistics.mean(times) * 1e3, "measured_step_samples": step_k,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": config_dict(cfg, k, world),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "host": info},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -243,14 +319,20 @@ def run_errors(tc, g, mot, delta, wts, C, k, prop=None):
     return errs
 
 
-def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weights_ms, n_train, stream,
-                       objective="closure", exact_C=None, plain_errors=None, n_stats=None, eps=0.05):
-    """Learned proposal q ~ w (eps + g) against the plain q ~ w on the same
-    graph: features, training on n_train plain samples and the proposal are
-    timed once; then k samples with the proposal.  Relative error at a fixed
-    GPU time follows from the per-sample variance (k SE^2) and the GPU time
-    per sample of each sampler; with the exact count C, also as the mean
-    relative error of five seeds' runs at the GPU time of k plain samples."""
+def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n_train, stream, variant="closure",
+                       exact_C=None, plain_errors=None, n_stats=None, eps=0.05):
+    """A learned proposal q ~ w (eps + g) against the plain q ~ w on the same
+    graph.  Setup, once per (graph, motif, delta): the edge features, the
+    sample statistics (not for as_written) and training on n_train plain
+    samples.  Per query: the inference, h, q and q-prefix with its guide
+    (tc_proposal_weights), then the proposal's sampling.  The learned GPU time
+    is inference + q-scan + sampling, the plain one its sampling (key-order
+    sort and sampling launches: plain_ms per k samples).  Relative error at a
+    fixed GPU time follows from the per-sample variance (k SE^2) and the time
+    per sample of each sampler; with the exact count C, it is also measured
+    as the mean relative error of five seeds' runs at the GPU time of k plain
+    samples, the learned sampler taking what the budget leaves after its
+    inference."""
     import torch
 
     def timed(fn):
@@ -261,14 +343,18 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
         torch.cuda.synchronize()
         return out, a.elapsed_time(b)
 
+    objective = {"closure": "closure", "variance": "variance", "as_written": "bce"}[variant]
     feat, feat_ms = timed(lambda: tc.tc_edge_features(g, mot, delta, wts))
-    # sample statistics from n_stats plain samples (default n_train) of another seed than the training paths
-    n_stats = n_stats or n_train
-    _, sfeat_ms = timed(lambda: tc.tc_sample_features(g, mot, delta, wts, feat, n_stats, seed=777))
+    n_stats = 0 if variant == "as_written" else (n_stats or n_train)
+    sfeat_ms = 0.0
+    if n_stats:  # sample statistics from plain samples of another seed than the training paths
+        _, sfeat_ms = timed(lambda: tc.tc_sample_features(g, mot, delta, wts, feat, n_stats, seed=777))
     mlp = tc.MLP(seed=1)
     losses, train_ms = timed(lambda: tc.tc_mlp_train(mlp, g, mot, delta, wts, feat, n_train, seed=12345,
                                                      batch=16384, lr=3e-3, objective=objective, eps=eps))
-    prop, prop_ms = timed(lambda: tc.tc_proposal_weights(mlp, g, mot, delta, wts, feat, eps=eps))
+    props = [timed(lambda: tc.tc_proposal_weights(mlp, g, mot, delta, wts, feat, eps=eps)) for _ in range(3)]
+    prop = props[-1][0]
+    prop_ms = statistics.median(ms for _, ms in props)
     runs = []
     for i in range(4):
         r, ms = timed(lambda: tc.tc_sample_estimate_q(g, mot, delta, wts, prop, k, seed=0, offset=(50 + i) * k))
@@ -278,32 +364,42 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_sampler_ms, weigh
     var_plain = plain["std_err"] ** 2 * k
     var_learned = rq["std_err"] ** 2 * k
     c = rq["estimate"]
-
-    def t_1pct(var, ms_per_sample):  # sampling time for a 1% relative standard error
-        return var / (0.01 * c) ** 2 * ms_per_sample
-
-    tp = t_1pct(var_plain, plain_sampler_ms / k)
-    tl = t_1pct(var_learned, q_ms / k)
+    # GPU time to a 1% relative standard error
+    tp = var_plain / (0.01 * c) ** 2 * plain_ms / k
+    tl_sampling = var_learned / (0.01 * c) ** 2 * q_ms / k
+    setup_ms = feat_ms + sfeat_ms + train_ms
+    # time to the plain sampler's error at k samples: the learned sampler needs
+    # k var_learned / var_plain samples after its inference and q-scan
+    k_equal = k * var_learned / var_plain
+    t_equal = prop_ms + k_equal * q_ms / k
     budget = None
     if exact_C and plain_errors:
-        # the paper's metric: mean relative error over seeds at one GPU-time
-        # budget, that of k plain samples; the learned sampler gets as many
-        # samples as fit in it
-        k_l = max(2, int(k * plain_sampler_ms / q_ms))
-        errs = run_errors(tc, g, mot, delta, wts, exact_C, k_l, prop)
-        budget = {"budget_ms": plain_sampler_ms, "seeds": list(BUDGET_SEEDS), "k_plain": k, "k_learned": k_l,
-                  "rel_error_plain": statistics.mean(plain_errors), "rel_error_learned": statistics.mean(errs),
-                  "rel_error_ratio_learned_over_plain": statistics.mean(errs) / max(statistics.mean(plain_errors),
-                                                                                    1e-300)}
+        k_l = int(k * (plain_ms - prop_ms) / q_ms)
+        if k_l >= 2:
+            errs = run_errors(tc, g, mot, delta, wts, exact_C, k_l, prop)
+            budget = {"budget_ms": plain_ms, "inference_ms": prop_ms, "seeds": list(BUDGET_SEEDS), "k_plain": k,
+                      "k_learned": k_l, "rel_error_plain": statistics.mean(plain_errors),
+                      "rel_error_learned": statistics.mean(errs),
+                      "rel_error_ratio_learned_over_plain": statistics.mean(errs) / max(statistics.mean(plain_errors),
+                                                                                        1e-300)}
+        else:
+            budget = {"budget_ms": plain_ms, "inference_ms": prop_ms, "k_learned": 0,
+                      "note": "the inference and q-scan alone exceed the budget"}
     mlp.destroy()
-    return {"objective": objective, "eps": eps, "train_samples": n_train, "stats_samples": n_stats,
-            "train_ms": train_ms, "features_ms": feat_ms, "sample_features_ms": sfeat_ms, "proposal_ms": prop_ms,
+    del feat
+    return {"variant": variant, "objective": objective, "inputs": 12 if variant == "as_written" else 16, "eps": eps,
+            "train_samples": n_train, "stats_samples": n_stats,
+            "setup_ms": {"features": feat_ms, "sample_statistics": sfeat_ms, "training": train_ms},
+            "inference_ms": prop_ms, "sampler_ms": q_ms, "samples_per_s": k / (q_ms / 1e3),
             "loss_first_batch": losses[0], "loss_last_batch": losses[1],
-            "sampler_ms": q_ms, "samples_per_s": k / (q_ms / 1e3), "estimate": c, "std_err": rq["std_err"],
-            "plain_estimate": plain["estimate"], "plain_std_err": plain["std_err"],
+            "estimate": c, "std_err": rq["std_err"], "plain_estimate": plain["estimate"],
+            "plain_std_err": plain["std_err"],
             "variance_ratio_learned_over_plain": var_learned / var_plain,
-            "time_to_1pct_ms_plain": tp, "time_to_1pct_ms_learned": tl, "time_ratio_learned_over_plain": tl / tp,
-            "time_ratio_with_setup": (tl + feat_ms + sfeat_ms + train_ms + prop_ms) / (tp + weights_ms),
+            "sampling_time_ratio": tl_sampling / tp,
+            "time_to_plain_error_ms": {"plain": plain_ms, "learned": t_equal,
+                                       "ratio": t_equal / plain_ms,
+                                       "ratio_with_setup": (t_equal + setup_ms) / plain_ms,
+                                       "ratio_with_weights_both": (t_equal + weights_ms) / (plain_ms + weights_ms)},
             "fixed_budget": budget}
 
 
@@ -312,15 +408,17 @@ def config_dict(cfg, k, world):
         return {"workload": WORKLOADS[cfg["name"]], "k": int(k), "seed": 0,
                 "parallelism": "dp%d (sample-id ranges)" % world,
                 "reference_sample": "oracle on the 50M-edge graph, first query (4-cycle, delta=600)"}
-    wl = WORKLOADS[cfg["name"]]
+    wl = WORKLOADS.get(cfg["name"], cfg["name"])
     if cfg.get("motif_override"):
         wl += "; motif replaced by %s" % cfg["motif_override"]
+    m = int(len(cfg["src"]))
     return {"workload": wl,
-            "n": int(cfg["n"]), "m": int(len(cfg["src"])),
+            "n": int(cfg["n"]), "m": m,
             "motif": MOTIF_NAMES.get(str([tuple(e) for e in cfg["motif"]]), str(cfg["motif"])),
             "delta": int(cfg["delta"]),
             "k": int(k), "seed": 0, "parallelism": "dp%d (sample-id ranges)" % world,
-            "l2": "inputs larger than L2 (graph + index ~2.4 GB resident)"}
+            "l2": "inputs larger than L2: resident graph lists ~%.1f GB, sampling index %.1f GB, prefix %.1f GB "
+                  "(L2 129 MB); no flush between steps" % (60e-9 * m, 32e-9 * m, 8e-9 * m)}
 
 
 def run_batch(args, rank, world, local):
@@ -469,6 +567,7 @@ def main():
     n, m, delta = cfg["n"], len(cfg["src"]), cfg["delta"]
     stream = torch.cuda.current_stream()
     mot = tc.make_motif(cfg["motif"])
+    (alpha1, alpha3, _, _) = tc.tc_motif_plan(mot)[1]
 
     src_d = torch.from_numpy(cfg["src"]).cuda()
     dst_d = torch.from_numpy(cfg["dst"]).cuda()
@@ -481,20 +580,21 @@ def main():
     torch.cuda.synchronize()
     csr_ms = ev0.elapsed_time(ev1)
     del src_d, dst_d, t_d
+    compact_times = (g.t_max - g.t_min) < (1 << 32)
 
     wts = tc.alloc_weights(g)
+    phases = {"weights": [], "index": [], "order": [], "sample": []}
 
-    kernel_ms = []
-
-    def step(i, sample_events=None):
+    def step(i, record=False):
         # step i of rank r draws sample ids [(i * world + r) * k, + k)
         tc.tc_path_weights(g, mot, delta, out=wts, want_W=False)
-        if sample_events is not None:
-            sample_events[0].record(stream)
+        if record:
+            phases["weights"].append(tc.tc_last_phase_ms("weights"))
+            phases["index"].append(tc.tc_last_phase_ms("index"))
         r = tc.tc_sample_estimate(g, mot, delta, wts, k, seed=0, offset=(i * world + rank) * k)
-        if sample_events is not None:
-            sample_events[1].record(stream)
-            kernel_ms.append(tc.tc_last_sampler_ms())
+        if record:
+            phases["order"].append(tc.tc_last_phase_ms("order"))
+            phases["sample"].append(tc.tc_last_phase_ms("sample"))
         return r
 
     for i in range(args.warmup):
@@ -506,15 +606,14 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = tc.tc_kernel_launches()
-    tc.tc_set_timing(True)  # events around the sampling launch inside each call
+    tc.tc_set_timing(True)  # events around each phase's launches inside each call
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     start.record(stream)
     results = []
     for i in range(args.steps):
-        results.append(step(args.warmup + i, pairs[i]))
+        results.append(step(args.warmup + i, record=True))
     end.record(stream)
     torch.cuda.synchronize()
     tc.tc_set_timing(False)
@@ -527,16 +626,8 @@ def main():
         total_ms = float(tt.item())
     ms_per_step = total_ms / args.steps
     value = world * k / (ms_per_step / 1e3)
-    sampler_ms = statistics.mean(a.elapsed_time(b) for a, b in pairs)
-
-    # weights-only timing (the HBM-bound kernels), after the timed region
-    wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
-    for a, b in wev:
-        a.record(stream)
-        tc.tc_path_weights(g, mot, delta, out=wts, want_W=False)
-        b.record(stream)
-    torch.cuda.synchronize()
-    weights_ms = statistics.median(a.elapsed_time(b) for a, b in wev)
+    ph = {p: statistics.mean(v) for p, v in phases.items()}
+    sampler_call_ms = ph["order"] + ph["sample"]  # the plain sampler's GPU time per k samples
 
     r0 = results[-1]
     # exact count by the exhaustive path sum (all W paths), for the relative error
@@ -550,35 +641,44 @@ def main():
         ex_ms = ev[0].elapsed_time(ev[1])
         exact = {"C": ex["sum_x"], "paths": ex["k"], "ms": ex_ms,
                  "paths_per_s": ex["k"] / (ex_ms / 1e3) if ex_ms > 0 else None,
-                 "rel_error_plain": abs(r0["estimate"] - ex["sum_x"]) / max(ex["sum_x"], 1)}
+                 "rel_error_plain": abs(r0["estimate"] - ex["sum_x"]) / max(ex["sum_x"], 1),
+                 "method": "tc_exact_count: CheckMotif summed over all W paths (Claim 2's proof); pinned against "
+                           "the oracle's backtracking count on 1% time slices (slice_check, tests)"}
     merged = None
     if world > 1:  # the one exchange: exact integer sums of the last step over ranks
         from paper_2409_08975_gb300 import dist as tcdist
         merged = tcdist.merge_runs(r0, r0["W"], device="cuda")
-    checked_frac = r0["checked"] / max(r0["k"], 1)
-    # sampler bytes per sample: guide entry, prefix entry, edge record and the
-    # end-edge entries (two for a 3-path anchor, one for a wedge): 5 or 4
-    # sectors; a checked path adds the pair list lookup (4 sectors)
-    ends = sum(1 for a in tc.tc_motif_plan(mot)[1][:2] if a != 0)
-    bytes_per_sample = SECTOR * (3 + ends + 4 * checked_frac)
+
     peak, peak_kind = load_peaks()
-    k_sample_ms = statistics.mean(kernel_ms)  # the sampling launch alone, key-order sort excluded
-    achieved = bytes_per_sample * k / (k_sample_ms / 1e3) / 1e9
-    tps = SAMPLER_TRAFFIC_PER_SAMPLE.get((cfg["name"], MOTIF_NAMES.get(str([tuple(e) for e in cfg["motif"]]))))
-    roofline = {"bound": "hbm", "kernel": "k_sample (sampler, Alg. 2-4)", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": tps * k if tps else None, "peak_kind": peak_kind,
-                "bytes_per_sample": bytes_per_sample, "kernel_ms": k_sample_ms, "sampler_call_ms": sampler_ms}
-    # algorithmic bytes of the weights step, per the kernels: the v-window pass
-    # 44 B/edge (absent for a wedge whose window is at u); the u-window pass
-    # 16 B edge + 8 B parked v window + 16 B of the searched list (absent for
-    # a wedge at v) + 32 B record + 8 B w; the exact scan 24 B/edge; the
-    # guide 8 B/edge plus 4 B per bucket
-    alpha1, alpha3 = tc.tc_motif_plan(mot)[1][:2]
-    per_edge = (44 if alpha3 else 0) + 16 + (8 if alpha3 else 0) + (16 if alpha1 else 0) + 40 + 24 + 8
-    weights_bytes = per_edge * m + 4 * (2 ** max(1, (m - 1).bit_length()))
-    weights = {"ms": weights_ms, "bytes": weights_bytes, "bytes_per_edge": per_edge,
-               "achieved_gbs": weights_bytes / (weights_ms / 1e3) / 1e9,
-               "frac": weights_bytes / (weights_ms / 1e3) / 1e9 / peak}
+    checked_frac = r0["checked"] / max(r0["k"], 1)
+    # sampler algorithmic bytes per sample (sector model): guide entry, prefix
+    # entry, edge record and the end-edge entries (two for a 3-path anchor,
+    # one for a wedge): 5 or 4 sectors; a checked path adds the pair-list
+    # lookup (hash slot and pair-list times: 4 sectors)
+    ends = sum(1 for a in (alpha1, alpha3) if a != 0)
+    bytes_per_sample = SECTOR * (3 + ends + 4 * checked_frac)
+    achieved = bytes_per_sample * k / (ph["sample"] / 1e3) / 1e9
+    key = (cfg["name"], MOTIF_NAMES.get(str([tuple(e) for e in cfg["motif"]])))
+    tps = SAMPLER_TRAFFIC_PER_SAMPLE.get(key)
+    roofline = {"bound": "hbm", "kernel": "k_sample (sampler with CheckMotif / ListCount, Alg. 2-4)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": tps * k if tps else None, "peak_kind": peak_kind,
+                "limiter": "latency of dependent random loads (long-scoreboard stalls in ncu)",
+                "bytes_per_sample": bytes_per_sample, "kernel_ms": ph["sample"],
+                "dram_bytes_per_sample": tps,
+                "dram_frac": (tps * k / (ph["sample"] / 1e3) / 1e9 / peak) if tps else None}
+    # the paper's algorithmic bytes of a1 (Claim 1, Alg. 1): the edge's time,
+    # the searched list's times, its dst / in->out entry and the w write --
+    # 20 B per edge with 32-bit time offsets (28 with int64 times); a2: 16 B
+    # per edge (read w, write prefix); the implementation's DRAM bytes beside
+    a1 = 20 if compact_times else 28
+    a12 = (a1 + 16) * m
+    wtr = WEIGHTS_TRAFFIC_PER_EDGE.get(key)
+    weights = {"ms": ph["weights"], "alg_bytes_per_edge": {"a1": a1, "a2": 16}, "alg_bytes": a12,
+               "achieved_gbs": a12 / (ph["weights"] / 1e3) / 1e9,
+               "frac": a12 / (ph["weights"] / 1e3) / 1e9 / peak, "peak": peak, "peak_kind": peak_kind,
+               "dram_bytes_per_edge": wtr,
+               "index_ms": ph["index"], "order_ms": ph["order"], "sample_ms": ph["sample"]}
 
     # end to end through the host entry point, pinned host buffers
     src_h = torch.from_numpy(cfg["src"]).pin_memory()
@@ -592,6 +692,7 @@ def main():
         dt = time.perf_counter() - t0
         if i > 0:
             e2e_times.append(dt)
+    del src_h, dst_h, t_h
     e2e = None
     if e2e_times:
         e2e_s = statistics.mean(e2e_times)
@@ -602,23 +703,36 @@ def main():
 
     comparisons = {}
     plain_errors = None
-    if exact and exact["C"] and not args.no_learned and rank == 0:
+    variants = [] if args.no_learned else [v for v in args.learned.split(",") if v]
+    if exact and exact["C"] and variants and rank == 0:
         plain_errors = run_errors(tc, g, mot, delta, wts, exact["C"], k)
-    if not args.no_learned and rank == 0:
-        objectives = ["closure", "variance"] if args.objective == "both" else [args.objective]
-        for obj in objectives:
-            comparisons[obj] = learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_ms, weights_ms,
-                                                  args.train_samples, stream, obj,
+    if rank == 0:
+        for var in variants:
+            comparisons[var] = learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_call_ms, ph["weights"],
+                                                  args.train_samples, stream, var,
                                                   exact["C"] if exact else None, plain_errors, args.stats_samples,
                                                   args.eps)
             if exact:
-                comparisons[obj]["rel_error"] = abs(comparisons[obj]["estimate"] - exact["C"]) / max(exact["C"], 1)
-    learned = comparisons.get("closure", comparisons.get("variance"))
-    learned_variance = comparisons.get("variance") if len(comparisons) == 2 else None
+                comparisons[var]["rel_error"] = abs(comparisons[var]["estimate"] - exact["C"]) / max(exact["C"], 1)
 
-    base = None
-    if rank == 0 and not args.no_cpu_baseline and args.workload == "mid":
-        base = cpu_baseline(cfg, k)[0]
+    base, slice_check = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        base, ex_or, sg = cpu_baseline(cfg, k, args.cpu_samples)
+        # the GPU's exact count of the oracle's sample graph, against the oracle's
+        dev = lambda a, dt: torch.from_numpy(a).to(device="cuda", dtype=dt)
+        gs = tc.tc_build_temporal_csr(sg["n"], dev(sg["src"], torch.int32), dev(sg["dst"], torch.int32),
+                                      dev(sg["t"], torch.int64))
+        ws = tc.tc_path_weights(gs, mot, delta)
+        ev[0].record(stream)
+        exs = tc.tc_exact_count(gs, mot, delta, ws)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        slice_check = dict(ex_or, C_gpu=exs["sum_x"], W_gpu=ws.W, gpu_ms=ev[0].elapsed_time(ev[1]),
+                           equal=(exs["sum_x"] == ex_or["C"] and ws.W == ex_or["W"]),
+                           what="exact count of the oracle's sample graph (1% time slice of a graph above %d edges, "
+                                "else the whole graph): oracle backtracking (Def. 2, all host cores) vs "
+                                "tc_exact_count" % SLICE_MIN_EDGES)
+        gs.destroy()
 
     if world > 1:
         torch.distributed.barrier()
@@ -628,11 +742,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_dict(cfg, k, world),
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-            "cpu_baseline": base, "csr_build_ms": csr_ms, "weights": weights, "learned": learned,
-            "learned_variance": learned_variance,
+            "cpu_baseline": base, "csr_build_ms": csr_ms, "weights": weights,
+            "learned": comparisons.get("closure"), "learned_variance": comparisons.get("variance"),
+            "learned_as_written": comparisons.get("as_written"),
             "estimate": {"W": r0["W"], "estimate": r0["estimate"], "std_err": r0["std_err"], "hits": r0["hits"],
                          "checked": r0["checked"]},
-            "merged_over_ranks": merged, "exact": exact,
+            "merged_over_ranks": merged, "exact": exact, "slice_check": slice_check,
         }))
     g.destroy()
     if world > 1:

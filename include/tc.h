@@ -511,6 +511,20 @@ uint64_t tc_kernel_launches(void);
 tc_status tc_set_timing(int32_t enabled);
 float tc_last_sampler_ms(void);
 
+/* Device time, in milliseconds, of one phase of the last call on this
+ * thread that ran it while timing was enabled (tc_set_timing): the sum over
+ * CUDA events recorded around the phase's launches on the call's stream (0
+ * when timing was off or the phase did not run).  Phases: the path weights
+ * and their exact prefix sum (Claim 1, Alg. 1) of tc_path_weights; its
+ * sampling index (records' guide table); the key-order sort of the sample
+ * ids of a sampling call; its sampling launches (Alg. 2-4, the same as
+ * tc_last_sampler_ms). */
+#define TC_PHASE_WEIGHTS 0
+#define TC_PHASE_INDEX 1
+#define TC_PHASE_ORDER 2
+#define TC_PHASE_SAMPLE 3
+float tc_last_phase_ms(int32_t phase);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* tc_last_error(void);
 

@@ -295,6 +295,8 @@ tc_status tc_set_timing(int32_t enabled) {
 
 float tc_last_sampler_ms(void) { return last_sampler_ms(); }
 
+float tc_last_phase_ms(int32_t phase) { return last_phase_ms(phase); }
+
 tc_status tc_motif_plan(const tc_motif* motif, int32_t* h_anchor, int32_t* h_class) {
   Plan p;
   TC_TRY(plan_of(motif, &p));
@@ -428,9 +430,14 @@ tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delt
   }
   char* idx = (char*)d_index;
   EdgeRec* rec = (EdgeRec*)(idx + kIndexHeaderBytes);
+  PhaseTimer wt(TC_PHASE_WEIGHTS, st), it(TC_PHASE_INDEX, st);
+  wt.start();
   if (s == TC_OK) s = launch_weights(g, plan, delta, rec, w, st);
   if (s == TC_OK) s = scan_u64(w, d_prefix, m, err, st);
+  wt.stop();
+  it.start();
   if (s == TC_OK) s = launch_guide(g, plan, delta, d_prefix, d_index, err, st);
+  it.stop();
   uint32_t h_err = 0;
   if (s == TC_OK && h_W) {
     e = cudaMemcpyAsync(h_W, d_prefix + m, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);

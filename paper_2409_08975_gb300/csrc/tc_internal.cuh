@@ -378,8 +378,19 @@ tc_status launch_sample_batch(int block_size, uint32_t tile, unsigned blocks, co
                               const uint64_t* d_tile_begin, uint32_t nq, unsigned long long* d_next_item,
                               SampleSums* d_sums, cudaStream_t st);
 
-// Diagnostic timing of the sampling launches (tc_set_timing, tc_last_sampler_ms).
+// Diagnostic timing by phase (tc_set_timing, tc_last_phase_ms): a
+// PhaseTimer records an event pair around each start()/stop() on its stream
+// while timing is on; constructing one drops the phase's earlier events.
+constexpr int kNumPhases = 4;
+struct PhaseTimer {
+  int ph;
+  cudaStream_t st;
+  PhaseTimer(int phase, cudaStream_t s);
+  void start();
+  void stop();
+};
 void set_timing(bool on);
+float last_phase_ms(int phase);
 float last_sampler_ms();
 
 // Host form of the estimate from the sums (tc_api.cu).

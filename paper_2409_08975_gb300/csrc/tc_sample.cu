@@ -968,48 +968,52 @@ tc_status sort_sample_ids(const IndexHeader* hdr, uint64_t seed, uint64_t first,
   return s;
 }
 
-// Diagnostic timing of the sampling launches alone (tc_set_timing): event
-// pairs around each launch, summed when the caller asks.
+// Diagnostic timing by phase (tc_set_timing): event pairs around the
+// launches of a phase, recorded on the launching stream and summed when the
+// caller asks.  A call that runs a phase first drops that phase's events of
+// the previous call.
 static thread_local bool t_timing = false;
-static thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events;
+static thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events[kNumPhases];
 
-struct SamplerTimer {
-  cudaStream_t st;
-  explicit SamplerTimer(cudaStream_t s) : st(s) {
-    if (!t_timing) return;
-    for (auto& e : t_events) {
-      cudaEventDestroy(e.first);
-      cudaEventDestroy(e.second);
-    }
-    t_events.clear();
+PhaseTimer::PhaseTimer(int phase, cudaStream_t s) : ph(phase), st(s) {
+  if (!t_timing) return;
+  for (auto& e : t_events[ph]) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
   }
-  void start() {
-    if (!t_timing) return;
-    std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
-    if (cudaEventCreate(&e.first) != cudaSuccess) return;
-    if (cudaEventCreate(&e.second) != cudaSuccess) {
-      cudaEventDestroy(e.first);
-      return;
-    }
-    cudaEventRecord(e.first, st);
-    t_events.push_back(e);
+  t_events[ph].clear();
+}
+
+void PhaseTimer::start() {
+  if (!t_timing) return;
+  std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+  if (cudaEventCreate(&e.first) != cudaSuccess) return;
+  if (cudaEventCreate(&e.second) != cudaSuccess) {
+    cudaEventDestroy(e.first);
+    return;
   }
-  void stop() {
-    if (t_timing && !t_events.empty()) cudaEventRecord(t_events.back().second, st);
-  }
-};
+  cudaEventRecord(e.first, st);
+  t_events[ph].push_back(e);
+}
+
+void PhaseTimer::stop() {
+  if (t_timing && !t_events[ph].empty()) cudaEventRecord(t_events[ph].back().second, st);
+}
 
 void set_timing(bool on) { t_timing = on; }
 
-float last_sampler_ms() {
+float last_phase_ms(int phase) {
+  if (phase < 0 || phase >= kNumPhases) return 0.f;
   float total = 0.f;
-  for (auto& e : t_events) {
+  for (auto& e : t_events[phase]) {
     float ms = 0.f;
     if (cudaEventSynchronize(e.second) == cudaSuccess && cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess)
       total += ms;
   }
   return total;
 }
+
+float last_sampler_ms() { return last_phase_ms(TC_PHASE_SAMPLE); }
 
 tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
                          const void* index, uint64_t k, uint64_t seed, uint64_t offset, uint64_t* trace,
@@ -1075,7 +1079,7 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
     TC_CUDA(cudaGetLastError());
     return TC_OK;
   };
-  SamplerTimer timer(st);
+  PhaseTimer timer(TC_PHASE_SAMPLE, st), sort_timer(TC_PHASE_ORDER, st);
   if (k < kSortedMinSamples) {
     timer.start();
     tc_status s = run(nullptr, 0, k);
@@ -1091,7 +1095,9 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   tc_status s = TC_OK;
   for (uint64_t base = 0; base < k && s == TC_OK; base += chunk) {
     const uint64_t count = (k - base) < chunk ? (k - base) : chunk;
+    sort_timer.start();
     s = sort_sample_ids(v.hdr, seed, offset + base, count, buf, order, st);
+    sort_timer.stop();
     timer.start();
     if (s == TC_OK) s = run(order, base, count);
     timer.stop();

@@ -121,6 +121,8 @@ def lib():
         L.tc_set_timing.restype = st
         L.tc_last_sampler_ms.argtypes = []
         L.tc_last_sampler_ms.restype = ctypes.c_float
+        L.tc_last_phase_ms.argtypes = [ctypes.c_int32]
+        L.tc_last_phase_ms.restype = ctypes.c_float
         L.tc_last_error.argtypes = []
         L.tc_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -154,6 +156,15 @@ def tc_set_timing(enabled):
 
 def tc_last_sampler_ms():
     return float(lib().tc_last_sampler_ms())
+
+
+PHASES = {"weights": 0, "index": 1, "order": 2, "sample": 3}
+
+
+def tc_last_phase_ms(phase):
+    """Device ms of a phase ("weights": a1 + a2, "index", "order", "sample")
+    in the last call on this thread that ran it with timing enabled."""
+    return float(lib().tc_last_phase_ms(PHASES[phase]))
 
 
 def make_motif(edges, anchor=None, window=WINDOW_STRICT):
