@@ -708,31 +708,23 @@ def main():
         plain_errors = run_errors(tc, g, mot, delta, wts, exact["C"], k)
     if rank == 0:
         for var in variants:
-            comparisons[var] = learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_call_ms, ph["weights"],
-                                                  args.train_samples, stream, var,
-                                                  exact["C"] if exact else None, plain_errors, args.stats_samples,
-                                                  args.eps)
-            if exact:
-                comparisons[var]["rel_error"] = abs(comparisons[var]["estimate"] - exact["C"]) / max(exact["C"], 1)
+            try:
+                comparisons[var] = learned_comparison(tc, g, mot, delta, wts, k, r0, sampler_call_ms, ph["weights"],
+                                                      args.train_samples, stream, var,
+                                                      exact["C"] if exact else None, plain_errors,
+                                                      args.stats_samples, args.eps)
+                if exact:
+                    comparisons[var]["rel_error"] = abs(comparisons[var]["estimate"] - exact["C"]) / max(exact["C"],
+                                                                                                         1)
+            except Exception as exc:  # keep the line: report the failure instead
+                comparisons[var] = {"variant": var, "error": "%s: %s" % (type(exc).__name__, exc)}
 
     base, slice_check = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        base, ex_or, sg = cpu_baseline(cfg, k, args.cpu_samples)
-        # the GPU's exact count of the oracle's sample graph, against the oracle's
-        dev = lambda a, dt: torch.from_numpy(a).to(device="cuda", dtype=dt)
-        gs = tc.tc_build_temporal_csr(sg["n"], dev(sg["src"], torch.int32), dev(sg["dst"], torch.int32),
-                                      dev(sg["t"], torch.int64))
-        ws = tc.tc_path_weights(gs, mot, delta)
-        ev[0].record(stream)
-        exs = tc.tc_exact_count(gs, mot, delta, ws)
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        slice_check = dict(ex_or, C_gpu=exs["sum_x"], W_gpu=ws.W, gpu_ms=ev[0].elapsed_time(ev[1]),
-                           equal=(exs["sum_x"] == ex_or["C"] and ws.W == ex_or["W"]),
-                           what="exact count of the oracle's sample graph (1% time slice of a graph above %d edges, "
-                                "else the whole graph): oracle backtracking (Def. 2, all host cores) vs "
-                                "tc_exact_count" % SLICE_MIN_EDGES)
-        gs.destroy()
+        try:
+            base, slice_check = cpu_leg(args, cfg, k, tc, mot, delta, stream, ev)
+        except Exception as exc:  # keep the line: report the failure instead
+            slice_check = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     if world > 1:
         torch.distributed.barrier()
@@ -752,6 +744,29 @@ def main():
     g.destroy()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def cpu_leg(args, cfg, k, tc, mot, delta, stream, ev):
+    """The oracle's CPU baseline, and the GPU's exact count of the oracle's
+    sample graph beside the oracle's."""
+    import torch
+    base, ex_or, sg = cpu_baseline(cfg, k, args.cpu_samples)
+    # the GPU's exact count of the oracle's sample graph, against the oracle's
+    dev = lambda a, dt: torch.from_numpy(a).to(device="cuda", dtype=dt)
+    gs = tc.tc_build_temporal_csr(sg["n"], dev(sg["src"], torch.int32), dev(sg["dst"], torch.int32),
+                                  dev(sg["t"], torch.int64))
+    ws = tc.tc_path_weights(gs, mot, delta)
+    ev[0].record(stream)
+    exs = tc.tc_exact_count(gs, mot, delta, ws)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    slice_check = dict(ex_or, C_gpu=exs["sum_x"], W_gpu=ws.W, gpu_ms=ev[0].elapsed_time(ev[1]),
+                       equal=(exs["sum_x"] == ex_or["C"] and ws.W == ex_or["W"]),
+                       what="exact count of the oracle's sample graph (1%% time slice of a graph above %d edges, "
+                            "else the whole graph): oracle backtracking (Def. 2, all host cores) vs "
+                            "tc_exact_count" % SLICE_MIN_EDGES)
+    gs.destroy()
+    return base, slice_check
 
 
 if __name__ == "__main__":
