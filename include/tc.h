@@ -164,12 +164,12 @@ tc_status tc_graph_copy(const tc_graph* g, int32_t which, void* d_dst, void* str
 tc_status tc_graph_edge_order(const tc_graph* g, int64_t* d_perm, void* stream);
 
 /*
- * Bytes of device memory a sampling index needs for graph g: per canonical
- * edge a 32-byte record {int32 u, int32 v, int64 t, uint32 lo1, uint32 d1,
- * uint32 lo3, uint32 d3} (the edge and both window ranges of Alg. 2), a
- * 256-byte header, and a guide table of uint32 that maps equal slices of
- * [0, W) to the first candidate edge of the CDF search.  Independent of the
- * motif and delta.
+ * Bytes of device memory a sampling index needs for graph g: a 256-byte
+ * header, per canonical edge a 16-byte entry {uint32 lo1, uint32 d1,
+ * uint32 lo3, uint32 d3} (both window ranges of Alg. 2: e1 lies at list
+ * positions [lo1, lo1 + d1), e3 at [lo3, lo3 + d3)), and a guide table of
+ * uint32 that maps equal slices of [0, W) to the first candidate edge of
+ * the CDF search.  Independent of the motif and delta.
  */
 tc_status tc_sample_index_bytes(const tc_graph* g, size_t* h_bytes);
 
@@ -185,8 +185,12 @@ tc_status tc_sample_index_bytes(const tc_graph* g, size_t* h_bytes);
  *   d_index   tc_sample_index_bytes(g) bytes, 256-byte aligned; receives the
  *             sampling index consumed by tc_sample_estimate
  *   h_W       optional; receives W = prefix[m] (synchronises the stream)
+ * The weights, the windows and the prefix are formed in one pass over the
+ * edges (a single-pass scan whose blocks wait, for a bounded time, on the
+ * sums of the blocks before them).
  * Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED_MOTIF, TC_ERR_OVERFLOW (W
- * does not fit 64 bits; reported when h_W is requested), TC_ERR_CUDA.
+ * does not fit 64 bits; reported when h_W is requested), TC_ERR_TIMEOUT (a
+ * wait gave up; reported when h_W is requested), TC_ERR_CUDA.
  */
 tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delta, uint64_t* d_w,
                           uint64_t* d_prefix, void* d_index, uint64_t* h_W, void* stream);

@@ -69,6 +69,7 @@ tc_status device_status(uint32_t bits, const char* what) {
   if (bits & kErrOverflow) return set_error(TC_ERR_OVERFLOW, w + ": a 64-bit count overflowed");
   if (bits & kErrRng) return set_error(TC_ERR_RNG_EXHAUSTED, w + ": 64 rejected draws in a row");
   if (bits & kErrBounds) return set_error(TC_ERR_BOUNDS, w + ": device index check failed");
+  if (bits & kErrTimeout) return set_error(TC_ERR_TIMEOUT, w + ": a bounded device wait gave up");
   return TC_OK;
 }
 
@@ -252,8 +253,9 @@ static tc_status plan_of(const tc_motif* motif, Plan* p) {
 tc_status compile_plan_checked(const tc_motif* motif, Plan* p) { return plan_of(motif, p); }
 
 static void free_graph_arrays(tc_graph* g) {
-  void* ps[] = {g->out_off, g->out_e, g->perm, g->in_off, g->in_e, g->in_eid, g->pair_off,
-                g->pair_dst, g->pair_eoff, g->pair_t, g->pair_eid, g->pair_hash, g->out_t32, g->in_t32, g->pair_t32};
+  void* ps[] = {g->out_off, g->out_e,  g->perm,     g->in_off,  g->in_e,    g->in_eid,  g->pair_off, g->pair_dst,
+                g->pair_eoff, g->pair_t, g->pair_eid, g->pair_hash, g->out_t32, g->in_t32, g->pair_t32, g->x_in,
+                g->x_out, g->out2in};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -415,25 +417,18 @@ tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delt
   if (((uintptr_t)d_index & 255) != 0) return set_error(TC_ERR_INVALID_ARG, "index must be 256-byte aligned");
   cudaStream_t st = S(stream);
   const uint64_t m = (uint64_t)g->m;
-  uint64_t* w = d_w;
-  uint32_t* err = nullptr;
+  char* scratch = nullptr;  // error word, then the scan's tile states
   tc_status s = TC_OK;
-  if (!w) {
-    cudaError_t e = pool_malloc(&w, sizeof(uint64_t) * (m ? m : 1), st);
-    if (e != cudaSuccess) return cuda_status(e, "pool_malloc(w)");
-  }
-  cudaError_t e = pool_malloc(&err, sizeof(uint32_t), st);
-  if (e != cudaSuccess) s = cuda_status(e, "pool_malloc(err)");
-  if (s == TC_OK) {
-    e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
-    if (e != cudaSuccess) s = cuda_status(e, "cudaMemsetAsync");
-  }
+  cudaError_t e = pool_malloc(&scratch, 256 + weights_scan_scratch_bytes(m), st);
+  if (e != cudaSuccess) return cuda_status(e, "pool_malloc(weights scratch)");
+  uint32_t* err = (uint32_t*)scratch;
+  e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) s = cuda_status(e, "cudaMemsetAsync");
   char* idx = (char*)d_index;
-  EdgeRec* rec = (EdgeRec*)(idx + kIndexHeaderBytes);
+  EdgeWin* win = (EdgeWin*)(idx + kIndexHeaderBytes);
   PhaseTimer wt(TC_PHASE_WEIGHTS, st), it(TC_PHASE_INDEX, st);
   wt.start();
-  if (s == TC_OK) s = launch_weights(g, plan, delta, rec, w, st);
-  if (s == TC_OK) s = scan_u64(w, d_prefix, m, err, st);
+  if (s == TC_OK) s = launch_weights_scan(g, plan, delta, win, d_prefix, d_w, scratch + 256, err, st);
   wt.stop();
   it.start();
   if (s == TC_OK) s = launch_guide(g, plan, delta, d_prefix, d_index, err, st);
@@ -445,8 +440,7 @@ tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delt
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = cuda_status(e, "tc_path_weights");
   }
-  if (err) cudaFreeAsync(err, st);
-  if (!d_w && w) cudaFreeAsync(w, st);
+  cudaFreeAsync(scratch, st);
   if (s == TC_OK && h_err) s = device_status(h_err, "tc_path_weights");
   return s;
 }
@@ -636,8 +630,8 @@ tc_status tc_edge_features(const tc_graph* g, const tc_motif* motif, int64_t del
   if (!d_index || !d_feat) return set_error(TC_ERR_INVALID_ARG, "index or features is NULL");
   cudaStream_t st = S(stream);
   TC_TRY(check_index_header(g, plan, delta, d_index, st));
-  const EdgeRec* rec = (const EdgeRec*)((const char*)d_index + kIndexHeaderBytes);
-  return launch_features(g, rec, delta, d_feat, st);
+  const EdgeWin* win = (const EdgeWin*)((const char*)d_index + kIndexHeaderBytes);
+  return launch_features(g, win, delta, d_feat, st);
 }
 
 tc_status tc_sample_features(const tc_graph* g, const tc_motif* motif, int64_t delta, const uint64_t* d_prefix,
@@ -819,15 +813,15 @@ tc_status tc_proposal_weights(const tc_mlp* mlp, const tc_graph* g, const tc_mot
     return set_error(TC_ERR_INVALID_ARG, "need scale >= 1, eps >= 0 and scale (1 + eps) + 1 <= 4095");
   cudaStream_t st = S(stream);
   const uint64_t m = (uint64_t)g->m;
-  uint64_t* q = nullptr;
-  uint32_t* err = nullptr;
+  char* scratch = nullptr;  // error word, then the scan's tile states
   tc_status s = TC_OK;
-  cudaError_t e = pool_malloc(&q, 8 * (m ? m : 1), st);
-  if (e == cudaSuccess) e = pool_malloc(&err, sizeof(uint32_t), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+  cudaError_t e = pool_malloc(&scratch, 256 + proposal_scan_scratch_bytes(m), st);
+  if (e != cudaSuccess) return cuda_status(e, "tc_proposal_weights allocation");
+  uint32_t* err = (uint32_t*)scratch;
+  e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) s = cuda_status(e, "tc_proposal_weights allocation");
-  if (s == TC_OK) s = launch_proposal(mlp, d_feat, d_prefix, m, eps, (float)scale, d_h, q, st);
-  if (s == TC_OK) s = scan_u64(q, d_qprefix, m, err, st);
+  if (s == TC_OK)
+    s = launch_proposal_scan(mlp, d_feat, d_prefix, m, eps, (float)scale, d_h, d_qprefix, scratch + 256, err, st);
   if (s == TC_OK)
     s = launch_guide_at(g, plan, delta, d_qprefix, (IndexHeader*)d_qindex,
                         (uint32_t*)((char*)d_qindex + kIndexHeaderBytes), err, st);
@@ -838,8 +832,7 @@ tc_status tc_proposal_weights(const tc_mlp* mlp, const tc_graph* g, const tc_mot
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = cuda_status(e, "tc_proposal_weights");
   }
-  if (q) cudaFreeAsync(q, st);
-  if (err) cudaFreeAsync(err, st);
+  cudaFreeAsync(scratch, st);
   if (s == TC_OK && h_err) s = device_status(h_err, "tc_proposal_weights");
   return s;
 }

@@ -45,9 +45,7 @@ struct tc_batch {
   std::vector<Slot> slots;
   std::vector<void*> allocations;  // every cudaMalloc of the batch
   uint64_t device_bytes = 0;
-  uint64_t* w = nullptr;           // weights scratch, max m
-  uint64_t* scan_scratch = nullptr;
-  uint64_t scan_words = 0;
+  void* scan_scratch = nullptr;    // tile states of the weights scan, for the largest graph
   void* sort_scratch = nullptr;
   uint32_t* err = nullptr;         // one error word per slot
   char* records = nullptr;         // nq * kBatchQueryBytes
@@ -119,9 +117,8 @@ tc_status enqueue_prologue(tc_batch* b, cudaStream_t st) {
   for (size_t s = 0; s < ns; s++) {
     const Slot& S = b->slots[s];
     const uint64_t m = (uint64_t)S.g->m;
-    EdgeRec* rec = (EdgeRec*)(S.index + kIndexHeaderBytes);
-    TC_TRY(launch_weights(S.g, S.plan, S.delta, rec, b->w, st));
-    TC_TRY(scan_u64_in_scratch(b->w, S.prefix, m, true, b->err + s, b->scan_scratch, b->scan_words, st));
+    EdgeWin* win = (EdgeWin*)(S.index + kIndexHeaderBytes);
+    TC_TRY(launch_weights_scan(S.g, S.plan, S.delta, win, S.prefix, nullptr, b->scan_scratch, b->err + s, st));
     TC_TRY(launch_guide(S.g, S.plan, S.delta, S.prefix, S.index, b->err + s, st));
   }
   for (const Query& Q : b->queries) {
@@ -271,9 +268,7 @@ tc_status create(const tc_query* hq, int64_t nq, const tc_batch_options* opts, c
     TC_TRY(batch_alloc(b, (void**)&S.prefix, sizeof(uint64_t) * (m + 1)));
     TC_TRY(batch_alloc(b, (void**)&S.index, index_bytes(m)));
   }
-  b->scan_words = scan_u64_scratch_words(max_m) + 1;
-  TC_TRY(batch_alloc(b, (void**)&b->w, sizeof(uint64_t) * (max_m ? max_m : 1)));
-  TC_TRY(batch_alloc(b, (void**)&b->scan_scratch, sizeof(uint64_t) * b->scan_words));
+  TC_TRY(batch_alloc(b, (void**)&b->scan_scratch, weights_scan_scratch_bytes(max_m)));
   TC_TRY(batch_alloc(b, (void**)&b->err, sizeof(uint32_t) * b->slots.size()));
   if (max_sort) TC_TRY(batch_alloc(b, &b->sort_scratch, sort_scratch_bytes(max_sort)));
   uint32_t* order = nullptr;

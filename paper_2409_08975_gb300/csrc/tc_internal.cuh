@@ -26,12 +26,9 @@ struct __align__(16) InEdge {  // in-lists sorted by (dst, t, input index)
   int64_t t;
 };
 
-// One sampler record per canonical edge: the edge and both window ranges of
-// Alg. 2, so that drawing the middle edge costs one 32-byte sector.
-struct __align__(32) EdgeRec {
-  int32_t u;
-  int32_t v;
-  int64_t t;
+// Both end-edge windows of a canonical middle edge (Alg. 2), one 16-byte
+// entry per edge of the sampling index; the edge itself is out_e.
+struct __align__(16) EdgeWin {
   uint32_t lo1, d1;  // window of e1: positions [lo1, lo1 + d1) of u's alpha1 list
   uint32_t lo3, d3;  // window of e3: positions [lo3, lo3 + d3) of v's alpha3 list
 };
@@ -80,6 +77,7 @@ enum : uint32_t {
   kErrBounds = 1u << 2,
   kErrBadId = 1u << 3,
   kErrIndexMismatch = 1u << 4,
+  kErrTimeout = 1u << 5,
 };
 
 // ---------------------------------------------------------------------------
@@ -136,6 +134,13 @@ struct tc_graph {
   uint32_t* out_t32;
   uint32_t* in_t32;
   uint32_t* pair_t32;  // pair-list times as t - tmin (same condition)
+  // Anchors of the window searches, per canonical edge e = (u, v, t),
+  // independent of delta and of the motif: positions in the concatenated
+  // lists where u's in-list and v's out-list reach time t (the first entry
+  // with time >= t), and e's own position in v's in-list.
+  uint32_t* x_in;    // first position p in u's in-list with in_e[p].t >= t
+  uint32_t* x_out;   // first position p in v's out-list with out_e[p].t >= t
+  uint32_t* out2in;  // canonical position -> in-list position (inverse of in_eid)
 };
 
 namespace tc {
@@ -281,6 +286,117 @@ __device__ __forceinline__ void window_range(const OutEdge* __restrict__ out_e,
 }
 
 // ---------------------------------------------------------------------------
+// Single-pass exclusive scan across the tiles of one launch (decoupled
+// look-back, Merrill & Garland 2016).  Each block takes the next tile from a
+// counter (so every earlier tile belongs to a block that already runs),
+// publishes its tile sum (flag 1), adds the sums of the tiles before it
+// until it meets a published inclusive prefix (flag 2), and publishes its
+// own.  Tile states live in caller scratch: a counter, then flags, tile sums
+// and inclusive prefixes; the counter and the flags are cleared before each
+// launch.  Waits on predecessors are bounded (kLookbackSpins polls).
+
+struct ScanState {
+  uint32_t* counter;
+  uint32_t* flag;  // 0 none, 1 tile sum published, 2 inclusive prefix published
+  unsigned long long* agg;
+  unsigned long long* inc;
+};
+
+inline size_t scan_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+inline size_t scan_state_clear_bytes(uint64_t tiles) { return 256 + scan_align256(4 * (tiles ? tiles : 1)); }
+inline size_t scan_state_bytes(uint64_t tiles) {
+  return scan_state_clear_bytes(tiles) + 2 * scan_align256(8 * (tiles ? tiles : 1));
+}
+inline ScanState scan_state_view(void* scratch, uint64_t tiles) {
+  char* p = (char*)scratch;
+  const size_t c = scan_state_clear_bytes(tiles), a = scan_align256(8 * (tiles ? tiles : 1));
+  ScanState S;
+  S.counter = (uint32_t*)p;
+  S.flag = (uint32_t*)(p + 256);
+  S.agg = (unsigned long long*)(p + c);
+  S.inc = (unsigned long long*)(p + c + a);
+  return S;
+}
+
+constexpr uint32_t kLookbackSpins = 1u << 22;  // x 64 ns: about a quarter of a second
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Called by all 32 lanes of one warp of the block that owns `tile`, with
+// the tile's sum; returns (to every lane) the sum of all earlier tiles and
+// publishes this tile's inclusive prefix.  Overflow beyond 64 bits and a
+// wait that gives up set bits in *err (kErrOverflow, kErrTimeout).
+__device__ __forceinline__ unsigned long long scan_lookback(const ScanState& S, uint32_t tile,
+                                                            unsigned long long tile_sum, uint32_t* err) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long excl = 0;
+  if (tile == 0) {
+    if (lane == 0) {
+      S.inc[0] = tile_sum;
+      st_release_u32(S.flag, 2u);
+    }
+    return 0;
+  }
+  if (lane == 0) {
+    S.agg[tile] = tile_sum;
+    st_release_u32(S.flag + tile, 1u);
+  }
+  int64_t j = (int64_t)tile - 1;
+  uint32_t spins = 0;
+  for (;;) {
+    const int64_t idx = j - lane;
+    uint32_t f = 2u;  // before tile 0: an inclusive prefix of 0
+    unsigned long long v = 0;
+    if (idx >= 0) {
+      f = ld_acquire_u32(S.flag + idx);
+      if (f == 1u) v = ld_relaxed_u64(S.agg + idx);
+      else if (f == 2u) v = ld_relaxed_u64(S.inc + idx);
+    }
+    const unsigned inc_mask = __ballot_sync(0xffffffffu, f == 2u);
+    const unsigned zero_mask = __ballot_sync(0xffffffffu, f == 0u);
+    const int first = inc_mask ? __ffs(inc_mask) - 1 : 32;  // nearest inclusive prefix
+    const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+    if (zero_mask & need) {
+      if (++spins > kLookbackSpins) {
+        *err |= kErrTimeout;
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    unsigned __int128 sum = lane <= first ? v : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)sum, o);
+      const uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(sum >> 64), o);
+      sum += ((unsigned __int128)hi << 64) | lo;
+    }
+    if ((sum >> 64) || excl + (uint64_t)sum < excl) *err |= kErrOverflow;
+    excl += (uint64_t)sum;
+    if (first < 32) break;
+    j -= 32;
+  }
+  if (lane == 0) {
+    if (excl + tile_sum < excl) *err |= kErrOverflow;
+    S.inc[tile] = excl + tile_sum;
+    st_release_u32(S.flag + tile, 2u);
+  }
+  return excl;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files).
 
 // Exclusive scans.  scan_u64 writes out[0..n] (out[n] = total) and sets
@@ -304,8 +420,14 @@ tc_status launch_widen_u32(const uint32_t* in, uint64_t n, int64_t* out, cudaStr
 tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t,
                       cudaStream_t st, tc_graph* g);
 
-tc_status launch_weights(const tc_graph* g, const Plan& plan, int64_t delta, EdgeRec* rec, uint64_t* w,
-                         cudaStream_t st);
+// Path weights, their exact prefix sum and the windows in one pass over the
+// canonical edges (single-pass scan with decoupled look-back): prefix[m + 1],
+// win[m], and w[m] when w is not NULL.  scratch: weights_scan_scratch_bytes(m)
+// bytes (tile states; cleared here on the stream); *d_err collects overflow
+// and wait-timeout bits.
+size_t weights_scan_scratch_bytes(uint64_t m);
+tc_status launch_weights_scan(const tc_graph* g, const Plan& plan, int64_t delta, EdgeWin* win, uint64_t* prefix,
+                              uint64_t* w, void* scratch, uint32_t* d_err, cudaStream_t st);
 tc_status launch_guide(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
                        void* index, uint32_t* d_err, cudaStream_t st);
 tc_status launch_guide_at(const tc_graph* g, const Plan& plan, int64_t delta, const uint64_t* prefix,
@@ -320,7 +442,7 @@ void mlp_destroy(tc_mlp* M);
 int mlp_num_params();
 tc_status mlp_set_params(tc_mlp* M, const float* h);
 tc_status mlp_get_params(const tc_mlp* M, float* h);
-tc_status launch_features(const tc_graph* g, const EdgeRec* rec, int64_t delta, uint16_t* feat, cudaStream_t st);
+tc_status launch_features(const tc_graph* g, const EdgeWin* win, int64_t delta, uint16_t* feat, cudaStream_t st);
 tc_status launch_mlp_forward(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, uint64_t n, float* out,
                              cudaStream_t st);
 tc_status launch_mlp_grad(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, const float* labels,
@@ -338,8 +460,12 @@ tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint6
 tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st,
                                bool clip = false);
 tc_status launch_clip_labels(const float* labels, uint64_t n, float* out, cudaStream_t st);
-tc_status launch_proposal(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
-                          float scale, uint16_t* h, uint64_t* q, cudaStream_t st);
+// Proposal h, q = w h and the exact prefix of q in one pass (scratch:
+// proposal_scan_scratch_bytes(m) bytes, cleared here on the stream).
+size_t proposal_scan_scratch_bytes(uint64_t m);
+tc_status launch_proposal_scan(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
+                               float scale, uint16_t* h, uint64_t* qprefix, void* scratch, uint32_t* d_err,
+                               cudaStream_t st);
 int guide_bits(uint64_t m);
 
 struct SampleSums {  // per-call device accumulator

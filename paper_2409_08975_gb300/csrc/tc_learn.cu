@@ -79,25 +79,26 @@ __global__ void __launch_bounds__(256) k_features(const OutEdge* __restrict__ ou
                                                   const uint32_t* __restrict__ out_off,
                                                   const InEdge* __restrict__ in_e, const uint32_t* __restrict__ in_off,
                                                   const PairSlot* __restrict__ table, uint64_t mask,
-                                                  const int64_t* __restrict__ pair_t, const EdgeRec* __restrict__ rec,
+                                                  const int64_t* __restrict__ pair_t, const EdgeWin* __restrict__ win,
                                                   uint64_t m, int64_t delta, __nv_bfloat16* __restrict__ feat) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-    const EdgeRec r = rec[i];
-    const int64_t lo = sat_sub(r.t, delta), hi = sat_add(r.t, delta);
+    const EdgeWin r = win[i];
+    const OutEdge e = out_e[i];
+    const int64_t lo = sat_sub(e.t, delta), hi = sat_add(e.t, delta);
     float c[kNFeat];
     c[0] = (float)r.d1;
     c[1] = (float)r.d3;
     c[2] = (float)((uint64_t)r.d1 * (uint64_t)r.d3);
-    c[3] = (float)count_window(out_e, out_off, in_e, in_off, true, r.u, lo, hi);
-    c[4] = (float)count_window(out_e, out_off, in_e, in_off, false, r.u, lo, hi);
-    c[5] = (float)count_window(out_e, out_off, in_e, in_off, true, r.v, lo, hi);
-    c[6] = (float)count_window(out_e, out_off, in_e, in_off, false, r.v, lo, hi);
-    c[7] = (float)pair_count(table, mask, pair_t, r.u, r.v, lo, hi);
-    c[8] = (float)pair_count(table, mask, pair_t, r.v, r.u, lo, hi);
-    c[9] = (float)(__ldg(out_off + r.u + 1) - __ldg(out_off + r.u));
-    c[10] = (float)(__ldg(in_off + r.v + 1) - __ldg(in_off + r.v));
-    c[11] = (float)(__ldg(in_off + r.u + 1) - __ldg(in_off + r.u));
+    c[3] = (float)count_window(out_e, out_off, in_e, in_off, true, e.src, lo, hi);
+    c[4] = (float)count_window(out_e, out_off, in_e, in_off, false, e.src, lo, hi);
+    c[5] = (float)count_window(out_e, out_off, in_e, in_off, true, e.dst, lo, hi);
+    c[6] = (float)count_window(out_e, out_off, in_e, in_off, false, e.dst, lo, hi);
+    c[7] = (float)pair_count(table, mask, pair_t, e.src, e.dst, lo, hi);
+    c[8] = (float)pair_count(table, mask, pair_t, e.dst, e.src, lo, hi);
+    c[9] = (float)(__ldg(out_off + e.src + 1) - __ldg(out_off + e.src));
+    c[10] = (float)(__ldg(in_off + e.dst + 1) - __ldg(in_off + e.dst));
+    c[11] = (float)(__ldg(in_off + e.src + 1) - __ldg(in_off + e.src));
     __align__(16) __nv_bfloat16 row[kF];
 #pragma unroll
     for (int j = 0; j < kNFeat; j++) row[j] = __float2bfloat16_rn(log1pf(c[j]));
@@ -224,21 +225,29 @@ __global__ void __launch_bounds__(256) k_te_lookup(const OutEdge* __restrict__ o
 //   B (16x8):             regs (k = 2q..2q+1, n = g), (k = 2q+8..2q+9, n = g)
 //   C (16x8):             (g, 2q), (g, 2q+1), (g+8, 2q), (g+8, 2q+1)
 
+// Row strides of the weights in shared memory, padded so that the lanes of
+// a fragment load (8 rows g x 4 column pairs q) and of the backward's column
+// walk fall in distinct banks: a 48-byte W1 row puts lane (g, q) in bank
+// 12 g + q, a 144-byte W2 row in bank 4 g + q (mod 32), a 132-byte W2^T row
+// lane k in bank k + const.
+constexpr int kW1S = 24, kW2S = 72, kW2TS = 66;
+
 struct MlpShared {
-  __nv_bfloat16 W1[kH * kF];   // [n][k]
-  __nv_bfloat16 W2[kH * kH];   // [n][k]
-  __nv_bfloat16 W2T[kH * kH];  // [k][n]
+  __nv_bfloat16 W1[kH * kW1S];   // [n][k]
+  __nv_bfloat16 W2[kH * kW2S];   // [n][k]
+  __nv_bfloat16 W2T[kH * kW2TS];  // [k][n]
   float W3[kH];                // bf16 values held as FP32
   float b1[kH], b2[kH];
   float b3;
 };
 
 __device__ __forceinline__ void load_mlp_shared(MlpShared& S, const float* __restrict__ p) {
-  for (int i = threadIdx.x; i < kH * kF; i += blockDim.x) S.W1[i] = __float2bfloat16_rn(p[kOffW1 + i]);
+  for (int i = threadIdx.x; i < kH * kF; i += blockDim.x)
+    S.W1[(i / kF) * kW1S + i % kF] = __float2bfloat16_rn(p[kOffW1 + i]);
   for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
     const __nv_bfloat16 v = __float2bfloat16_rn(p[kOffW2 + i]);
-    S.W2[i] = v;
-    S.W2T[(i % kH) * kH + i / kH] = v;
+    S.W2[(i / kH) * kW2S + i % kH] = v;
+    S.W2T[(i % kH) * kW2TS + i / kH] = v;
   }
   for (int i = threadIdx.x; i < kH; i += blockDim.x) {
     S.W3[i] = __bfloat162float(__float2bfloat16_rn(p[kOffW3 + i]));
@@ -292,7 +301,7 @@ __device__ __forceinline__ void tile_forward(const MlpShared& S, const uint32_t 
   for (int j = 0; j < 8; j++) {
     const int n = j * 8 + g;
     float c[4] = {S.b1[j * 8 + 2 * q], S.b1[j * 8 + 2 * q + 1], S.b1[j * 8 + 2 * q], S.b1[j * 8 + 2 * q + 1]};
-    mma_bf16(c, x, ld_pair(&S.W1[n * kF + 2 * q]), ld_pair(&S.W1[n * kF + 2 * q + 8]));
+    mma_bf16(c, x, ld_pair(&S.W1[n * kW1S + 2 * q]), ld_pair(&S.W1[n * kW1S + 2 * q + 8]));
 #pragma unroll
     for (int r = 0; r < 4; r++) T.z1[j][r] = c[r];
   }
@@ -312,7 +321,7 @@ __device__ __forceinline__ void tile_forward(const MlpShared& S, const uint32_t 
     float c[4] = {S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1], S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1]};
 #pragma unroll
     for (int kk = 0; kk < 4; kk++)
-      mma_bf16(c, a1[kk], ld_pair(&S.W2[n * kH + kk * 16 + 2 * q]), ld_pair(&S.W2[n * kH + kk * 16 + 2 * q + 8]));
+      mma_bf16(c, a1[kk], ld_pair(&S.W2[n * kW2S + kk * 16 + 2 * q]), ld_pair(&S.W2[n * kW2S + kk * 16 + 2 * q + 8]));
 #pragma unroll
     for (int r = 0; r < 4; r++) T.z2[j][r] = c[r];
   }
@@ -361,37 +370,194 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ p
   }
 }
 
-// Proposal: h_e = max(1, floor(scale (eps + g_e) + 1/2)) and q_e = w_e h_e for
-// every canonical edge, with w_e = prefix[e + 1] - prefix[e].
-__global__ void __launch_bounds__(128) k_proposal(const float* __restrict__ params,
-                                                  const __nv_bfloat16* __restrict__ feat,
-                                                  const uint64_t* __restrict__ prefix, uint64_t m, float eps,
-                                                  float scale, uint16_t* __restrict__ h, uint64_t* __restrict__ q) {
-  __shared__ MlpShared S;
-  load_mlp_shared(S, params);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2;
-  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < m; tile += warps) {
-    const uint64_t ia = tile * 16 + g, ib = ia + 8;
-    uint32_t x[4];
-    load_rows(feat, ia < m ? (int64_t)ia : -1, ib < m ? (int64_t)ib : -1, x);
-    TileAct T;
-    tile_forward(S, x, T);
-    if ((lane & 3) == 0) {
+// Logits of one 16-row tile for rows g and g + 8 of the fragment layout: the
+// forward of tile_forward without keeping the pre-activations (inference).
+struct MlpFwdShared {
+  __nv_bfloat16 W1[kH * kW1S];  // [n][k], padded rows as in MlpShared
+  __nv_bfloat16 W2[kH * kW2S];  // [n][k]
+  float W3[kH];               // bf16 values held as FP32
+  float b1[kH], b2[kH];
+  float b3;
+};
+
+__device__ __forceinline__ void load_mlp_fwd_shared(MlpFwdShared& S, const float* __restrict__ p) {
+  for (int i = threadIdx.x; i < kH * kF; i += blockDim.x)
+    S.W1[(i / kF) * kW1S + i % kF] = __float2bfloat16_rn(p[kOffW1 + i]);
+  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x)
+    S.W2[(i / kH) * kW2S + i % kH] = __float2bfloat16_rn(p[kOffW2 + i]);
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    S.W3[i] = __bfloat162float(__float2bfloat16_rn(p[kOffW3 + i]));
+    S.b1[i] = p[kOffB1 + i];
+    S.b2[i] = p[kOffB2 + i];
+  }
+  if (threadIdx.x == 0) S.b3 = p[kOffB3];
+}
+
+__device__ __forceinline__ void tile_logits(const MlpFwdShared& S, const uint32_t (&x)[4], float* z3g, float* z3g8) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  uint32_t a1[4][4];  // layer 1, ReLU, bf16: the A fragments of layer 2
 #pragma unroll
-      for (int r = 0; r < 2; r++) {
-        const uint64_t i = r ? ib : ia;
-        if (i < m) {
-          const float z = r ? T.z3g8 : T.z3g;
-          const float v = floorf(scale * (eps + sigmoidf_(z)) + 0.5f);
-          const uint32_t hv = v < 1.f ? 1u : (uint32_t)v;
-          h[i] = (uint16_t)hv;
-          q[i] = (prefix[i + 1] - prefix[i]) * (uint64_t)hv;
+  for (int j = 0; j < 8; j++) {
+    const int n = j * 8 + g;
+    float c[4] = {S.b1[j * 8 + 2 * q], S.b1[j * 8 + 2 * q + 1], S.b1[j * 8 + 2 * q], S.b1[j * 8 + 2 * q + 1]};
+    mma_bf16(c, x, ld_pair(&S.W1[n * kW1S + 2 * q]), ld_pair(&S.W1[n * kW1S + 2 * q + 8]));
+    const int kk = j >> 1;
+    if ((j & 1) == 0) {
+      a1[kk][0] = pack_bf16(fmaxf(c[0], 0.f), fmaxf(c[1], 0.f));
+      a1[kk][1] = pack_bf16(fmaxf(c[2], 0.f), fmaxf(c[3], 0.f));
+    } else {
+      a1[kk][2] = pack_bf16(fmaxf(c[0], 0.f), fmaxf(c[1], 0.f));
+      a1[kk][3] = pack_bf16(fmaxf(c[2], 0.f), fmaxf(c[3], 0.f));
+    }
+  }
+  float sg = 0.f, sg8 = 0.f;  // layer 2, then layer 3 in FP32 on the bf16-rounded activations
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int n = j * 8 + g;
+    float c[4] = {S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1], S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1]};
+#pragma unroll
+    for (int kk = 0; kk < 4; kk++)
+      mma_bf16(c, a1[kk], ld_pair(&S.W2[n * kW2S + kk * 16 + 2 * q]), ld_pair(&S.W2[n * kW2S + kk * 16 + 2 * q + 8]));
+    const int n0 = j * 8 + 2 * q;
+    sg += __bfloat162float(__float2bfloat16_rn(fmaxf(c[0], 0.f))) * S.W3[n0] +
+          __bfloat162float(__float2bfloat16_rn(fmaxf(c[1], 0.f))) * S.W3[n0 + 1];
+    sg8 += __bfloat162float(__float2bfloat16_rn(fmaxf(c[2], 0.f))) * S.W3[n0] +
+           __bfloat162float(__float2bfloat16_rn(fmaxf(c[3], 0.f))) * S.W3[n0 + 1];
+  }
+  sg += __shfl_xor_sync(0xffffffffu, sg, 1);
+  sg += __shfl_xor_sync(0xffffffffu, sg, 2);
+  sg8 += __shfl_xor_sync(0xffffffffu, sg8, 1);
+  sg8 += __shfl_xor_sync(0xffffffffu, sg8, 2);
+  *z3g = sg + S.b3;
+  *z3g8 = sg8 + S.b3;
+}
+
+// Proposal with its exact prefix in one pass: for every canonical edge e,
+// h_e = max(1, floor(scale (eps + g_e) + 1/2)) with g_e = sigmoid(network
+// logit of e's feature row), q_e = w_e h_e with w_e = prefix[e + 1] -
+// prefix[e], and qprefix[e + 1] = q_0 + ... + q_e.  Persistent blocks (the
+// network is staged in shared memory once per block) take tiles of kPTile
+// edges from a counter; each warp runs its 16-row sub-tiles on the tensor
+// cores with the next sub-tile's feature fragments loaded ahead; h and q go
+// through shared memory, so the global writes are coalesced; the tiles'
+// prefix sums are chained by the decoupled look-back.
+constexpr int kPThreads = 256;
+constexpr int kPRowsPerWarp = 128;
+constexpr int kPTile = (kPThreads / 32) * kPRowsPerWarp;  // 1024 edges
+constexpr int kPItems = kPTile / kPThreads;              // 4 per thread in the scan
+
+__global__ void __launch_bounds__(kPThreads, 3) k_proposal_scan(const float* __restrict__ params,
+                                                                const __nv_bfloat16* __restrict__ feat,
+                                                                const uint64_t* __restrict__ prefix, uint64_t m,
+                                                                float eps, float scale, uint16_t* __restrict__ h,
+                                                                uint64_t* __restrict__ qprefix, ScanState S,
+                                                                uint32_t* __restrict__ d_err) {
+  __shared__ MlpFwdShared net;
+  __shared__ unsigned long long s_pre[kPTile + 1];
+  __shared__ unsigned long long s_q[kPTile + kPTile / 8];
+  __shared__ uint16_t s_h[kPTile];
+  __shared__ unsigned long long s_warp[kPThreads / 32];
+  __shared__ unsigned long long s_excl;
+  __shared__ uint32_t s_tile, s_err;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, g = lane >> 2, qd = lane & 3;
+  load_mlp_fwd_shared(net, params);
+  if (tid == 0) s_err = 0;
+  auto pad = [](uint32_t i) { return i + (i >> 3); };
+  const uint64_t T = (m + kPTile - 1) / kPTile;
+  uint32_t err = 0;
+  for (;;) {
+    __syncthreads();  // the previous tile's shared arrays are consumed
+    if (tid == 0) s_tile = atomicAdd(S.counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= T) break;
+    const uint64_t base = (uint64_t)tile * kPTile;
+    const uint32_t rows = (uint32_t)(m - base < (uint64_t)kPTile ? m - base : (uint64_t)kPTile);
+    for (uint32_t i = tid; i <= rows; i += kPThreads) s_pre[i] = __ldg(prefix + base + i);
+    __syncthreads();
+    // 1. logits, h and q of the warp's rows
+    const uint32_t r0 = (uint32_t)wid * kPRowsPerWarp;
+    auto fetch = [&](uint32_t sub, uint32_t (&x)[4]) {
+      const uint32_t ra = r0 + sub * 16 + g, rb = ra + 8;
+      load_rows(feat, ra < rows ? (int64_t)(base + ra) : -1, rb < rows ? (int64_t)(base + rb) : -1, x);
+    };
+    uint32_t xn[4];
+    fetch(0, xn);
+#pragma unroll 1
+    for (uint32_t sub = 0; sub < kPRowsPerWarp / 16; sub++) {
+      uint32_t x[4] = {xn[0], xn[1], xn[2], xn[3]};
+      if (sub + 1 < kPRowsPerWarp / 16) fetch(sub + 1, xn);
+      float za, zb;
+      tile_logits(net, x, &za, &zb);
+      if (qd == 0) {
+#pragma unroll
+        for (int rr = 0; rr < 2; rr++) {
+          const uint32_t r = r0 + sub * 16 + g + 8 * rr;
+          uint16_t hv16 = 0;
+          unsigned long long qv = 0;
+          if (r < rows) {
+            const float v = floorf(scale * (eps + sigmoidf_(rr ? zb : za)) + 0.5f);
+            const uint32_t hv = v < 1.f ? 1u : (uint32_t)v;
+            const unsigned long long wv = s_pre[r + 1] - s_pre[r];
+            if (__umul64hi(wv, hv)) err |= kErrOverflow;
+            qv = wv * hv;
+            hv16 = (uint16_t)hv;
+          }
+          s_h[r] = hv16;
+          s_q[pad(r)] = qv;
         }
       }
     }
+    __syncthreads();
+    // 2. inclusive scan of q over the tile: kPItems consecutive per thread
+    unsigned long long run = 0;
+#pragma unroll
+    for (int k = 0; k < kPItems; k++) {
+      const uint32_t i = pad((uint32_t)tid * kPItems + k);
+      const unsigned long long nv = run + s_q[i];
+      if (nv < run) err |= kErrOverflow;
+      run = nv;
+      s_q[i] = run;
+    }
+    unsigned long long incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) {
+        if (incl + y < incl) err |= kErrOverflow;
+        incl += y;
+      }
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    unsigned long long before = 0;
+    for (int v = 0; v < wid; v++) {
+      if (before + s_warp[v] < before) err |= kErrOverflow;
+      before += s_warp[v];
+    }
+    if (before + incl < before) err |= kErrOverflow;
+    unsigned long long tile_sum = 0;
+    for (int v = 0; v < kPThreads / 32; v++) tile_sum += s_warp[v];
+    const unsigned long long thread_excl = before + incl - run;
+#pragma unroll
+    for (int k = 0; k < kPItems; k++) s_q[pad((uint32_t)tid * kPItems + k)] += thread_excl;
+    // 3. the tile's exclusive prefix (warp 0)
+    if (wid == 0) {
+      const unsigned long long excl = scan_lookback(S, tile, tile_sum, &err);
+      if (lane == 0) s_excl = excl;
+    }
+    __syncthreads();
+    // 4. coalesced writes
+    const unsigned long long tex = s_excl;
+    for (uint32_t i = tid; i < rows; i += kPThreads) {
+      qprefix[base + i + 1] = tex + s_q[pad(i)];
+      h[base + i] = s_h[i];
+    }
+    if (tile == 0 && tid == 0) qprefix[0] = 0;
   }
+  if (err) atomicOr(&s_err, err);
+  __syncthreads();
+  if (tid == 0 && s_err) atomicOr(d_err, s_err);
 }
 
 // ---------------------------------------------------------------------------
@@ -546,7 +712,7 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_mlp_grad(const float* __re
         const int k = lane + 32 * h2;
         float s = 0.f;
 #pragma unroll 8
-        for (int nn = 0; nn < kH; nn++) s += S.dz2[row][nn] * __bfloat162float(S.net.W2T[k * kH + nn]);
+        for (int nn = 0; nn < kH; nn++) s += S.dz2[row][nn] * __bfloat162float(S.net.W2T[k * kW2TS + nn]);
         S.dz1[row][k] *= s;
       }
     }
@@ -696,11 +862,11 @@ tc_status mlp_get_params(const tc_mlp* M, float* h) {
   return TC_OK;
 }
 
-tc_status launch_features(const tc_graph* g, const EdgeRec* rec, int64_t delta, uint16_t* feat, cudaStream_t st) {
+tc_status launch_features(const tc_graph* g, const EdgeWin* win, int64_t delta, uint16_t* feat, cudaStream_t st) {
   const uint64_t m = (uint64_t)g->m;
   if (!m) return TC_OK;
   k_features<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->pair_hash,
-                                                          g->hash_mask, g->pair_t, rec, m, delta,
+                                                          g->hash_mask, g->pair_t, win, m, delta,
                                                           reinterpret_cast<__nv_bfloat16*>(feat));
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
@@ -814,11 +980,28 @@ tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows
   return TC_OK;
 }
 
-tc_status launch_proposal(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
-                          float scale, uint16_t* h, uint64_t* q, cudaStream_t st) {
-  if (!m) return TC_OK;
-  k_proposal<<<grid_cap((m + 15) / 16, 4), 128, 0, st>>>(M->params, reinterpret_cast<const __nv_bfloat16*>(feat),
-                                                          prefix, m, eps, scale, h, q);
+size_t proposal_scan_scratch_bytes(uint64_t m) { return scan_state_bytes((m + kPTile - 1) / kPTile); }
+
+tc_status launch_proposal_scan(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
+                               float scale, uint16_t* h, uint64_t* qprefix, void* scratch, uint32_t* d_err,
+                               cudaStream_t st) {
+  if (!m) {
+    TC_CUDA(cudaMemsetAsync(qprefix, 0, sizeof(uint64_t), st));
+    return TC_OK;
+  }
+  const uint64_t T = (m + kPTile - 1) / kPTile;
+  if (T > 0xFFFFFFFFull) return set_error(TC_ERR_INVALID_ARG, "too many edges for the proposal scan");
+  TC_CUDA(cudaMemsetAsync(scratch, 0, scan_state_clear_bytes(T), st));
+  static int bps = 0;
+  if (!bps) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_proposal_scan, kPThreads, 0);
+    if (bps <= 0) bps = 1;
+  }
+  uint64_t blocks = (uint64_t)num_sms() * bps;
+  if (blocks > T) blocks = T;
+  k_proposal_scan<<<(unsigned)blocks, kPThreads, 0, st>>>(M->params, reinterpret_cast<const __nv_bfloat16*>(feat),
+                                                          prefix, m, eps, scale, h, qprefix,
+                                                          scan_state_view(scratch, T), d_err);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;

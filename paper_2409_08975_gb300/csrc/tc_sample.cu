@@ -13,141 +13,403 @@ namespace tc {
 // ---------------------------------------------------------------------------
 // Weights (Claim 1, Alg. 1): w_e = d1 * d3 for every canonical edge
 // e = (u, v, t), the sizes of the window of u's alpha1 list and of v's alpha3
-// list, found by binary search on time (four searches per edge).  Two passes
-// so that the lanes of a warp search the same list in lockstep and share the
-// probes of their searches:
-//   pass 1 runs over the in-lists (edges grouped by v) and finds v's window;
-//          its (lo3, d3) is parked in w at the edge's canonical position;
-//   pass 2 runs over the canonical order (edges grouped by u), finds u's
-//          window, writes the sampler record and w_e.
+// list, with their exact prefix sum, in one pass over the canonical order.
+//
+// The four binary searches per edge of Alg. 1 start from anchors built with
+// the lists (tc_graph::x_in, x_out, out2in; independent of delta): each
+// window bound is found by a galloping search (doubling steps, then
+// bisection) from a position where the list reaches time t, so a window of
+// d entries costs O(log d) probes near the anchor instead of O(log deg)
+// probes over the whole list.  The u side of consecutive edges (one source
+// vertex in time order) searches the same list at increasing positions.
+//
+// The prefix sum is the single-pass scan with decoupled look-back (Merrill &
+// Garland, 2016): each block takes the next tile of kWTile edges from a
+// counter (so every earlier tile belongs to a block that already runs),
+// publishes its tile sum, then adds the sums of the tiles before it until
+// it meets one whose inclusive prefix is published.  The waits on
+// predecessors are bounded; a wait that gives up sets kErrTimeout.
+//
 // A wedge anchor (3-vertex motif) has one window, at u or at v; the other
-// side is the dummy [0, 1), so w_e is the size of that window, and pass 1 is
-// skipped when the window is at u.
-
-// Edges per thread of the weight kernels, processed together so that the
-// loads of their independent searches overlap.
-// Pair-list searches of the sampler on the 32-bit times when the graph has them.
-#ifndef TC_COMPACT_PAIRS
-#define TC_COMPACT_PAIRS 1
-#endif
+// side is the dummy [0, 1), so w_e is the size of that window.
 
 // Window searches on the 32-bit time arrays when the graph has them.
 #ifndef TC_COMPACT_TIMES
 #define TC_COMPACT_TIMES 1
 #endif
 
-#ifndef TC_WEIGHTS_ILP
-#define TC_WEIGHTS_ILP 2
+// Pair-list searches of the sampler on the 32-bit times when the graph has them.
+#ifndef TC_COMPACT_PAIRS
+#define TC_COMPACT_PAIRS 1
 #endif
 
-template <bool Compact>
-__global__ void __launch_bounds__(256) k_weights_dst(const OutEdge* __restrict__ out_e,
-                                                     const uint32_t* __restrict__ out_off,
-                                                     const InEdge* __restrict__ in_e,
-                                                     const uint32_t* __restrict__ in_off,
-                                                     const uint32_t* __restrict__ in_eid,
-                                                     const uint32_t* __restrict__ out_t32,
-                                                     const uint32_t* __restrict__ in_t32, int64_t tmin, uint64_t m,
-                                                     Plan plan, int64_t delta, uint64_t* __restrict__ w) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < m; p0 += stride * TC_WEIGHTS_ILP) {
-    InEdge e[TC_WEIGHTS_ILP];
-    uint32_t lo3[TC_WEIGHTS_ILP], hi3[TC_WEIGHTS_ILP];
-#pragma unroll
-    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
-      const uint64_t p = p0 + j * stride;
-      if (p < m) e[j] = in_e[p];
+// Resident blocks per SM the weights kernel is compiled for (caps its registers).
+#ifndef TC_WEIGHTS_MIN_BLOCKS
+#define TC_WEIGHTS_MIN_BLOCKS 6
+#endif
+
+constexpr int kWThreads = 256;
+constexpr int kWItems = 8;
+constexpr int kWTile = kWThreads * kWItems;  // edges per tile
+// First position p in [s, f) whose time is >= x (Gt: > x), searched from a
+// position a in [s, f]: doubling steps away from a until the answer is
+// bracketed, then bisection.  At most 2 log2(f - s) + 2 probes.
+template <bool Gt, class TimeAt>
+__device__ __forceinline__ uint32_t gallop(uint32_t s, uint32_t f, uint32_t a, int64_t x, TimeAt tt) {
+  auto pred = [&](uint32_t p) {
+    const int64_t v = tt(p);
+    return Gt ? v > x : v >= x;
+  };
+  uint32_t lo, hi;  // the answer lies in [lo, hi]; pred(hi) holds or hi == f
+  if (a < f && !pred(a)) {
+    lo = a + 1;
+    hi = f;
+    uint32_t step = 1;
+    while (lo < hi) {
+      const uint32_t p = (hi - lo > step - 1) ? lo + (step - 1) : hi - 1;
+      if (pred(p)) {
+        hi = p;
+        break;
+      }
+      lo = p + 1;
+      step <<= 1;
     }
-#pragma unroll
-    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
-      const uint64_t p = p0 + j * stride;
-      if (p < m)
-        window_range<Compact>(out_e, out_off, in_e, in_off, out_t32, in_t32, tmin, plan.alpha3, plan.beta3,
-                              plan.closed, e[j].dst, e[j].t, delta, &lo3[j], &hi3[j]);
+  } else {
+    lo = s;
+    hi = a;
+    uint32_t step = 1;
+    while (hi > lo) {
+      const uint32_t p = (hi - lo > step) ? hi - step : lo;
+      if (!pred(p)) {
+        lo = p + 1;
+        break;
+      }
+      hi = p;
+      step <<= 1;
     }
-#pragma unroll
-    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
-      const uint64_t p = p0 + j * stride;
-      if (p < m) w[in_eid[p]] = (uint64_t)lo3[j] | ((uint64_t)(hi3[j] - lo3[j]) << 32);
-    }
+  }
+  while (lo < hi) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if (pred(mid)) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// The window of list [s, f) around time t (beta < 0: before, else after;
+// strict or closed at t) as positions [*lo, *hi), searched from an anchor a
+// with lower_bound(t) <= a <= upper_bound(t).
+template <class TimeAt>
+__device__ __forceinline__ void window_from(uint32_t s, uint32_t f, uint32_t a, int beta, int closed, int64_t t,
+                                            int64_t delta, TimeAt tt, uint32_t* lo, uint32_t* hi) {
+  if (beta < 0) {
+    *hi = closed ? gallop<true>(s, f, a, t, tt) : gallop<false>(s, f, a, t, tt);
+    *lo = gallop<false>(s, f, *hi, sat_sub(t, delta), tt);
+  } else {
+    *lo = closed ? gallop<false>(s, f, a, t, tt) : gallop<true>(s, f, a, t, tt);
+    *hi = gallop<true>(s, f, *lo, sat_add(t, delta), tt);
   }
 }
 
+struct WeightsArgs {
+  const OutEdge* out_e;
+  const InEdge* in_e;
+  const uint32_t* out_off;
+  const uint32_t* in_off;
+  const uint32_t* out_t32;
+  const uint32_t* in_t32;
+  const uint32_t* x_in;
+  const uint32_t* x_out;
+  const uint32_t* out2in;
+  int64_t tmin;
+  uint64_t m;
+  int64_t delta;
+  int alpha1, alpha3, beta1, beta3, closed;
+  EdgeWin* win;
+  uint64_t* prefix;
+  uint64_t* w;  // optional
+  ScanState scan;  // tile states of the prefix sum
+  uint32_t* err;
+};
+
+// Window of side alpha (< 0: the vertex's in-list, > 0: its out-list) of
+// canonical edge i = (x, ., t), searched from anchor a.
 template <bool Compact>
-__global__ void __launch_bounds__(256) k_weights_src(const OutEdge* __restrict__ out_e,
-                                                     const uint32_t* __restrict__ out_off,
-                                                     const InEdge* __restrict__ in_e,
-                                                     const uint32_t* __restrict__ in_off,
-                                                     const uint32_t* __restrict__ out_t32,
-                                                     const uint32_t* __restrict__ in_t32, int64_t tmin, uint64_t m,
-                                                     Plan plan, int64_t delta, EdgeRec* __restrict__ rec,
-                                                     uint64_t* __restrict__ w) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += stride * TC_WEIGHTS_ILP) {
-    OutEdge e[TC_WEIGHTS_ILP];
-    uint32_t lo1[TC_WEIGHTS_ILP], hi1[TC_WEIGHTS_ILP];
-#pragma unroll
-    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
-      const uint64_t i = i0 + j * stride;
-      if (i < m) e[j] = out_e[i];
-    }
-#pragma unroll
-    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
-      const uint64_t i = i0 + j * stride;
-      lo1[j] = 0;  // a wedge at v: the u side is the one-position dummy
-      hi1[j] = 1;
-      if (i < m && plan.alpha1 != 0)
-        window_range<Compact>(out_e, out_off, in_e, in_off, out_t32, in_t32, tmin, plan.alpha1, plan.beta1,
-                              plan.closed, e[j].src, e[j].t, delta, &lo1[j], &hi1[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < TC_WEIGHTS_ILP; j++) {
-      const uint64_t i = i0 + j * stride;
-      if (i >= m) continue;
-      const uint64_t parked = plan.alpha3 != 0 ? w[i] : (1ull << 32);  // v side [0, 1) for a wedge at u
-      EdgeRec r;
-      r.u = e[j].src;
-      r.v = e[j].dst;
-      r.t = e[j].t;
-      r.lo1 = lo1[j];
-      r.d1 = hi1[j] - lo1[j];
-      r.lo3 = (uint32_t)parked;
-      r.d3 = (uint32_t)(parked >> 32);
-      rec[i] = r;
-      w[i] = (uint64_t)r.d1 * (uint64_t)r.d3;
-    }
+__device__ __forceinline__ void side_window(const WeightsArgs& A, int alpha, int beta, int32_t x, uint32_t a,
+                                            int64_t t, uint32_t* lo, uint32_t* hi) {
+  if (alpha < 0) {
+    auto tt = [&](uint32_t p) -> int64_t { return Compact ? (int64_t)__ldg(A.in_t32 + p) + A.tmin : A.in_e[p].t; };
+    window_from(__ldg(A.in_off + x), __ldg(A.in_off + x + 1), a, beta, A.closed, t, A.delta, tt, lo, hi);
+  } else {
+    auto tt = [&](uint32_t p) -> int64_t { return Compact ? (int64_t)__ldg(A.out_t32 + p) + A.tmin : A.out_e[p].t; };
+    window_from(__ldg(A.out_off + x), __ldg(A.out_off + x + 1), a, beta, A.closed, t, A.delta, tt, lo, hi);
   }
 }
 
-tc_status launch_weights(const tc_graph* g, const Plan& plan, int64_t delta, EdgeRec* rec, uint64_t* w,
-                         cudaStream_t st) {
-  const uint64_t m = (uint64_t)g->m;
-  if (m == 0) return TC_OK;
-  const unsigned blocks = (unsigned)((m + 256 * TC_WEIGHTS_ILP - 1) / (256 * TC_WEIGHTS_ILP));
-  const bool compact = TC_COMPACT_TIMES && g->out_t32 && g->in_t32;
-  if (plan.alpha3 != 0) {  // a wedge at u has no v-side window
-    if (compact)
-      k_weights_dst<true><<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->in_eid, g->out_t32,
-                                                  g->in_t32, g->tmin, m, plan, delta, w);
-    else
-      k_weights_dst<false><<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->in_eid, nullptr,
-                                                   nullptr, 0, m, plan, delta, w);
-    TC_LAUNCHED(1);
-    TC_CUDA(cudaGetLastError());
+// Fused: the tile scan and look-back follow in the same kernel; otherwise
+// the kernel writes w (A.w) and the windows only, block b taking tile b.
+template <bool Compact, bool Fused>
+__global__ void __launch_bounds__(kWThreads, TC_WEIGHTS_MIN_BLOCKS) k_weights_scan(const __grid_constant__ WeightsArgs A) {
+  __shared__ unsigned long long s_w[Fused ? kWTile + kWTile / 8 : 1];  // one pad word per 8: conflict-free rows
+  __shared__ unsigned long long s_warp[kWThreads / 32];
+  __shared__ unsigned long long s_excl;
+  __shared__ uint32_t s_tile, s_err;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (Fused) {
+    if (tid == 0) {
+      s_tile = atomicAdd(A.scan.counter, 1u);
+      s_err = 0;
+    }
+    __syncthreads();
   }
-  if (compact)
-    k_weights_src<true><<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, g->out_t32, g->in_t32,
-                                                g->tmin, m, plan, delta, rec, w);
-  else
-    k_weights_src<false><<<blocks, 256, 0, st>>>(g->out_e, g->out_off, g->in_e, g->in_off, nullptr, nullptr, 0, m,
-                                                 plan, delta, rec, w);
+  const uint32_t tile = Fused ? s_tile : blockIdx.x;
+  const uint64_t base = (uint64_t)tile * kWTile;
+  auto pad = [](uint32_t q) { return q + (q >> 3); };
+  uint32_t err = 0;
+  // 1. windows and weights of the tile's edges (coalesced: edge base + j * 256 + tid)
+#pragma unroll 1
+  for (int j = 0; j < kWItems; j++) {
+    const uint32_t q = (uint32_t)j * kWThreads + tid;
+    const uint64_t i = base + q;
+    unsigned long long wv = 0;
+    if (i < A.m) {
+      const OutEdge e = A.out_e[i];
+      uint32_t lo1 = 0, hi1 = 1, lo3 = 0, hi3 = 1;  // a wedge's unused side is [0, 1)
+      if (A.alpha1 != 0)
+        side_window<Compact>(A, A.alpha1, A.beta1, e.src, A.alpha1 < 0 ? __ldg(A.x_in + i) : (uint32_t)i, e.t, &lo1,
+                             &hi1);
+      if (A.alpha3 != 0)
+        side_window<Compact>(A, A.alpha3, A.beta3, e.dst, A.alpha3 < 0 ? __ldg(A.out2in + i) : __ldg(A.x_out + i),
+                             e.t, &lo3, &hi3);
+      EdgeWin r;
+      r.lo1 = lo1;
+      r.d1 = hi1 - lo1;
+      r.lo3 = lo3;
+      r.d3 = hi3 - lo3;
+      A.win[i] = r;
+      wv = (unsigned long long)r.d1 * (unsigned long long)r.d3;
+      if (A.w) A.w[i] = wv;
+    }
+    if (Fused) s_w[pad(q)] = wv;
+  }
+  if (!Fused) return;
+  __syncthreads();
+  // 2. inclusive scan of the tile: each thread its 8 consecutive edges, then
+  // the 256 thread sums
+  unsigned long long run = 0;
+#pragma unroll
+  for (int k = 0; k < kWItems; k++) {
+    const uint32_t q = pad((uint32_t)tid * kWItems + k);
+    const unsigned long long nv = run + s_w[q];
+    if (nv < run) err |= kErrOverflow;
+    run = nv;
+    s_w[q] = run;
+  }
+  unsigned long long incl = run;  // warp-inclusive scan of the thread sums
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) {
+      if (incl + y < incl) err |= kErrOverflow;
+      incl += y;
+    }
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  unsigned long long before = 0;
+  for (int v = 0; v < wid; v++) {
+    if (before + s_warp[v] < before) err |= kErrOverflow;
+    before += s_warp[v];
+  }
+  if (before + incl < before) err |= kErrOverflow;  // the tile sum is the last thread's before + incl
+  unsigned long long tile_sum = 0;
+  for (int v = 0; v < kWThreads / 32; v++) tile_sum += s_warp[v];
+  const unsigned long long thread_excl = before + incl - run;
+  // 3. the tile's exclusive prefix from its predecessors (warp 0)
+  if (wid == 0) {
+    const unsigned long long excl = scan_lookback(A.scan, tile, tile_sum, &err);
+    if (lane == 0) s_excl = excl;
+  }
+  if (err) atomicOr(&s_err, err);
+  __syncthreads();
+  // 4. prefix[i + 1] = tile prefix + inclusive sum within the tile
+  const unsigned long long tex = s_excl;
+#pragma unroll
+  for (int k = 0; k < kWItems; k++) {
+    const uint32_t q = pad((uint32_t)tid * kWItems + k);
+    s_w[q] += thread_excl;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kWItems; j++) {
+    const uint32_t q = (uint32_t)j * kWThreads + tid;
+    const uint64_t i = base + q;
+    if (i < A.m) A.prefix[i + 1] = tex + s_w[pad(q)];
+  }
+  if (tile == 0 && tid == 0) A.prefix[0] = 0;
+  if (tid == 0 && s_err) atomicOr(A.err, s_err);
+}
+
+// Exclusive prefix of n uint64 in one pass (out[0] = 0, out[i + 1] = in[0]
+// + ... + in[i]; in and out distinct): tiles of kWTile values, coalesced
+// through shared memory, chained by the decoupled look-back.
+__global__ void __launch_bounds__(kWThreads) k_scan_lookback(const uint64_t* __restrict__ in, uint64_t n,
+                                                             uint64_t* __restrict__ out, ScanState S,
+                                                             uint32_t* __restrict__ d_err) {
+  __shared__ unsigned long long s_w[kWTile + kWTile / 8];
+  __shared__ unsigned long long s_warp[kWThreads / 32];
+  __shared__ unsigned long long s_excl;
+  __shared__ uint32_t s_tile, s_err;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    s_tile = atomicAdd(S.counter, 1u);
+    s_err = 0;
+  }
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * kWTile;
+  auto pad = [](uint32_t q) { return q + (q >> 3); };
+  uint32_t err = 0;
+#pragma unroll
+  for (int j = 0; j < kWItems; j++) {
+    const uint32_t q = (uint32_t)j * kWThreads + tid;
+    const uint64_t i = base + q;
+    s_w[pad(q)] = i < n ? __ldg(in + i) : 0ull;
+  }
+  __syncthreads();
+  unsigned long long run = 0;
+#pragma unroll
+  for (int k = 0; k < kWItems; k++) {
+    const uint32_t q = pad((uint32_t)tid * kWItems + k);
+    const unsigned long long nv = run + s_w[q];
+    if (nv < run) err |= kErrOverflow;
+    run = nv;
+    s_w[q] = run;
+  }
+  unsigned long long incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) {
+      if (incl + y < incl) err |= kErrOverflow;
+      incl += y;
+    }
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  unsigned long long before = 0;
+  for (int v = 0; v < wid; v++) {
+    if (before + s_warp[v] < before) err |= kErrOverflow;
+    before += s_warp[v];
+  }
+  if (before + incl < before) err |= kErrOverflow;
+  unsigned long long tile_sum = 0;
+  for (int v = 0; v < kWThreads / 32; v++) tile_sum += s_warp[v];
+  const unsigned long long thread_excl = before + incl - run;
+  if (wid == 0) {
+    const unsigned long long excl = scan_lookback(S, tile, tile_sum, &err);
+    if (lane == 0) s_excl = excl;
+  }
+  if (err) atomicOr(&s_err, err);
+#pragma unroll
+  for (int k = 0; k < kWItems; k++) s_w[pad((uint32_t)tid * kWItems + k)] += thread_excl;
+  __syncthreads();
+  const unsigned long long tex = s_excl;
+#pragma unroll
+  for (int j = 0; j < kWItems; j++) {
+    const uint32_t q = (uint32_t)j * kWThreads + tid;
+    const uint64_t i = base + q;
+    if (i < n) out[i + 1] = tex + s_w[pad(q)];
+  }
+  if (tile == 0 && tid == 0) out[0] = 0;
+  if (tid == 0 && s_err) atomicOr(d_err, s_err);
+}
+
+// The weights and the prefix as one fused pass (each block waits on the sums
+// of the blocks before it) or as two: the windows and w, then the
+// single-pass scan of w (whose tiles cost the same, so their waits are
+// short while the windows' cost varies with the degrees).
+#ifndef TC_WEIGHTS_FUSED_SCAN
+#define TC_WEIGHTS_FUSED_SCAN 0
+#endif
+
+static uint64_t weights_tiles(uint64_t m) { return (m + kWTile - 1) / kWTile; }
+
+size_t weights_scan_scratch_bytes(uint64_t m) {
+  return scan_state_bytes(weights_tiles(m)) + (TC_WEIGHTS_FUSED_SCAN ? 0 : scan_align256(8 * (m ? m : 1)));
+}
+
+tc_status launch_scan_lookback(const uint64_t* in, uint64_t n, uint64_t* out, void* scratch, uint32_t* d_err,
+                               cudaStream_t st) {
+  if (n == 0) {
+    TC_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
+    return TC_OK;
+  }
+  const uint64_t T = weights_tiles(n);
+  if (T > 0xFFFFFFFFull) return set_error(TC_ERR_INVALID_ARG, "too many values for the scan");
+  TC_CUDA(cudaMemsetAsync(scratch, 0, scan_state_clear_bytes(T), st));
+  k_scan_lookback<<<(unsigned)T, kWThreads, 0, st>>>(in, n, out, scan_state_view(scratch, T), d_err);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
 
+tc_status launch_weights_scan(const tc_graph* g, const Plan& plan, int64_t delta, EdgeWin* win, uint64_t* prefix,
+                              uint64_t* w, void* scratch, uint32_t* d_err, cudaStream_t st) {
+  const uint64_t m = (uint64_t)g->m;
+  if (m == 0) {
+    TC_CUDA(cudaMemsetAsync(prefix, 0, sizeof(uint64_t), st));
+    return TC_OK;
+  }
+  const uint64_t T = weights_tiles(m);
+  if (T > 0xFFFFFFFFull) return set_error(TC_ERR_INVALID_ARG, "too many edges for the weights scan");
+  WeightsArgs A;
+  A.scan = scan_state_view(scratch, T);
+  const bool fused = TC_WEIGHTS_FUSED_SCAN;
+  // the counter and the tile flags start at zero (the sums are written before their flags)
+  if (fused) TC_CUDA(cudaMemsetAsync(scratch, 0, scan_state_clear_bytes(T), st));
+  uint64_t* wbuf = w ? w : (uint64_t*)((char*)scratch + scan_state_bytes(T));
+  const bool compact = TC_COMPACT_TIMES && g->out_t32 && g->in_t32;
+  A.out_e = g->out_e;
+  A.in_e = g->in_e;
+  A.out_off = g->out_off;
+  A.in_off = g->in_off;
+  A.out_t32 = g->out_t32;
+  A.in_t32 = g->in_t32;
+  A.x_in = g->x_in;
+  A.x_out = g->x_out;
+  A.out2in = g->out2in;
+  A.tmin = g->tmin;
+  A.m = m;
+  A.delta = delta;
+  A.alpha1 = plan.alpha1;
+  A.alpha3 = plan.alpha3;
+  A.beta1 = plan.beta1;
+  A.beta3 = plan.beta3;
+  A.closed = plan.closed;
+  A.win = win;
+  A.prefix = prefix;
+  A.w = fused ? w : wbuf;
+  A.err = d_err;
+  if (fused) {
+    if (compact)
+      k_weights_scan<true, true><<<(unsigned)T, kWThreads, 0, st>>>(A);
+    else
+      k_weights_scan<false, true><<<(unsigned)T, kWThreads, 0, st>>>(A);
+    TC_LAUNCHED(1);
+    TC_CUDA(cudaGetLastError());
+    return TC_OK;
+  }
+  if (compact)
+    k_weights_scan<true, false><<<(unsigned)T, kWThreads, 0, st>>>(A);
+  else
+    k_weights_scan<false, false><<<(unsigned)T, kWThreads, 0, st>>>(A);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return launch_scan_lookback(wbuf, m, prefix, scratch, d_err, st);
+}
+
 // ---------------------------------------------------------------------------
-// Index layout: [header 256 B][EdgeRec m][guide uint32 (2^gbits + 1)].
+// Index layout: [header 256 B][EdgeWin m][guide uint32 (2^gbits + 1)].
 
 int guide_bits(uint64_t m) {
   int b = 0;
@@ -158,12 +420,12 @@ int guide_bits(uint64_t m) {
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t index_bytes(uint64_t m) {
-  return kIndexHeaderBytes + align256(sizeof(EdgeRec) * m) + sizeof(uint32_t) * ((1ull << guide_bits(m)) + 1);
+  return kIndexHeaderBytes + align256(sizeof(EdgeWin) * m) + sizeof(uint32_t) * ((1ull << guide_bits(m)) + 1);
 }
 
 struct IndexView {
   IndexHeader* hdr;
-  EdgeRec* rec;
+  EdgeWin* win;
   uint32_t* guide;
 };
 
@@ -171,8 +433,8 @@ static IndexView index_view(void* index, uint64_t m) {
   char* p = (char*)index;
   IndexView v;
   v.hdr = (IndexHeader*)p;
-  v.rec = (EdgeRec*)(p + kIndexHeaderBytes);
-  v.guide = (uint32_t*)(p + kIndexHeaderBytes + align256(sizeof(EdgeRec) * m));
+  v.win = (EdgeWin*)(p + kIndexHeaderBytes);
+  v.guide = (uint32_t*)(p + kIndexHeaderBytes + align256(sizeof(EdgeWin) * m));
   return v;
 }
 
@@ -286,7 +548,7 @@ struct SamplerArgs {
   int64_t tmin;
   const uint64_t* prefix;
   const IndexHeader* hdr;
-  const EdgeRec* rec;
+  const EdgeWin* win;
   const uint32_t* guide;
   uint64_t k, seed, offset;
   const uint32_t* order;  // processing order of the chunk's samples (NULL: in id order)
@@ -299,7 +561,7 @@ struct SamplerArgs {
   SampleSums* sums;
   // proposal mode (h != NULL): the middle edge is drawn from the proposal's
   // prefix and guide (hdr, prefix, guide), the records come from the plain
-  // index (rec, rec_hdr), and each hit adds X and X^2 to bins[3 h + 0..2]
+  // index (win, rec_hdr), and each hit adds X and X^2 to bins[3 h + 0..2]
   const uint16_t* h;
   unsigned long long* bins;
   const IndexHeader* rec_hdr;
@@ -579,16 +841,18 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS_DECL) k_path_sum(con
       const uint32_t mid = lo + ((hi - lo + 1) >> 1);
       if (__ldg(A.prefix + mid) <= p) lo = mid; else hi = mid - 1;
     }
-    const EdgeRec e = A.rec[lo];
-    if (e.d1 == 0 || e.d3 == 0) { err |= kErrBounds; continue; }
+    if (lo >= A.m) { err |= kErrBounds; continue; }
+    const EdgeWin wn = A.win[lo];
+    const OutEdge e = A.out_e[lo];
+    if (wn.d1 == 0 || wn.d3 == 0) { err |= kErrBounds; continue; }
     const uint64_t j = p - __ldg(A.prefix + lo);
-    const uint32_t p1 = e.lo1 + (uint32_t)(j / e.d3), p3 = e.lo3 + (uint32_t)(j % e.d3);
-    if (lo >= A.m || p1 >= A.m || p3 >= A.m) { err |= kErrBounds; continue; }
+    const uint32_t p1 = wn.lo1 + (uint32_t)(j / wn.d3), p3 = wn.lo3 + (uint32_t)(j % wn.d3);
+    if (p1 >= A.m || p3 >= A.m) { err |= kErrBounds; continue; }
     int32_t up, vp;
     int64_t t1, t3;
     end_edge(A, P.alpha1, p1, &up, &t1);
     end_edge(A, P.alpha3, p3, &vp, &t3);
-    const uint64_t X = check_motif(A, P, up, e.u, e.v, vp, t1, e.t, t3, &s_err, &checked);
+    const uint64_t X = check_motif(A, P, up, e.src, e.dst, vp, t1, e.t, t3, &s_err, &checked);
     const uint64_t nx = sx + X;
     if (nx < sx) err |= kErrOverflow;
     sx = nx;
@@ -597,7 +861,6 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS_DECL) k_path_sum(con
   }
   block_commit(A.sums, W, sx, sx2, hits, checked, err, s_err, s_x, s_x2lo, s_x2hi, s_hits, s_checked);
 }
-
 
 // The rejection loops: the first attempt is tested in the sampler itself and
 // these run only when it is rejected (probability below range / 2^64),
@@ -629,7 +892,9 @@ __device__ __forceinline__ void sample_one(const SamplerArgs& A, const Plan& P, 
     const uint32_t mid = lo + ((hi - lo + 1) >> 1);
     if (__ldg(A.prefix + mid) <= r2) lo = mid; else hi = mid - 1;
   }
-  const EdgeRec e = A.rec[lo];
+  if (lo >= A.m) { T.err |= kErrBounds; return; }
+  const EdgeWin e = A.win[lo];
+  const OutEdge me = A.out_e[lo];  // the middle edge (u, v, t)
   if (e.d1 == 0 || e.d3 == 0) { T.err |= kErrBounds; return; }  // index not built from this prefix
   // e1 and e3 from the two halves of block 1; a draw over one position is 0
   // without drawing (a wedge's dummy end, or a window of one edge)
@@ -645,12 +910,12 @@ __device__ __forceinline__ void sample_one(const SamplerArgs& A, const Plan& P, 
     }
   }
   const uint32_t p1 = e.lo1 + (uint32_t)r1, p3 = e.lo3 + (uint32_t)r3;
-  if (lo >= A.m || p1 >= A.m || p3 >= A.m) { T.err |= kErrBounds; return; }
+  if (p1 >= A.m || p3 >= A.m) { T.err |= kErrBounds; return; }
   int32_t up, vp;
   int64_t t1, t3;
   end_edge(A, P.alpha1, p1, &up, &t1);
   end_edge(A, P.alpha3, p3, &vp, &t3);
-  const uint64_t X = check_motif(A, P, up, e.u, e.v, vp, t1, e.t, t3, s_err, &T.checked);
+  const uint64_t X = check_motif(A, P, up, me.src, me.dst, vp, t1, me.t, t3, s_err, &T.checked);
   if (A.h && X) {  // exact per-h bins of the proposal estimator
     unsigned long long* bin = A.bins + 3 * (uint64_t)__ldg(A.h + lo);
     atomicAdd(bin, (unsigned long long)X);
@@ -1037,7 +1302,7 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   A.tmin = g->tmin;
   A.prefix = prefix;
   A.hdr = v.hdr;
-  A.rec = v.rec;
+  A.win = v.win;
   A.guide = v.guide;
   A.k = k;
   A.order = nullptr;
@@ -1121,7 +1386,7 @@ tc_status launch_path_sum(const tc_graph* g, const Plan& plan, int64_t delta, co
   A.tmin = g->tmin;
   A.prefix = prefix;
   A.hdr = v.hdr;
-  A.rec = v.rec;
+  A.win = v.win;
   A.guide = v.guide;
   A.m = (uint32_t)m;
   A.delta = delta;
@@ -1169,7 +1434,7 @@ void batch_query_record(void* h_rec, const tc_graph* g, const Plan& plan, int64_
   A.tmin = g->tmin;
   A.prefix = prefix;
   A.hdr = v.hdr;
-  A.rec = v.rec;
+  A.win = v.win;
   A.guide = v.guide;
   A.k = k;
   A.seed = seed;

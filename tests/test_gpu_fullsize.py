@@ -57,9 +57,9 @@ def test_weights_full_size(setup):
     assert w.W == int(opre[-1]) > 0
     assert (w.w.cpu().numpy().view(np.uint64)[:m] == ow["w"]).all()
     assert (w.prefix.cpu().numpy().view(np.uint64) == opre).all()
-    rec = w.index.cpu().numpy()[256:256 + 32 * m].view(np.uint32).reshape(m, 8)
-    assert (rec[:, 4] == ow["lo1"]).all() and (rec[:, 5] == ow["d1"]).all()
-    assert (rec[:, 6] == ow["lo3"]).all() and (rec[:, 7] == ow["d3"]).all()
+    rec = w.index.cpu().numpy()[256:256 + 16 * m].view(np.uint32).reshape(m, 4)
+    assert (rec[:, 0] == ow["lo1"]).all() and (rec[:, 1] == ow["d1"]).all()
+    assert (rec[:, 2] == ow["lo3"]).all() and (rec[:, 3] == ow["d3"]).all()
 
 
 def test_sampler_full_size(setup):

@@ -102,7 +102,7 @@ def test_csr_bit_exact(tc, case):
 def _records(w):
     idx = w.index.cpu().numpy()
     m = (len(w.prefix) - 1)
-    rec = idx[256:256 + 32 * m].view(np.uint32).reshape(m, 8)
+    rec = idx[256:256 + 16 * m].view(np.uint32).reshape(m, 4)
     return rec
 
 
@@ -124,8 +124,8 @@ def test_weights_prefix_bit_exact(tc, case):
                 assert (_u64(w.w)[:og.m] == ow["w"]).all(), (edges, window, delta)
                 assert (_u64(w.prefix) == opre).all()
                 rec = _records(w)
-                assert (rec[:, 4] == ow["lo1"]).all() and (rec[:, 5] == ow["d1"]).all()
-                assert (rec[:, 6] == ow["lo3"]).all() and (rec[:, 7] == ow["d3"]).all()
+                assert (rec[:, 0] == ow["lo1"]).all() and (rec[:, 1] == ow["d1"]).all()
+                assert (rec[:, 2] == ow["lo3"]).all() and (rec[:, 3] == ow["d3"]).all()
 
 
 @pytest.mark.parametrize("case", GRAPHS, ids=lambda c: c[0])

@@ -89,9 +89,9 @@ def test_wedge_weights_and_sampler_bit_exact(tc, case):
             m = og.m
             assert (_u64(w.w)[:m] == ow["w"]).all(), (edges, window)
             assert (_u64(w.prefix) == opre).all()
-            rec = w.index.cpu().numpy()[256:256 + 32 * m].view(np.uint32).reshape(m, 8)
-            assert (rec[:, 4] == ow["lo1"]).all() and (rec[:, 5] == ow["d1"]).all()
-            assert (rec[:, 6] == ow["lo3"]).all() and (rec[:, 7] == ow["d3"]).all()
+            rec = w.index.cpu().numpy()[256:256 + 16 * m].view(np.uint32).reshape(m, 4)
+            assert (rec[:, 0] == ow["lo1"]).all() and (rec[:, 1] == ow["d1"]).all()
+            assert (rec[:, 2] == ow["lo3"]).all() and (rec[:, 3] == ow["d3"]).all()
             if w.W == 0:
                 continue
             k, seed, off = 20_000, 4242, 31
