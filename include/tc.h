@@ -185,12 +185,8 @@ tc_status tc_sample_index_bytes(const tc_graph* g, size_t* h_bytes);
  *   d_index   tc_sample_index_bytes(g) bytes, 256-byte aligned; receives the
  *             sampling index consumed by tc_sample_estimate
  *   h_W       optional; receives W = prefix[m] (synchronises the stream)
- * The weights, the windows and the prefix are formed in one pass over the
- * edges (a single-pass scan whose blocks wait, for a bounded time, on the
- * sums of the blocks before them).
  * Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED_MOTIF, TC_ERR_OVERFLOW (W
- * does not fit 64 bits; reported when h_W is requested), TC_ERR_TIMEOUT (a
- * wait gave up; reported when h_W is requested), TC_ERR_CUDA.
+ * does not fit 64 bits; reported when h_W is requested), TC_ERR_CUDA.
  */
 tc_status tc_path_weights(const tc_graph* g, const tc_motif* motif, int64_t delta, uint64_t* d_w,
                           uint64_t* d_prefix, void* d_index, uint64_t* h_W, void* stream);

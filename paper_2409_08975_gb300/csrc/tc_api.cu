@@ -69,7 +69,6 @@ tc_status device_status(uint32_t bits, const char* what) {
   if (bits & kErrOverflow) return set_error(TC_ERR_OVERFLOW, w + ": a 64-bit count overflowed");
   if (bits & kErrRng) return set_error(TC_ERR_RNG_EXHAUSTED, w + ": 64 rejected draws in a row");
   if (bits & kErrBounds) return set_error(TC_ERR_BOUNDS, w + ": device index check failed");
-  if (bits & kErrTimeout) return set_error(TC_ERR_TIMEOUT, w + ": a bounded device wait gave up");
   return TC_OK;
 }
 
@@ -821,7 +820,8 @@ tc_status tc_proposal_weights(const tc_mlp* mlp, const tc_graph* g, const tc_mot
   e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) s = cuda_status(e, "tc_proposal_weights allocation");
   if (s == TC_OK)
-    s = launch_proposal_scan(mlp, d_feat, d_prefix, m, eps, (float)scale, d_h, d_qprefix, scratch + 256, err, st);
+    s = launch_proposal_scan(mlp, d_feat, d_prefix, m, eps, (float)scale, d_h, d_qprefix,
+                             (uint32_t*)((char*)d_qindex + kProposalRangeOffset), scratch + 256, err, st);
   if (s == TC_OK)
     s = launch_guide_at(g, plan, delta, d_qprefix, (IndexHeader*)d_qindex,
                         (uint32_t*)((char*)d_qindex + kIndexHeaderBytes), err, st);

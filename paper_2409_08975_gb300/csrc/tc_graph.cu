@@ -225,6 +225,26 @@ tc_status scan_u64_in_scratch(const uint64_t* in, uint64_t* out, uint64_t n, boo
   return scan_in_scratch<uint64_t>(in, out, n, write_total, d_err, scratch, scratch_words, st);
 }
 
+// The reduce-then-scan with the first level's tile sums already formed by
+// the kernel that wrote in (sums[t] = the sum of in over tile t of
+// kScanTile values, its overflow already reported): the sums are scanned in
+// place into tile offsets, then each tile is scanned from its offset.
+tc_status scan_u64_from_tile_sums(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* sums, uint32_t* d_err,
+                                  uint64_t* scratch, uint64_t scratch_words, cudaStream_t st) {
+  if (n == 0) {
+    TC_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
+    return TC_OK;
+  }
+  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles > 1) TC_TRY(scan_in_scratch<uint64_t>(sums, sums, tiles, false, d_err, scratch, scratch_words, st));
+  k_tile_scan<uint64_t><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tiles > 1 ? sums : nullptr, out, true, d_err);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+uint64_t scan_tile_size() { return kScanTile; }
+
 tc_status scan_u32_in_scratch(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* scratch,
                               uint64_t scratch_words, cudaStream_t st) {
   return scan_in_scratch<uint32_t>(in, out, n, true, nullptr, scratch, scratch_words, st);

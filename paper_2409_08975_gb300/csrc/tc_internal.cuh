@@ -53,6 +53,9 @@ __host__ __device__ __forceinline__ uint64_t pair_key(uint32_t x, uint32_t y) {
 
 constexpr uint64_t kIndexMagic = 0x7463696e64657831ull;  // "tcindex1"
 constexpr size_t kIndexHeaderBytes = 256;
+// A proposal index keeps its smallest and largest h (uint32 each) at this
+// offset of its header, after the IndexHeader fields.
+constexpr size_t kProposalRangeOffset = 192;
 
 // Header at the start of a sampling index; written on the device by the guide
 // kernel so that sampling needs no host round trip.
@@ -69,6 +72,7 @@ struct IndexHeader {
   uint64_t graph_id;
   uint32_t status;   // device error bits of the weights and prefix pass
 };
+static_assert(sizeof(IndexHeader) <= 192, "the proposal's h range follows the header fields");
 
 // Device error bits, reduced into a status at the next synchronisation.
 enum : uint32_t {
@@ -77,7 +81,6 @@ enum : uint32_t {
   kErrBounds = 1u << 2,
   kErrBadId = 1u << 3,
   kErrIndexMismatch = 1u << 4,
-  kErrTimeout = 1u << 5,
 };
 
 // ---------------------------------------------------------------------------
@@ -286,117 +289,6 @@ __device__ __forceinline__ void window_range(const OutEdge* __restrict__ out_e,
 }
 
 // ---------------------------------------------------------------------------
-// Single-pass exclusive scan across the tiles of one launch (decoupled
-// look-back, Merrill & Garland 2016).  Each block takes the next tile from a
-// counter (so every earlier tile belongs to a block that already runs),
-// publishes its tile sum (flag 1), adds the sums of the tiles before it
-// until it meets a published inclusive prefix (flag 2), and publishes its
-// own.  Tile states live in caller scratch: a counter, then flags, tile sums
-// and inclusive prefixes; the counter and the flags are cleared before each
-// launch.  Waits on predecessors are bounded (kLookbackSpins polls).
-
-struct ScanState {
-  uint32_t* counter;
-  uint32_t* flag;  // 0 none, 1 tile sum published, 2 inclusive prefix published
-  unsigned long long* agg;
-  unsigned long long* inc;
-};
-
-inline size_t scan_align256(size_t x) { return (x + 255) & ~(size_t)255; }
-inline size_t scan_state_clear_bytes(uint64_t tiles) { return 256 + scan_align256(4 * (tiles ? tiles : 1)); }
-inline size_t scan_state_bytes(uint64_t tiles) {
-  return scan_state_clear_bytes(tiles) + 2 * scan_align256(8 * (tiles ? tiles : 1));
-}
-inline ScanState scan_state_view(void* scratch, uint64_t tiles) {
-  char* p = (char*)scratch;
-  const size_t c = scan_state_clear_bytes(tiles), a = scan_align256(8 * (tiles ? tiles : 1));
-  ScanState S;
-  S.counter = (uint32_t*)p;
-  S.flag = (uint32_t*)(p + 256);
-  S.agg = (unsigned long long*)(p + c);
-  S.inc = (unsigned long long*)(p + c + a);
-  return S;
-}
-
-constexpr uint32_t kLookbackSpins = 1u << 22;  // x 64 ns: about a quarter of a second
-
-__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Called by all 32 lanes of one warp of the block that owns `tile`, with
-// the tile's sum; returns (to every lane) the sum of all earlier tiles and
-// publishes this tile's inclusive prefix.  Overflow beyond 64 bits and a
-// wait that gives up set bits in *err (kErrOverflow, kErrTimeout).
-__device__ __forceinline__ unsigned long long scan_lookback(const ScanState& S, uint32_t tile,
-                                                            unsigned long long tile_sum, uint32_t* err) {
-  const int lane = threadIdx.x & 31;
-  unsigned long long excl = 0;
-  if (tile == 0) {
-    if (lane == 0) {
-      S.inc[0] = tile_sum;
-      st_release_u32(S.flag, 2u);
-    }
-    return 0;
-  }
-  if (lane == 0) {
-    S.agg[tile] = tile_sum;
-    st_release_u32(S.flag + tile, 1u);
-  }
-  int64_t j = (int64_t)tile - 1;
-  uint32_t spins = 0;
-  for (;;) {
-    const int64_t idx = j - lane;
-    uint32_t f = 2u;  // before tile 0: an inclusive prefix of 0
-    unsigned long long v = 0;
-    if (idx >= 0) {
-      f = ld_acquire_u32(S.flag + idx);
-      if (f == 1u) v = ld_relaxed_u64(S.agg + idx);
-      else if (f == 2u) v = ld_relaxed_u64(S.inc + idx);
-    }
-    const unsigned inc_mask = __ballot_sync(0xffffffffu, f == 2u);
-    const unsigned zero_mask = __ballot_sync(0xffffffffu, f == 0u);
-    const int first = inc_mask ? __ffs(inc_mask) - 1 : 32;  // nearest inclusive prefix
-    const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
-    if (zero_mask & need) {
-      if (++spins > kLookbackSpins) {
-        *err |= kErrTimeout;
-        break;
-      }
-      __nanosleep(64);
-      continue;
-    }
-    unsigned __int128 sum = lane <= first ? v : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)sum, o);
-      const uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(sum >> 64), o);
-      sum += ((unsigned __int128)hi << 64) | lo;
-    }
-    if ((sum >> 64) || excl + (uint64_t)sum < excl) *err |= kErrOverflow;
-    excl += (uint64_t)sum;
-    if (first < 32) break;
-    j -= 32;
-  }
-  if (lane == 0) {
-    if (excl + tile_sum < excl) *err |= kErrOverflow;
-    S.inc[tile] = excl + tile_sum;
-    st_release_u32(S.flag + tile, 2u);
-  }
-  return excl;
-}
-
-// ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files).
 
 // Exclusive scans.  scan_u64 writes out[0..n] (out[n] = total) and sets
@@ -409,22 +301,28 @@ tc_status scan_u32_in_scratch(const uint32_t* in, uint32_t* out, uint64_t n, uin
                               uint64_t scratch_words, cudaStream_t st);
 tc_status scan_u64_in_scratch(const uint64_t* in, uint64_t* out, uint64_t n, bool write_total, uint32_t* d_err,
                               uint64_t* scratch, uint64_t scratch_words, cudaStream_t st);
+// The same scan when the kernel that wrote `in` also wrote the sums of its
+// tiles of scan_tile_size() values into sums[ceil(n / scan_tile_size())]
+// (scanned in place; scratch: scan_u64_scratch_words(tiles) words).
+uint64_t scan_tile_size();
+tc_status scan_u64_from_tile_sums(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* sums, uint32_t* d_err,
+                                  uint64_t* scratch, uint64_t scratch_words, cudaStream_t st);
 
 // Stable LSD radix sort of (key, val) pairs on key bits [bit0, bit1).  The
 // sorted data ends in (k0, v0); k1, v1 are scratch of the same size.
 tc_status radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint64_t n, int bit0,
                            int bit1, cudaStream_t st);
 
+inline size_t scan_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 tc_status launch_widen_u32(const uint32_t* in, uint64_t n, int64_t* out, cudaStream_t st);
 
 tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t* d_dst, const int64_t* d_t,
                       cudaStream_t st, tc_graph* g);
 
-// Path weights, their exact prefix sum and the windows in one pass over the
-// canonical edges (single-pass scan with decoupled look-back): prefix[m + 1],
-// win[m], and w[m] when w is not NULL.  scratch: weights_scan_scratch_bytes(m)
-// bytes (tile states; cleared here on the stream); *d_err collects overflow
-// and wait-timeout bits.
+// Path weights, their windows and their exact prefix sum: prefix[m + 1],
+// win[m], and w[m] when w is not NULL.  scratch:
+// weights_scan_scratch_bytes(m) bytes; *d_err collects overflow bits.
 size_t weights_scan_scratch_bytes(uint64_t m);
 tc_status launch_weights_scan(const tc_graph* g, const Plan& plan, int64_t delta, EdgeWin* win, uint64_t* prefix,
                               uint64_t* w, void* scratch, uint32_t* d_err, cudaStream_t st);
@@ -460,12 +358,12 @@ tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint6
 tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st,
                                bool clip = false);
 tc_status launch_clip_labels(const float* labels, uint64_t n, float* out, cudaStream_t st);
-// Proposal h, q = w h and the exact prefix of q in one pass (scratch:
-// proposal_scan_scratch_bytes(m) bytes, cleared here on the stream).
+// Proposal h, q = w h and the exact prefix of q (scratch:
+// proposal_scan_scratch_bytes(m) bytes).
 size_t proposal_scan_scratch_bytes(uint64_t m);
 tc_status launch_proposal_scan(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
-                               float scale, uint16_t* h, uint64_t* qprefix, void* scratch, uint32_t* d_err,
-                               cudaStream_t st);
+                               float scale, uint16_t* h, uint64_t* qprefix, uint32_t* hrange, void* scratch,
+                               uint32_t* d_err, cudaStream_t st);
 int guide_bits(uint64_t m);
 
 struct SampleSums {  // per-call device accumulator

@@ -346,29 +346,7 @@ __device__ __forceinline__ void tile_forward(const MlpShared& S, const uint32_t 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
 
 // Logits of rows (rows[i] or i) -> out[i].
-__global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ params,
-                                                     const __nv_bfloat16* __restrict__ feat,
-                                                     const uint32_t* __restrict__ rows, uint64_t n,
-                                                     float* __restrict__ out) {
-  __shared__ MlpShared S;
-  load_mlp_shared(S, params);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2;
-  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < n; tile += warps) {
-    const uint64_t ia = tile * 16 + g, ib = ia + 8;
-    const int64_t ra = ia < n ? (int64_t)(rows ? rows[ia] : ia) : -1;
-    const int64_t rb = ib < n ? (int64_t)(rows ? rows[ib] : ib) : -1;
-    uint32_t x[4];
-    load_rows(feat, ra, rb, x);
-    TileAct T;
-    tile_forward(S, x, T);
-    if ((lane & 3) == 0) {
-      if (ia < n) out[ia] = T.z3g;
-      if (ib < n) out[ib] = T.z3g8;
-    }
-  }
-}
+
 
 // Logits of one 16-row tile for rows g and g + 8 of the fragment layout: the
 // forward of tile_forward without keeping the pre-activations (inference).
@@ -393,89 +371,161 @@ __device__ __forceinline__ void load_mlp_fwd_shared(MlpFwdShared& S, const float
   if (threadIdx.x == 0) S.b3 = p[kOffB3];
 }
 
-__device__ __forceinline__ void tile_logits(const MlpFwdShared& S, const uint32_t (&x)[4], float* z3g, float* z3g8) {
+// ReLU of two FP32 values rounded to a bf16 pair (lo in the low half): one
+// instruction, the activations' rounding of the forward.
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// The network's B fragments held in registers for the whole kernel (the
+// weights are the same for every tile): layer 2 (8 output tiles x 4 k-tiles
+// x 2 registers) and layer 3 as an 8-column tile whose column 0 is W3 and
+// whose other columns are zero, so that the last layer is one more MMA
+// chain; layer 1 (K = 16) is read from shared memory.
+struct MlpFrags {
+  uint32_t w2[8][4][2];
+  uint32_t w3[4][2];
+  float b3;
+};
+
+__device__ __forceinline__ void load_mlp_frags(const MlpFwdShared& S, MlpFrags& F) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  uint32_t a1[4][4];  // layer 1, ReLU, bf16: the A fragments of layer 2
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int n = j * 8 + g;
+#pragma unroll
+    for (int kk = 0; kk < 4; kk++) {
+      F.w2[j][kk][0] = ld_pair(&S.W2[n * kW2S + kk * 16 + 2 * q]);
+      F.w2[j][kk][1] = ld_pair(&S.W2[n * kW2S + kk * 16 + 2 * q + 8]);
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; kk++) {  // B of layer 3: k = kk * 16 + 2q (+8), column n = g (only g = 0 is W3)
+    const int k0 = kk * 16 + 2 * q;
+    F.w3[kk][0] = g == 0 ? pack_bf16(S.W3[k0], S.W3[k0 + 1]) : 0u;
+    F.w3[kk][1] = g == 0 ? pack_bf16(S.W3[k0 + 8], S.W3[k0 + 9]) : 0u;
+  }
+  F.b3 = S.b3;
+}
+
+// Logits of one 16-row tile (rows g and g + 8 of the fragment layout; lanes
+// with q = 0 hold them): layer 1 on the tensor cores from shared-memory W1,
+// ReLU and bf16 rounding packed straight into the A fragments of the next
+// layer, layer 2 and layer 3 from the register fragments.
+__device__ __forceinline__ void tile_logits(const MlpFwdShared& S, const MlpFrags& F, const uint32_t (&x)[4],
+                                            float* z3g, float* z3g8) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  uint32_t a1[4][4];
 #pragma unroll
   for (int j = 0; j < 8; j++) {
     const int n = j * 8 + g;
     float c[4] = {S.b1[j * 8 + 2 * q], S.b1[j * 8 + 2 * q + 1], S.b1[j * 8 + 2 * q], S.b1[j * 8 + 2 * q + 1]};
     mma_bf16(c, x, ld_pair(&S.W1[n * kW1S + 2 * q]), ld_pair(&S.W1[n * kW1S + 2 * q + 8]));
-    const int kk = j >> 1;
-    if ((j & 1) == 0) {
-      a1[kk][0] = pack_bf16(fmaxf(c[0], 0.f), fmaxf(c[1], 0.f));
-      a1[kk][1] = pack_bf16(fmaxf(c[2], 0.f), fmaxf(c[3], 0.f));
-    } else {
-      a1[kk][2] = pack_bf16(fmaxf(c[0], 0.f), fmaxf(c[1], 0.f));
-      a1[kk][3] = pack_bf16(fmaxf(c[2], 0.f), fmaxf(c[3], 0.f));
-    }
+    const int kk = j >> 1, hi = (j & 1) * 2;
+    a1[kk][hi] = relu_bf16x2(c[0], c[1]);
+    a1[kk][hi + 1] = relu_bf16x2(c[2], c[3]);
   }
-  float sg = 0.f, sg8 = 0.f;  // layer 2, then layer 3 in FP32 on the bf16-rounded activations
+  uint32_t a2[4][4];
 #pragma unroll
   for (int j = 0; j < 8; j++) {
-    const int n = j * 8 + g;
     float c[4] = {S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1], S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1]};
 #pragma unroll
-    for (int kk = 0; kk < 4; kk++)
-      mma_bf16(c, a1[kk], ld_pair(&S.W2[n * kW2S + kk * 16 + 2 * q]), ld_pair(&S.W2[n * kW2S + kk * 16 + 2 * q + 8]));
-    const int n0 = j * 8 + 2 * q;
-    sg += __bfloat162float(__float2bfloat16_rn(fmaxf(c[0], 0.f))) * S.W3[n0] +
-          __bfloat162float(__float2bfloat16_rn(fmaxf(c[1], 0.f))) * S.W3[n0 + 1];
-    sg8 += __bfloat162float(__float2bfloat16_rn(fmaxf(c[2], 0.f))) * S.W3[n0] +
-           __bfloat162float(__float2bfloat16_rn(fmaxf(c[3], 0.f))) * S.W3[n0 + 1];
+    for (int kk = 0; kk < 4; kk++) mma_bf16(c, a1[kk], F.w2[j][kk][0], F.w2[j][kk][1]);
+    const int kk = j >> 1, hi = (j & 1) * 2;
+    a2[kk][hi] = relu_bf16x2(c[0], c[1]);
+    a2[kk][hi + 1] = relu_bf16x2(c[2], c[3]);
   }
-  sg += __shfl_xor_sync(0xffffffffu, sg, 1);
-  sg += __shfl_xor_sync(0xffffffffu, sg, 2);
-  sg8 += __shfl_xor_sync(0xffffffffu, sg8, 1);
-  sg8 += __shfl_xor_sync(0xffffffffu, sg8, 2);
-  *z3g = sg + S.b3;
-  *z3g8 = sg8 + S.b3;
+  float c3[4] = {F.b3, F.b3, F.b3, F.b3};
+#pragma unroll
+  for (int kk = 0; kk < 4; kk++) mma_bf16(c3, a2[kk], F.w3[kk][0], F.w3[kk][1]);
+  *z3g = c3[0];   // column 0, row g (lanes q = 0)
+  *z3g8 = c3[2];  // column 0, row g + 8
 }
 
-// Proposal with its exact prefix in one pass: for every canonical edge e,
-// h_e = max(1, floor(scale (eps + g_e) + 1/2)) with g_e = sigmoid(network
-// logit of e's feature row), q_e = w_e h_e with w_e = prefix[e + 1] -
-// prefix[e], and qprefix[e + 1] = q_0 + ... + q_e.  Persistent blocks (the
-// network is staged in shared memory once per block) take tiles of kPTile
-// edges from a counter; each warp runs its 16-row sub-tiles on the tensor
-// cores with the next sub-tile's feature fragments loaded ahead; h and q go
-// through shared memory, so the global writes are coalesced; the tiles'
-// prefix sums are chained by the decoupled look-back.
-constexpr int kPThreads = 256;
-constexpr int kPRowsPerWarp = 128;
-constexpr int kPTile = (kPThreads / 32) * kPRowsPerWarp;  // 1024 edges
-constexpr int kPItems = kPTile / kPThreads;              // 4 per thread in the scan
+// Logits of rows (rows[i] or i) -> out[i], with the inference path of the
+// proposal (tile_logits).
+__global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ params,
+                                                     const __nv_bfloat16* __restrict__ feat,
+                                                     const uint32_t* __restrict__ rows, uint64_t n,
+                                                     float* __restrict__ out) {
+  __shared__ MlpFwdShared S;
+  load_mlp_fwd_shared(S, params);
+  __syncthreads();
+  MlpFrags F;
+  load_mlp_frags(S, F);
+  const int lane = threadIdx.x & 31, g = lane >> 2;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t tile = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < n; tile += warps) {
+    const uint64_t ia = tile * 16 + g, ib = ia + 8;
+    const int64_t ra = ia < n ? (int64_t)(rows ? rows[ia] : ia) : -1;
+    const int64_t rb = ib < n ? (int64_t)(rows ? rows[ib] : ib) : -1;
+    uint32_t x[4];
+    load_rows(feat, ra, rb, x);
+    float za, zb;
+    tile_logits(S, F, x, &za, &zb);
+    if ((lane & 3) == 0) {
+      if (ia < n) out[ia] = za;
+      if (ib < n) out[ib] = zb;
+    }
+  }
+}
 
-__global__ void __launch_bounds__(kPThreads, 3) k_proposal_scan(const float* __restrict__ params,
-                                                                const __nv_bfloat16* __restrict__ feat,
-                                                                const uint64_t* __restrict__ prefix, uint64_t m,
-                                                                float eps, float scale, uint16_t* __restrict__ h,
-                                                                uint64_t* __restrict__ qprefix, ScanState S,
-                                                                uint32_t* __restrict__ d_err) {
+// Proposal: for every canonical edge e, h_e = max(1, floor(scale (eps +
+// g_e) + 1/2)) with g_e = sigmoid(network logit of e's feature row), and
+// q_e = w_e h_e with w_e = prefix[e + 1] - prefix[e]; each tile's sum of q
+// is the first level of the reduce-then-scan that writes the q-prefix.
+// Persistent blocks (the network is staged in shared memory and its
+// fragments in registers once per block) take tiles of kPTile edges in
+// turn; each warp runs its 16-row sub-tiles on the tensor cores with the
+// next sub-tile's feature fragments loaded ahead, while the tile's prefix
+// entries arrive in shared memory by cp.async; h and q are then formed and
+// written coalesced.
+constexpr int kPThreads = 128;
+constexpr int kPRowsPerWarp = 512;
+constexpr int kPTile = (kPThreads / 32) * kPRowsPerWarp;  // 2048 edges: the scan's tile
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Blocks per SM the proposal kernel is compiled for (caps its registers; the
+// network's fragments take about 80 of them).
+#ifndef TC_PROPOSAL_MIN_BLOCKS
+#define TC_PROPOSAL_MIN_BLOCKS 3
+#endif
+
+__global__ void __launch_bounds__(kPThreads, TC_PROPOSAL_MIN_BLOCKS) k_proposal(const float* __restrict__ params,
+                                                                              const __nv_bfloat16* __restrict__ feat,
+                                                                              const uint64_t* __restrict__ prefix,
+                                                                              uint64_t m, float eps, float scale,
+                                                                              uint16_t* __restrict__ h,
+                                                                              uint64_t* __restrict__ q,
+                                                                              uint64_t* __restrict__ tile_sums,
+                                                                              uint32_t* __restrict__ hrange,
+                                                                              uint32_t* __restrict__ d_err) {
   __shared__ MlpFwdShared net;
   __shared__ unsigned long long s_pre[kPTile + 1];
-  __shared__ unsigned long long s_q[kPTile + kPTile / 8];
-  __shared__ uint16_t s_h[kPTile];
+  __shared__ float s_z[kPTile];
   __shared__ unsigned long long s_warp[kPThreads / 32];
-  __shared__ unsigned long long s_excl;
-  __shared__ uint32_t s_tile, s_err;
+  __shared__ uint32_t s_err;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, g = lane >> 2, qd = lane & 3;
   load_mlp_fwd_shared(net, params);
   if (tid == 0) s_err = 0;
-  auto pad = [](uint32_t i) { return i + (i >> 3); };
+  __syncthreads();
+  MlpFrags F;
+  load_mlp_frags(net, F);
   const uint64_t T = (m + kPTile - 1) / kPTile;
-  uint32_t err = 0;
-  for (;;) {
-    __syncthreads();  // the previous tile's shared arrays are consumed
-    if (tid == 0) s_tile = atomicAdd(S.counter, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    if (tile >= T) break;
-    const uint64_t base = (uint64_t)tile * kPTile;
+  uint32_t err = 0, hlo = 0xFFFFFFFFu, hhi = 0;
+  for (uint64_t tile = blockIdx.x; tile < T; tile += gridDim.x) {
+    const uint64_t base = tile * kPTile;
     const uint32_t rows = (uint32_t)(m - base < (uint64_t)kPTile ? m - base : (uint64_t)kPTile);
-    for (uint32_t i = tid; i <= rows; i += kPThreads) s_pre[i] = __ldg(prefix + base + i);
-    __syncthreads();
-    // 1. logits, h and q of the warp's rows
+    __syncthreads();  // the previous tile's shared arrays are consumed
+    for (uint32_t i = tid; i <= rows; i += kPThreads) cp_async8(s_pre + i, prefix + base + i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
     const uint32_t r0 = (uint32_t)wid * kPRowsPerWarp;
     auto fetch = [&](uint32_t sub, uint32_t (&x)[4]) {
       const uint32_t ra = r0 + sub * 16 + g, rb = ra + 8;
@@ -488,72 +538,54 @@ __global__ void __launch_bounds__(kPThreads, 3) k_proposal_scan(const float* __r
       uint32_t x[4] = {xn[0], xn[1], xn[2], xn[3]};
       if (sub + 1 < kPRowsPerWarp / 16) fetch(sub + 1, xn);
       float za, zb;
-      tile_logits(net, x, &za, &zb);
+      tile_logits(net, F, x, &za, &zb);
       if (qd == 0) {
-#pragma unroll
-        for (int rr = 0; rr < 2; rr++) {
-          const uint32_t r = r0 + sub * 16 + g + 8 * rr;
-          uint16_t hv16 = 0;
-          unsigned long long qv = 0;
-          if (r < rows) {
-            const float v = floorf(scale * (eps + sigmoidf_(rr ? zb : za)) + 0.5f);
-            const uint32_t hv = v < 1.f ? 1u : (uint32_t)v;
-            const unsigned long long wv = s_pre[r + 1] - s_pre[r];
-            if (__umul64hi(wv, hv)) err |= kErrOverflow;
-            qv = wv * hv;
-            hv16 = (uint16_t)hv;
-          }
-          s_h[r] = hv16;
-          s_q[pad(r)] = qv;
-        }
+        s_z[r0 + sub * 16 + g] = za;
+        s_z[r0 + sub * 16 + g + 8] = zb;
       }
     }
+    cp_async_wait_all();
     __syncthreads();
-    // 2. inclusive scan of q over the tile: kPItems consecutive per thread
-    unsigned long long run = 0;
-#pragma unroll
-    for (int k = 0; k < kPItems; k++) {
-      const uint32_t i = pad((uint32_t)tid * kPItems + k);
-      const unsigned long long nv = run + s_q[i];
-      if (nv < run) err |= kErrOverflow;
-      run = nv;
-      s_q[i] = run;
+    unsigned long long sum = 0;
+    for (uint32_t r = tid; r < rows; r += kPThreads) {
+      const float v = floorf(scale * (eps + sigmoidf_(s_z[r])) + 0.5f);
+      const uint32_t hv = v < 1.f ? 1u : (uint32_t)v;
+      const unsigned long long wv = s_pre[r + 1] - s_pre[r];
+      if (__umul64hi(wv, hv)) err |= kErrOverflow;
+      const unsigned long long qv = wv * hv;
+      q[base + r] = qv;
+      h[base + r] = (uint16_t)hv;
+      if (sum + qv < sum) err |= kErrOverflow;
+      sum += qv;
+      hlo = hv < hlo ? hv : hlo;
+      hhi = hv > hhi ? hv : hhi;
     }
-    unsigned long long incl = run;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) {
-        if (incl + y < incl) err |= kErrOverflow;
-        incl += y;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, sum, o);
+      if (sum + y < sum) err |= kErrOverflow;
+      sum += y;
+    }
+    if (lane == 0) s_warp[wid] = sum;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long t = 0;
+      for (int v = 0; v < kPThreads / 32; v++) {
+        if (t + s_warp[v] < t) err |= kErrOverflow;
+        t += s_warp[v];
       }
+      tile_sums[tile] = t;
     }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    unsigned long long before = 0;
-    for (int v = 0; v < wid; v++) {
-      if (before + s_warp[v] < before) err |= kErrOverflow;
-      before += s_warp[v];
-    }
-    if (before + incl < before) err |= kErrOverflow;
-    unsigned long long tile_sum = 0;
-    for (int v = 0; v < kPThreads / 32; v++) tile_sum += s_warp[v];
-    const unsigned long long thread_excl = before + incl - run;
+  }
+  // the proposal's range of h, for the sampler's per-block bins
 #pragma unroll
-    for (int k = 0; k < kPItems; k++) s_q[pad((uint32_t)tid * kPItems + k)] += thread_excl;
-    // 3. the tile's exclusive prefix (warp 0)
-    if (wid == 0) {
-      const unsigned long long excl = scan_lookback(S, tile, tile_sum, &err);
-      if (lane == 0) s_excl = excl;
-    }
-    __syncthreads();
-    // 4. coalesced writes
-    const unsigned long long tex = s_excl;
-    for (uint32_t i = tid; i < rows; i += kPThreads) {
-      qprefix[base + i + 1] = tex + s_q[pad(i)];
-      h[base + i] = s_h[i];
-    }
-    if (tile == 0 && tid == 0) qprefix[0] = 0;
+  for (int o = 16; o > 0; o >>= 1) {
+    hlo = min(hlo, __shfl_xor_sync(0xffffffffu, hlo, o));
+    hhi = max(hhi, __shfl_xor_sync(0xffffffffu, hhi, o));
+  }
+  if (lane == 0 && hhi) {
+    atomicMin(hrange, hlo);
+    atomicMax(hrange + 1, hhi);
   }
   if (err) atomicOr(&s_err, err);
   __syncthreads();
@@ -980,31 +1012,39 @@ tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows
   return TC_OK;
 }
 
-size_t proposal_scan_scratch_bytes(uint64_t m) { return scan_state_bytes((m + kPTile - 1) / kPTile); }
+// Scratch of launch_proposal_scan: q, the tile sums of q and their scan levels.
+size_t proposal_scan_scratch_bytes(uint64_t m) {
+  const uint64_t T = (m + kPTile - 1) / kPTile ? (m + kPTile - 1) / kPTile : 1;
+  return scan_align256(8 * (m ? m : 1)) + scan_align256(8 * T) + scan_align256(8 * (scan_u64_scratch_words(T) + 1));
+}
 
 tc_status launch_proposal_scan(const tc_mlp* M, const uint16_t* feat, const uint64_t* prefix, uint64_t m, float eps,
-                               float scale, uint16_t* h, uint64_t* qprefix, void* scratch, uint32_t* d_err,
-                               cudaStream_t st) {
+                               float scale, uint16_t* h, uint64_t* qprefix, uint32_t* hrange, void* scratch,
+                               uint32_t* d_err, cudaStream_t st) {
+  TC_CUDA(cudaMemsetAsync(hrange, 0xFF, sizeof(uint32_t), st));  // smallest h: none yet
+  TC_CUDA(cudaMemsetAsync(hrange + 1, 0, sizeof(uint32_t), st));  // largest h: none yet
   if (!m) {
     TC_CUDA(cudaMemsetAsync(qprefix, 0, sizeof(uint64_t), st));
     return TC_OK;
   }
+  if (scan_tile_size() != (uint64_t)kPTile) return set_error(TC_ERR_INVALID_ARG, "scan tile mismatch");
   const uint64_t T = (m + kPTile - 1) / kPTile;
-  if (T > 0xFFFFFFFFull) return set_error(TC_ERR_INVALID_ARG, "too many edges for the proposal scan");
-  TC_CUDA(cudaMemsetAsync(scratch, 0, scan_state_clear_bytes(T), st));
+  char* p = (char*)scratch;
+  uint64_t* q = (uint64_t*)p;
+  uint64_t* sums = (uint64_t*)(p + scan_align256(8 * m));
+  uint64_t* scan_scratch = (uint64_t*)(p + scan_align256(8 * m) + scan_align256(8 * T));
   static int bps = 0;
   if (!bps) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_proposal_scan, kPThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_proposal, kPThreads, 0);
     if (bps <= 0) bps = 1;
   }
   uint64_t blocks = (uint64_t)num_sms() * bps;
   if (blocks > T) blocks = T;
-  k_proposal_scan<<<(unsigned)blocks, kPThreads, 0, st>>>(M->params, reinterpret_cast<const __nv_bfloat16*>(feat),
-                                                          prefix, m, eps, scale, h, qprefix,
-                                                          scan_state_view(scratch, T), d_err);
+  k_proposal<<<(unsigned)blocks, kPThreads, 0, st>>>(M->params, reinterpret_cast<const __nv_bfloat16*>(feat), prefix,
+                                                     m, eps, scale, h, q, sums, hrange, d_err);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
-  return TC_OK;
+  return scan_u64_from_tile_sums(q, qprefix, m, sums, d_err, scan_scratch, scan_u64_scratch_words(T) + 1, st);
 }
 
 }  // namespace tc

@@ -13,7 +13,7 @@ namespace tc {
 // ---------------------------------------------------------------------------
 // Weights (Claim 1, Alg. 1): w_e = d1 * d3 for every canonical edge
 // e = (u, v, t), the sizes of the window of u's alpha1 list and of v's alpha3
-// list, with their exact prefix sum, in one pass over the canonical order.
+// list, and their exact prefix sum.
 //
 // The four binary searches per edge of Alg. 1 start from anchors built with
 // the lists (tc_graph::x_in, x_out, out2in; independent of delta): each
@@ -23,12 +23,9 @@ namespace tc {
 // probes over the whole list.  The u side of consecutive edges (one source
 // vertex in time order) searches the same list at increasing positions.
 //
-// The prefix sum is the single-pass scan with decoupled look-back (Merrill &
-// Garland, 2016): each block takes the next tile of kWTile edges from a
-// counter (so every earlier tile belongs to a block that already runs),
-// publishes its tile sum, then adds the sums of the tiles before it until
-// it meets one whose inclusive prefix is published.  The waits on
-// predecessors are bounded; a wait that gives up sets kErrTimeout.
+// The weights pass also sums w over each tile of kWTile edges, the first
+// level of the reduce-then-scan that writes the prefix (so w is read once
+// more, not twice).
 //
 // A wedge anchor (3-vertex motif) has one window, at u or at v; the other
 // side is the dummy [0, 1), so w_e is the size of that window.
@@ -45,12 +42,15 @@ namespace tc {
 
 // Resident blocks per SM the weights kernel is compiled for (caps its registers).
 #ifndef TC_WEIGHTS_MIN_BLOCKS
-#define TC_WEIGHTS_MIN_BLOCKS 6
+#define TC_WEIGHTS_MIN_BLOCKS 8
 #endif
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int kWThreads = 256;
 constexpr int kWItems = 8;
-constexpr int kWTile = kWThreads * kWItems;  // edges per tile
+constexpr int kWTile = kWThreads * kWItems;  // edges per tile: the scan's tile
+
 // First position p in [s, f) whose time is >= x (Gt: > x), searched from a
 // position a in [s, f]: doubling steps away from a until the answer is
 // bracketed, then bisection.  At most 2 log2(f - s) + 2 probes.
@@ -125,9 +125,8 @@ struct WeightsArgs {
   int64_t delta;
   int alpha1, alpha3, beta1, beta3, closed;
   EdgeWin* win;
-  uint64_t* prefix;
-  uint64_t* w;  // optional
-  ScanState scan;  // tile states of the prefix sum
+  uint64_t* w;
+  uint64_t* tile_sums;  // sum of w over each tile
   uint32_t* err;
 };
 
@@ -145,230 +144,88 @@ __device__ __forceinline__ void side_window(const WeightsArgs& A, int alpha, int
   }
 }
 
-// Fused: the tile scan and look-back follow in the same kernel; otherwise
-// the kernel writes w (A.w) and the windows only, block b taking tile b.
-template <bool Compact, bool Fused>
-__global__ void __launch_bounds__(kWThreads, TC_WEIGHTS_MIN_BLOCKS) k_weights_scan(const __grid_constant__ WeightsArgs A) {
-  __shared__ unsigned long long s_w[Fused ? kWTile + kWTile / 8 : 1];  // one pad word per 8: conflict-free rows
+// Block b takes tile b: the windows and w of its kWTile edges (coalesced:
+// edge b kWTile + j 256 + thread), and the tile's sum of w.
+template <bool Compact>
+__global__ void __launch_bounds__(kWThreads, TC_WEIGHTS_MIN_BLOCKS) k_weights(const __grid_constant__ WeightsArgs A) {
   __shared__ unsigned long long s_warp[kWThreads / 32];
-  __shared__ unsigned long long s_excl;
-  __shared__ uint32_t s_tile, s_err;
+  __shared__ uint32_t s_ovf;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  if (Fused) {
-    if (tid == 0) {
-      s_tile = atomicAdd(A.scan.counter, 1u);
-      s_err = 0;
-    }
-    __syncthreads();
-  }
-  const uint32_t tile = Fused ? s_tile : blockIdx.x;
-  const uint64_t base = (uint64_t)tile * kWTile;
-  auto pad = [](uint32_t q) { return q + (q >> 3); };
-  uint32_t err = 0;
-  // 1. windows and weights of the tile's edges (coalesced: edge base + j * 256 + tid)
+  if (tid == 0) s_ovf = 0;
+  const uint64_t base = (uint64_t)blockIdx.x * kWTile;
+  unsigned long long sum = 0;
+  bool ovf = false;
 #pragma unroll 1
   for (int j = 0; j < kWItems; j++) {
-    const uint32_t q = (uint32_t)j * kWThreads + tid;
-    const uint64_t i = base + q;
-    unsigned long long wv = 0;
-    if (i < A.m) {
-      const OutEdge e = A.out_e[i];
-      uint32_t lo1 = 0, hi1 = 1, lo3 = 0, hi3 = 1;  // a wedge's unused side is [0, 1)
-      if (A.alpha1 != 0)
-        side_window<Compact>(A, A.alpha1, A.beta1, e.src, A.alpha1 < 0 ? __ldg(A.x_in + i) : (uint32_t)i, e.t, &lo1,
-                             &hi1);
-      if (A.alpha3 != 0)
-        side_window<Compact>(A, A.alpha3, A.beta3, e.dst, A.alpha3 < 0 ? __ldg(A.out2in + i) : __ldg(A.x_out + i),
-                             e.t, &lo3, &hi3);
-      EdgeWin r;
-      r.lo1 = lo1;
-      r.d1 = hi1 - lo1;
-      r.lo3 = lo3;
-      r.d3 = hi3 - lo3;
-      A.win[i] = r;
-      wv = (unsigned long long)r.d1 * (unsigned long long)r.d3;
-      if (A.w) A.w[i] = wv;
-    }
-    if (Fused) s_w[pad(q)] = wv;
+    const uint64_t i = base + (uint64_t)j * kWThreads + tid;
+    if (i >= A.m) break;
+    const OutEdge e = A.out_e[i];
+    uint32_t lo1 = 0, hi1 = 1, lo3 = 0, hi3 = 1;  // a wedge's unused side is [0, 1)
+    // anchors: u's in-list (x_in) or the edge itself in u's out-list; the
+    // edge itself in v's in-list (out2in) or v's out-list (x_out)
+    if (A.alpha1 != 0)
+      side_window<Compact>(A, A.alpha1, A.beta1, e.src, A.alpha1 < 0 ? __ldg(A.x_in + i) : (uint32_t)i, e.t, &lo1,
+                           &hi1);
+    if (A.alpha3 != 0)
+      side_window<Compact>(A, A.alpha3, A.beta3, e.dst, A.alpha3 < 0 ? __ldg(A.out2in + i) : __ldg(A.x_out + i), e.t,
+                           &lo3, &hi3);
+    EdgeWin r;
+    r.lo1 = lo1;
+    r.d1 = hi1 - lo1;
+    r.lo3 = lo3;
+    r.d3 = hi3 - lo3;
+    A.win[i] = r;
+    const unsigned long long wv = (unsigned long long)r.d1 * (unsigned long long)r.d3;
+    A.w[i] = wv;
+    if (sum + wv < sum) ovf = true;
+    sum += wv;
   }
-  if (!Fused) return;
-  __syncthreads();
-  // 2. inclusive scan of the tile: each thread its 8 consecutive edges, then
-  // the 256 thread sums
-  unsigned long long run = 0;
 #pragma unroll
-  for (int k = 0; k < kWItems; k++) {
-    const uint32_t q = pad((uint32_t)tid * kWItems + k);
-    const unsigned long long nv = run + s_w[q];
-    if (nv < run) err |= kErrOverflow;
-    run = nv;
-    s_w[q] = run;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, sum, o);
+    if (sum + y < sum) ovf = true;
+    sum += y;
   }
-  unsigned long long incl = run;  // warp-inclusive scan of the thread sums
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) {
-      if (incl + y < incl) err |= kErrOverflow;
-      incl += y;
-    }
-  }
-  if (lane == 31) s_warp[wid] = incl;
+  if (lane == 0) s_warp[wid] = sum;
+  if (ovf) s_ovf = 1;
   __syncthreads();
-  unsigned long long before = 0;
-  for (int v = 0; v < wid; v++) {
-    if (before + s_warp[v] < before) err |= kErrOverflow;
-    before += s_warp[v];
-  }
-  if (before + incl < before) err |= kErrOverflow;  // the tile sum is the last thread's before + incl
-  unsigned long long tile_sum = 0;
-  for (int v = 0; v < kWThreads / 32; v++) tile_sum += s_warp[v];
-  const unsigned long long thread_excl = before + incl - run;
-  // 3. the tile's exclusive prefix from its predecessors (warp 0)
-  if (wid == 0) {
-    const unsigned long long excl = scan_lookback(A.scan, tile, tile_sum, &err);
-    if (lane == 0) s_excl = excl;
-  }
-  if (err) atomicOr(&s_err, err);
-  __syncthreads();
-  // 4. prefix[i + 1] = tile prefix + inclusive sum within the tile
-  const unsigned long long tex = s_excl;
-#pragma unroll
-  for (int k = 0; k < kWItems; k++) {
-    const uint32_t q = pad((uint32_t)tid * kWItems + k);
-    s_w[q] += thread_excl;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < kWItems; j++) {
-    const uint32_t q = (uint32_t)j * kWThreads + tid;
-    const uint64_t i = base + q;
-    if (i < A.m) A.prefix[i + 1] = tex + s_w[pad(q)];
-  }
-  if (tile == 0 && tid == 0) A.prefix[0] = 0;
-  if (tid == 0 && s_err) atomicOr(A.err, s_err);
-}
-
-// Exclusive prefix of n uint64 in one pass (out[0] = 0, out[i + 1] = in[0]
-// + ... + in[i]; in and out distinct): tiles of kWTile values, coalesced
-// through shared memory, chained by the decoupled look-back.
-__global__ void __launch_bounds__(kWThreads) k_scan_lookback(const uint64_t* __restrict__ in, uint64_t n,
-                                                             uint64_t* __restrict__ out, ScanState S,
-                                                             uint32_t* __restrict__ d_err) {
-  __shared__ unsigned long long s_w[kWTile + kWTile / 8];
-  __shared__ unsigned long long s_warp[kWThreads / 32];
-  __shared__ unsigned long long s_excl;
-  __shared__ uint32_t s_tile, s_err;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) {
-    s_tile = atomicAdd(S.counter, 1u);
-    s_err = 0;
-  }
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * kWTile;
-  auto pad = [](uint32_t q) { return q + (q >> 3); };
-  uint32_t err = 0;
-#pragma unroll
-  for (int j = 0; j < kWItems; j++) {
-    const uint32_t q = (uint32_t)j * kWThreads + tid;
-    const uint64_t i = base + q;
-    s_w[pad(q)] = i < n ? __ldg(in + i) : 0ull;
-  }
-  __syncthreads();
-  unsigned long long run = 0;
-#pragma unroll
-  for (int k = 0; k < kWItems; k++) {
-    const uint32_t q = pad((uint32_t)tid * kWItems + k);
-    const unsigned long long nv = run + s_w[q];
-    if (nv < run) err |= kErrOverflow;
-    run = nv;
-    s_w[q] = run;
-  }
-  unsigned long long incl = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) {
-      if (incl + y < incl) err |= kErrOverflow;
-      incl += y;
+    unsigned long long t = 0;
+    bool o2 = s_ovf != 0;
+    for (int v = 0; v < kWThreads / 32; v++) {
+      if (t + s_warp[v] < t) o2 = true;
+      t += s_warp[v];
     }
+    A.tile_sums[blockIdx.x] = t;
+    if (o2) atomicOr(A.err, kErrOverflow);
   }
-  if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
-  unsigned long long before = 0;
-  for (int v = 0; v < wid; v++) {
-    if (before + s_warp[v] < before) err |= kErrOverflow;
-    before += s_warp[v];
-  }
-  if (before + incl < before) err |= kErrOverflow;
-  unsigned long long tile_sum = 0;
-  for (int v = 0; v < kWThreads / 32; v++) tile_sum += s_warp[v];
-  const unsigned long long thread_excl = before + incl - run;
-  if (wid == 0) {
-    const unsigned long long excl = scan_lookback(S, tile, tile_sum, &err);
-    if (lane == 0) s_excl = excl;
-  }
-  if (err) atomicOr(&s_err, err);
-#pragma unroll
-  for (int k = 0; k < kWItems; k++) s_w[pad((uint32_t)tid * kWItems + k)] += thread_excl;
-  __syncthreads();
-  const unsigned long long tex = s_excl;
-#pragma unroll
-  for (int j = 0; j < kWItems; j++) {
-    const uint32_t q = (uint32_t)j * kWThreads + tid;
-    const uint64_t i = base + q;
-    if (i < n) out[i + 1] = tex + s_w[pad(q)];
-  }
-  if (tile == 0 && tid == 0) out[0] = 0;
-  if (tid == 0 && s_err) atomicOr(d_err, s_err);
 }
-
-// The weights and the prefix as one fused pass (each block waits on the sums
-// of the blocks before it) or as two: the windows and w, then the
-// single-pass scan of w (whose tiles cost the same, so their waits are
-// short while the windows' cost varies with the degrees).
-#ifndef TC_WEIGHTS_FUSED_SCAN
-#define TC_WEIGHTS_FUSED_SCAN 0
-#endif
 
 static uint64_t weights_tiles(uint64_t m) { return (m + kWTile - 1) / kWTile; }
 
+// Scratch of launch_weights_scan: w (unless the caller keeps it), the tile
+// sums, and the tile sums' own scan levels.
 size_t weights_scan_scratch_bytes(uint64_t m) {
-  return scan_state_bytes(weights_tiles(m)) + (TC_WEIGHTS_FUSED_SCAN ? 0 : scan_align256(8 * (m ? m : 1)));
-}
-
-tc_status launch_scan_lookback(const uint64_t* in, uint64_t n, uint64_t* out, void* scratch, uint32_t* d_err,
-                               cudaStream_t st) {
-  if (n == 0) {
-    TC_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
-    return TC_OK;
-  }
-  const uint64_t T = weights_tiles(n);
-  if (T > 0xFFFFFFFFull) return set_error(TC_ERR_INVALID_ARG, "too many values for the scan");
-  TC_CUDA(cudaMemsetAsync(scratch, 0, scan_state_clear_bytes(T), st));
-  k_scan_lookback<<<(unsigned)T, kWThreads, 0, st>>>(in, n, out, scan_state_view(scratch, T), d_err);
-  TC_LAUNCHED(1);
-  TC_CUDA(cudaGetLastError());
-  return TC_OK;
+  const uint64_t T = weights_tiles(m) ? weights_tiles(m) : 1;
+  return align256(8 * (m ? m : 1)) + align256(8 * T) + align256(8 * (scan_u64_scratch_words(T) + 1));
 }
 
 tc_status launch_weights_scan(const tc_graph* g, const Plan& plan, int64_t delta, EdgeWin* win, uint64_t* prefix,
                               uint64_t* w, void* scratch, uint32_t* d_err, cudaStream_t st) {
+  static_assert(kWTile == 2048, "the weights tiles are the scan's tiles");
   const uint64_t m = (uint64_t)g->m;
   if (m == 0) {
     TC_CUDA(cudaMemsetAsync(prefix, 0, sizeof(uint64_t), st));
     return TC_OK;
   }
+  if (scan_tile_size() != (uint64_t)kWTile) return set_error(TC_ERR_INVALID_ARG, "scan tile mismatch");
   const uint64_t T = weights_tiles(m);
-  if (T > 0xFFFFFFFFull) return set_error(TC_ERR_INVALID_ARG, "too many edges for the weights scan");
+  if (T > 0x7FFFFFFFull) return set_error(TC_ERR_INVALID_ARG, "too many edges for the weights pass");
+  char* p = (char*)scratch;
+  uint64_t* wbuf = w ? w : (uint64_t*)p;
+  uint64_t* sums = (uint64_t*)(p + align256(8 * m));
+  uint64_t* scan_scratch = (uint64_t*)(p + align256(8 * m) + align256(8 * T));
   WeightsArgs A;
-  A.scan = scan_state_view(scratch, T);
-  const bool fused = TC_WEIGHTS_FUSED_SCAN;
-  // the counter and the tile flags start at zero (the sums are written before their flags)
-  if (fused) TC_CUDA(cudaMemsetAsync(scratch, 0, scan_state_clear_bytes(T), st));
-  uint64_t* wbuf = w ? w : (uint64_t*)((char*)scratch + scan_state_bytes(T));
-  const bool compact = TC_COMPACT_TIMES && g->out_t32 && g->in_t32;
   A.out_e = g->out_e;
   A.in_e = g->in_e;
   A.out_off = g->out_off;
@@ -387,25 +244,17 @@ tc_status launch_weights_scan(const tc_graph* g, const Plan& plan, int64_t delta
   A.beta3 = plan.beta3;
   A.closed = plan.closed;
   A.win = win;
-  A.prefix = prefix;
-  A.w = fused ? w : wbuf;
+  A.w = wbuf;
+  A.tile_sums = sums;
   A.err = d_err;
-  if (fused) {
-    if (compact)
-      k_weights_scan<true, true><<<(unsigned)T, kWThreads, 0, st>>>(A);
-    else
-      k_weights_scan<false, true><<<(unsigned)T, kWThreads, 0, st>>>(A);
-    TC_LAUNCHED(1);
-    TC_CUDA(cudaGetLastError());
-    return TC_OK;
-  }
+  const bool compact = TC_COMPACT_TIMES && g->out_t32 && g->in_t32;
   if (compact)
-    k_weights_scan<true, false><<<(unsigned)T, kWThreads, 0, st>>>(A);
+    k_weights<true><<<(unsigned)T, kWThreads, 0, st>>>(A);
   else
-    k_weights_scan<false, false><<<(unsigned)T, kWThreads, 0, st>>>(A);
+    k_weights<false><<<(unsigned)T, kWThreads, 0, st>>>(A);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
-  return launch_scan_lookback(wbuf, m, prefix, scratch, d_err, st);
+  return scan_u64_from_tile_sums(wbuf, prefix, m, sums, d_err, scan_scratch, scan_u64_scratch_words(T) + 1, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,7 +266,6 @@ int guide_bits(uint64_t m) {
   return b;
 }
 
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t index_bytes(uint64_t m) {
   return kIndexHeaderBytes + align256(sizeof(EdgeWin) * m) + sizeof(uint32_t) * ((1ull << guide_bits(m)) + 1);
@@ -564,8 +412,30 @@ struct SamplerArgs {
   // index (win, rec_hdr), and each hit adds X and X^2 to bins[3 h + 0..2]
   const uint16_t* h;
   unsigned long long* bins;
+  const uint32_t* hrange;  // proposal: smallest and largest h (in the proposal index header)
   const IndexHeader* rec_hdr;
 };
+
+// Two bisections of [s, e) at once: *a = the first position with time > xa,
+// *b = the first with time > xb (incl) or >= xb; one probe of each per step.
+template <class TimeAt>
+__device__ __forceinline__ void search_time2(uint32_t s, uint32_t e, int64_t xa, int64_t xb, bool incl, TimeAt tt,
+                                             uint32_t* a, uint32_t* b) {
+  uint32_t la = s, ha = e, lb = s, hb = e;
+  while (la < ha || lb < hb) {
+    const uint32_t ma = la + ((ha - la) >> 1), mb = lb + ((hb - lb) >> 1);
+    const bool ra = la < ha, rb = lb < hb;
+    const int64_t va = ra ? tt(ma) : 0, vb = rb ? tt(mb) : 0;
+    if (ra) {
+      if (va <= xa) la = ma + 1; else ha = ma;
+    }
+    if (rb) {
+      if (incl ? vb <= xb : vb < xb) lb = mb + 1; else hb = mb;
+    }
+  }
+  *a = la;
+  *b = lb;
+}
 
 // Positions [a, b) of the pair list L_{x,y} with time in (tlo, thi) or
 // (tlo, thi] (hi_incl).  The list's range comes from the pair hash table (one
@@ -588,14 +458,13 @@ __device__ __forceinline__ bool pair_window(const SamplerArgs& A, int32_t x, int
     h = (h + 1) & A.hash_mask;
   }
   if (!found) return false;
+  // both bounds bisect [s, e) in lockstep, so that their probes are in flight together
   if (A.pair_t32) {  // 4-byte entries, eight per sector
     auto tt = [&](uint32_t p) { return (int64_t)__ldg(A.pair_t32 + p) + A.tmin; };
-    *a = search_time<false>(s, e, tlo, tt);
-    *b = hi_incl ? search_time<false>(*a, e, thi, tt) : search_time<true>(*a, e, thi, tt);
+    search_time2(s, e, tlo, thi, hi_incl, tt, a, b);
   } else {
     auto tt = [&](uint32_t p) { return __ldg(A.pair_t + p); };
-    *a = search_time<false>(s, e, tlo, tt);
-    *b = hi_incl ? search_time<false>(*a, e, thi, tt) : search_time<true>(*a, e, thi, tt);
+    search_time2(s, e, tlo, thi, hi_incl, tt, a, b);
   }
   return true;
 }
@@ -871,9 +740,23 @@ __device__ __forceinline__ bool bounded_draw_slow(uint64_t seed, uint64_t s, uin
 }
 
 // One sample (Alg. 2, 3): sample index i within the call (id offset + i).
+constexpr uint32_t kSmemBins = 1024;  // per-block bins of the proposal sampler (see k_sample)
+constexpr size_t kSmemBinBytes = 3 * sizeof(unsigned long long) * kSmemBins;
+
+// Adds X and X^2 to bin h: three 64-bit words (sum X, sum X^2 low, high).
+__device__ __forceinline__ void bin_add(unsigned long long* bin, uint64_t X) {
+  atomicAdd(bin, (unsigned long long)X);
+  const unsigned __int128 x2 = (unsigned __int128)X * X;
+  const unsigned long long l2 = (uint64_t)x2;
+  const unsigned long long old = atomicAdd(bin + 1, l2);
+  const unsigned long long carry = (old + l2 < old) ? 1ull : 0ull;
+  if ((x2 >> 64) || carry) atomicAdd(bin + 2, (unsigned long long)(x2 >> 64) + carry);
+}
+
 template <bool Trace>
 __device__ __forceinline__ void sample_one(const SamplerArgs& A, const Plan& P, uint64_t W, uint32_t shift,
-                                           uint64_t i, ThreadSums& T, uint32_t* s_err) {
+                                           uint64_t i, ThreadSums& T, uint32_t* s_err,
+                                           unsigned long long* sbins = nullptr, uint32_t hmin = 0) {
   const uint64_t s = A.offset + i;
   uint64_t r2, r1, r3;
   const uint2 key = make_uint2((uint32_t)A.seed, (uint32_t)(A.seed >> 32));
@@ -916,14 +799,10 @@ __device__ __forceinline__ void sample_one(const SamplerArgs& A, const Plan& P, 
   end_edge(A, P.alpha1, p1, &up, &t1);
   end_edge(A, P.alpha3, p3, &vp, &t3);
   const uint64_t X = check_motif(A, P, up, me.src, me.dst, vp, t1, me.t, t3, s_err, &T.checked);
-  if (A.h && X) {  // exact per-h bins of the proposal estimator
-    unsigned long long* bin = A.bins + 3 * (uint64_t)__ldg(A.h + lo);
-    atomicAdd(bin, (unsigned long long)X);
-    const unsigned __int128 x2 = (unsigned __int128)X * X;
-    const unsigned long long l2 = (uint64_t)x2;
-    const unsigned long long old = atomicAdd(bin + 1, l2);
-    const unsigned long long carry = (old + l2 < old) ? 1ull : 0ull;
-    if ((x2 >> 64) || carry) atomicAdd(bin + 2, (unsigned long long)(x2 >> 64) + carry);
+  if (A.h && X) {  // exact per-h bins of the proposal estimator (the block's own when it has them)
+    const uint32_t hv = __ldg(A.h + lo);
+    const bool local = sbins && hv - hmin < kSmemBins;  // an h outside the recorded range goes to global
+    bin_add(local ? sbins + 3 * (uint64_t)(hv - hmin) : A.bins + 3 * (uint64_t)hv, X);
   }
   if (Trace) {
     A.trace[4 * i + 0] = lo;
@@ -938,9 +817,14 @@ __device__ __forceinline__ void sample_one(const SamplerArgs& A, const Plan& P, 
   T.hits += X != 0;
 }
 
+// Proposal mode: a block accumulates the per-h bins of its samples in
+// shared memory (kSmemBins consecutive h values from the proposal's
+// smallest h) and adds them to the global bins once at its end, instead of
+// one global atomic per hit on a few hot bins.
 template <bool Trace>
 __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __grid_constant__ SamplerArgs A,
                                                 const __grid_constant__ Plan P) {
+  extern __shared__ unsigned long long s_bins[];  // kSmemBinBytes in proposal mode, else none
   const IndexHeader* H = A.hdr;
   const uint64_t W = H->W;
   const uint32_t shift = H->shift;
@@ -949,6 +833,14 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __gr
   if (threadIdx.x == 0) {
     s_err = 0;
     s_x = s_x2lo = s_x2hi = s_hits = s_checked = 0;
+  }
+  uint32_t hmin = 0;
+  bool local_bins = false;
+  if (A.h && A.hrange) {
+    hmin = A.hrange[0];
+    local_bins = A.hrange[1] >= hmin && A.hrange[1] - hmin < kSmemBins;
+    if (local_bins)
+      for (uint32_t b = threadIdx.x; b < 3 * kSmemBins; b += blockDim.x) s_bins[b] = 0;
   }
   __syncthreads();
   const uint32_t bad = index_check(A, P);
@@ -960,7 +852,19 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __gr
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < A.count && W; j += stride) {
     const uint64_t i = A.chunk_base + (A.order ? __ldg(A.order + j) : j);  // sample index within the call
-    sample_one<Trace>(A, P, W, shift, i, T, &s_err);
+    sample_one<Trace>(A, P, W, shift, i, T, &s_err, local_bins ? s_bins : nullptr, hmin);
+  }
+  if (local_bins) {
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < kSmemBins; b += blockDim.x) {
+      const unsigned long long x = s_bins[3 * b], lo = s_bins[3 * b + 1], hi = s_bins[3 * b + 2];
+      if (!x && !lo && !hi) continue;
+      unsigned long long* g = A.bins + 3 * (uint64_t)(hmin + b);
+      atomicAdd(g, x);
+      const unsigned long long old = atomicAdd(g + 1, lo);
+      const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+      if (hi || carry) atomicAdd(g + 2, hi + carry);
+    }
   }
   block_commit(A.sums, W, T.sx, T.sx2, T.hits, T.checked, T.err, s_err, s_x, s_x2lo, s_x2hi, s_hits, s_checked);
 }
@@ -1317,15 +1221,16 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
   A.sums = d_sums;
   A.h = h;
   A.bins = bins;
+  A.hrange = h ? (const uint32_t*)((const char*)qindex + kProposalRangeOffset) : nullptr;
   A.rec_hdr = rec_hdr;
   static int blocks_per_sm[2] = {0, 0};
   const int ti = trace ? 1 : 0;
   if (!blocks_per_sm[ti]) {
     int b = 0;
     if (trace)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample<true>, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample<true>, 256, kSmemBinBytes);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample<false>, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sample<false>, 256, kSmemBinBytes);
     blocks_per_sm[ti] = b > 0 ? b : 1;
   }
   const uint64_t max_blocks = (uint64_t)num_sms() * blocks_per_sm[ti];
@@ -1336,10 +1241,11 @@ tc_status launch_sampler(const tc_graph* g, const Plan& plan, int64_t delta, con
     uint64_t blocks = max_blocks;
     const uint64_t need = (count + 255) / 256;
     if (need < blocks) blocks = need ? need : 1;
+    const size_t dyn = h ? kSmemBinBytes : 0;
     if (trace)
-      k_sample<true><<<(unsigned)blocks, 256, 0, st>>>(A, plan);
+      k_sample<true><<<(unsigned)blocks, 256, dyn, st>>>(A, plan);
     else
-      k_sample<false><<<(unsigned)blocks, 256, 0, st>>>(A, plan);
+      k_sample<false><<<(unsigned)blocks, 256, dyn, st>>>(A, plan);
     TC_LAUNCHED(1);
     TC_CUDA(cudaGetLastError());
     return TC_OK;
