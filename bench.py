@@ -160,6 +160,15 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def load_bf16_peak():
+    """Dense bf16 tensor throughput (TFLOP/s) of MEASURED_PEAKS.json (burst), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def workload(name="large"):
     from paper_2409_08975_gb300 import synth
     return synth.CONFIGS[name]()
@@ -352,9 +361,26 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
     mlp = tc.MLP(seed=1)
     losses, train_ms = timed(lambda: tc.tc_mlp_train(mlp, g, mot, delta, wts, feat, n_train, seed=12345,
                                                      batch=16384, lr=3e-3, objective=objective, eps=eps))
-    props = [timed(lambda: tc.tc_proposal_weights(mlp, g, mot, delta, wts, feat, eps=eps)) for _ in range(3)]
+    props, net_ms, guide_ms = [], [], []
+    tc.tc_set_timing(True)
+    for _ in range(3):
+        props.append(timed(lambda: tc.tc_proposal_weights(mlp, g, mot, delta, wts, feat, eps=eps)))
+        net_ms.append(tc.tc_last_phase_ms("proposal"))
+        guide_ms.append(tc.tc_last_phase_ms("index"))
+    tc.tc_set_timing(False)
     prop = props[-1][0]
     prop_ms = statistics.median(ms for _, ms in props)
+    # the network on the tensor cores: 2 (16 x 64 + 64 x 64 + 64) FLOP per edge
+    flops = 2 * (16 * 64 + 64 * 64 + 64) * g.m
+    tflops_peak = load_bf16_peak()
+    net = statistics.median(net_ms)
+    inference_phases = {"network_h_q_prefix_ms": net, "guide_ms": statistics.median(guide_ms),
+                        "tensor_tflops": flops / (net / 1e3) / 1e12 if net > 0 else None,
+                        "bf16_peak_tflops": tflops_peak,
+                        "frac_of_bf16_peak": flops / (net / 1e3) / 1e12 / tflops_peak if net > 0 else None,
+                        "path": ("tcgen05.mma kind::f16 M128 N64 (TMEM accumulators, one issuing thread)"
+                                 if tc.tc_mlp_kernel() == "tcgen05" else
+                                 "mma.sync m16n8k16 bf16 (warp-level tensor-core MMA)")}
     runs = []
     for i in range(4):
         r, ms = timed(lambda: tc.tc_sample_estimate_q(g, mot, delta, wts, prop, k, seed=0, offset=(50 + i) * k))
@@ -390,7 +416,8 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
     return {"variant": variant, "objective": objective, "inputs": 12 if variant == "as_written" else 16, "eps": eps,
             "train_samples": n_train, "stats_samples": n_stats,
             "setup_ms": {"features": feat_ms, "sample_statistics": sfeat_ms, "training": train_ms},
-            "inference_ms": prop_ms, "sampler_ms": q_ms, "samples_per_s": k / (q_ms / 1e3),
+            "inference_ms": prop_ms, "inference_phases": inference_phases, "sampler_ms": q_ms,
+            "samples_per_s": k / (q_ms / 1e3),
             "loss_first_batch": losses[0], "loss_last_batch": losses[1],
             "estimate": c, "std_err": rq["std_err"], "plain_estimate": plain["estimate"],
             "plain_std_err": plain["std_err"],

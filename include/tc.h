@@ -351,7 +351,9 @@ tc_status tc_sample_features(const tc_graph* g, const tc_motif* motif, int64_t d
                              uint16_t* d_feat, void* stream);
 
 /* Logits z of rows d_rows[i] (or i when d_rows is NULL) of d_feat into
- * d_logits[n] (FP32); g = sigmoid(z). */
+ * d_logits[n] (FP32); g = sigmoid(z).  Synchronises the stream.
+ * TC_ERR_TIMEOUT: a bounded wait of the tcgen05 inference kernel for its
+ * tensor-core MMAs gave up (the logits are then incomplete). */
 tc_status tc_mlp_forward(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, uint64_t n,
                          float* d_logits, void* stream);
 
@@ -515,15 +517,28 @@ float tc_last_sampler_ms(void);
  * thread that ran it while timing was enabled (tc_set_timing): the sum over
  * CUDA events recorded around the phase's launches on the call's stream (0
  * when timing was off or the phase did not run).  Phases: the path weights
- * and their exact prefix sum (Claim 1, Alg. 1) of tc_path_weights; its
- * sampling index (records' guide table); the key-order sort of the sample
- * ids of a sampling call; its sampling launches (Alg. 2-4, the same as
- * tc_last_sampler_ms). */
+ * and their exact prefix sum (Claim 1, Alg. 1) of tc_path_weights; the
+ * guide table of its sampling index (or of tc_proposal_weights' index); the
+ * key-order sort of the sample ids of a sampling call; its sampling
+ * launches (Alg. 2-4, the same as tc_last_sampler_ms); the network, h, q
+ * and q-prefix of tc_proposal_weights. */
 #define TC_PHASE_WEIGHTS 0
 #define TC_PHASE_INDEX 1
 #define TC_PHASE_ORDER 2
 #define TC_PHASE_SAMPLE 3
+#define TC_PHASE_PROPOSAL 4
 float tc_last_phase_ms(int32_t phase);
+
+/* Which kernel runs the network's inference (tc_mlp_forward, the logits of
+ * the variance objective, tc_proposal_weights), for the whole process:
+ * kind 0 = warp-level mma.sync tiles with register-resident weights,
+ * 1 = tcgen05 MMAs into TMEM accumulators issued by one thread per block;
+ * kind < 0 only queries.  Both compute the same network in the same
+ * precisions (bf16 operands, FP32 accumulation); sums may differ in
+ * rounding order.  The default is the build's TC_MLP_TCGEN05, overridden by
+ * the environment variable of the same name ("0" or "1").  Returns the kind
+ * in effect after the call; -1 for an unknown kind (nothing changes). */
+int32_t tc_mlp_kernel(int32_t kind);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* tc_last_error(void);

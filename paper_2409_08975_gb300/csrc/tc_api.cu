@@ -69,6 +69,7 @@ tc_status device_status(uint32_t bits, const char* what) {
   if (bits & kErrOverflow) return set_error(TC_ERR_OVERFLOW, w + ": a 64-bit count overflowed");
   if (bits & kErrRng) return set_error(TC_ERR_RNG_EXHAUSTED, w + ": 64 rejected draws in a row");
   if (bits & kErrBounds) return set_error(TC_ERR_BOUNDS, w + ": device index check failed");
+  if (bits & kErrTimeout) return set_error(TC_ERR_TIMEOUT, w + ": a bounded device wait gave up");
   return TC_OK;
 }
 
@@ -297,6 +298,8 @@ tc_status tc_set_timing(int32_t enabled) {
 float tc_last_sampler_ms(void) { return last_sampler_ms(); }
 
 float tc_last_phase_ms(int32_t phase) { return last_phase_ms(phase); }
+
+int32_t tc_mlp_kernel(int32_t kind) { return mlp_kernel(kind); }
 
 tc_status tc_motif_plan(const tc_motif* motif, int32_t* h_anchor, int32_t* h_class) {
   Plan p;
@@ -673,7 +676,8 @@ tc_status tc_sample_features(const tc_graph* g, const tc_motif* motif, int64_t d
 tc_status tc_mlp_forward(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, uint64_t n,
                          float* d_logits, void* stream) {
   if (!mlp || (n && (!d_feat || !d_logits))) return set_error(TC_ERR_INVALID_ARG, "NULL argument");
-  return launch_mlp_forward(mlp, d_feat, d_rows, n, d_logits, S(stream));
+  TC_TRY(launch_mlp_forward(mlp, d_feat, d_rows, n, d_logits, S(stream)));
+  return mlp_check_error(mlp, S(stream), "tc_mlp_forward");
 }
 
 tc_status tc_mlp_grad(const tc_mlp* mlp, const uint16_t* d_feat, const uint32_t* d_rows, const float* d_labels,
@@ -714,6 +718,7 @@ tc_status tc_mlp_grad_ex(const tc_mlp* mlp, const uint16_t* d_feat, const uint32
     if (e != cudaSuccess) s = cuda_status(e, "tc_mlp_grad");
   }
   cudaFreeAsync(buf, st);
+  if (s == TC_OK && var) s = mlp_check_error(mlp, st, "tc_mlp_grad_ex");
   if (s == TC_OK && h_loss) *h_loss = var ? hl : (n ? hl / (float)n : 0.f);
   return s;
 }
@@ -783,6 +788,7 @@ tc_status tc_mlp_train_ex(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif,
   for (void* p : {(void*)trace, (void*)rows, (void*)labels, (void*)losses, (void*)sums, (void*)zbuf})
     if (p) cudaFreeAsync(p, st);
   if (s == TC_OK && hs.err) s = device_status(hs.err, "tc_mlp_train");
+  if (s == TC_OK && var) s = mlp_check_error(mlp, st, "tc_mlp_train");
   if (s == TC_OK && h_losses) {
     const uint64_t last_n = n_samples - (steps - 1) * (uint64_t)batch;
     h_losses[0] = var ? first : first / (float)(batch < n_samples ? batch : n_samples);
@@ -819,12 +825,17 @@ tc_status tc_proposal_weights(const tc_mlp* mlp, const tc_graph* g, const tc_mot
   uint32_t* err = (uint32_t*)scratch;
   e = cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) s = cuda_status(e, "tc_proposal_weights allocation");
+  PhaseTimer pt(TC_PHASE_PROPOSAL, st), it(TC_PHASE_INDEX, st);
+  pt.start();
   if (s == TC_OK)
     s = launch_proposal_scan(mlp, d_feat, d_prefix, m, eps, (float)scale, d_h, d_qprefix,
                              (uint32_t*)((char*)d_qindex + kProposalRangeOffset), scratch + 256, err, st);
+  pt.stop();
+  it.start();
   if (s == TC_OK)
     s = launch_guide_at(g, plan, delta, d_qprefix, (IndexHeader*)d_qindex,
                         (uint32_t*)((char*)d_qindex + kIndexHeaderBytes), err, st);
+  it.stop();
   uint32_t h_err = 0;
   if (s == TC_OK && h_Q) {
     e = cudaMemcpyAsync(h_Q, d_qprefix + m, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);

@@ -81,6 +81,7 @@ enum : uint32_t {
   kErrBounds = 1u << 2,
   kErrBadId = 1u << 3,
   kErrIndexMismatch = 1u << 4,
+  kErrTimeout = 1u << 5,
 };
 
 // ---------------------------------------------------------------------------
@@ -353,6 +354,10 @@ tc_status launch_variance_grad(const tc_mlp* M, const uint16_t* feat, const uint
                                float* loss_scratch, cudaStream_t st);
 tc_status mlp_adam(tc_mlp* M, float lr, cudaStream_t st);
 float* mlp_grad_buffer(tc_mlp* M);
+int mlp_kernel(int kind);  // tc_mlp_kernel
+// Synchronises st, then reports (and clears) the error bits the network's
+// inference kernel left in the network's device error word.
+tc_status mlp_check_error(const tc_mlp* M, cudaStream_t st, const char* what);
 tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint64_t n, int64_t delta,
                                  uint16_t* feat, uint32_t* d_err, cudaStream_t st);
 tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st,
@@ -405,7 +410,7 @@ tc_status launch_sample_batch(int block_size, uint32_t tile, unsigned blocks, co
 // Diagnostic timing by phase (tc_set_timing, tc_last_phase_ms): a
 // PhaseTimer records an event pair around each start()/stop() on its stream
 // while timing is on; constructing one drops the phase's earlier events.
-constexpr int kNumPhases = 4;
+constexpr int kNumPhases = 5;
 struct PhaseTimer {
   int ph;
   cudaStream_t st;

@@ -30,6 +30,7 @@ struct tc_mlp {
   float* m1;      // Adam first moments
   float* m2;      // Adam second moments
   float* grad;    // gradient accumulator
+  uint32_t* err;  // device error word of the tcgen05 inference kernel
   uint64_t steps;
   int device;
 };
@@ -427,15 +428,24 @@ __device__ __forceinline__ void tile_logits(const MlpFwdShared& S, const MlpFrag
     a1[kk][hi] = relu_bf16x2(c[0], c[1]);
     a1[kk][hi + 1] = relu_bf16x2(c[2], c[3]);
   }
+  // layer 2: k-tile outer, so that the 8 output tiles' MMAs are independent
+  // back to back instead of 8 chains of 4 dependent ones
+  float c2[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    c2[j][0] = c2[j][2] = S.b2[j * 8 + 2 * q];
+    c2[j][1] = c2[j][3] = S.b2[j * 8 + 2 * q + 1];
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; kk++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) mma_bf16(c2[j], a1[kk], F.w2[j][kk][0], F.w2[j][kk][1]);
   uint32_t a2[4][4];
 #pragma unroll
   for (int j = 0; j < 8; j++) {
-    float c[4] = {S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1], S.b2[j * 8 + 2 * q], S.b2[j * 8 + 2 * q + 1]};
-#pragma unroll
-    for (int kk = 0; kk < 4; kk++) mma_bf16(c, a1[kk], F.w2[j][kk][0], F.w2[j][kk][1]);
     const int kk = j >> 1, hi = (j & 1) * 2;
-    a2[kk][hi] = relu_bf16x2(c[0], c[1]);
-    a2[kk][hi + 1] = relu_bf16x2(c[2], c[3]);
+    a2[kk][hi] = relu_bf16x2(c2[j][0], c2[j][1]);
+    a2[kk][hi + 1] = relu_bf16x2(c2[j][2], c2[j][3]);
   }
   float c3[4] = {F.b3, F.b3, F.b3, F.b3};
 #pragma unroll
@@ -593,6 +603,293 @@ __global__ void __launch_bounds__(kPThreads, TC_PROPOSAL_MIN_BLOCKS) k_proposal(
 }
 
 // ---------------------------------------------------------------------------
+// The network on the fifth-generation tensor cores (tcgen05): 128 rows per
+// MMA, accumulators in tensor memory (TMEM), operands in shared memory in the
+// canonical K-major layout without swizzle, one thread issuing the MMAs and
+// an mbarrier signalling their completion.  Each of the 128 threads owns one
+// row: it stages its feature row, reads its row of each layer's
+// accumulators back with tcgen05.ld, applies bias, ReLU and bf16 rounding
+// (the same arithmetic as the oracle's quantised forward), and stages the
+// next layer's operand; the last layer (64 -> 1) is an FP32 dot product in
+// the thread.
+
+// K-major operand without swizzle: 8-row x 16-byte core matrices; element
+// (r, k) of a bf16 matrix with K columns lies at byte
+//   (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2,
+// SBO = 16 K bytes (the core matrices of one 8-row group side by side along K,
+// 128 bytes apart: the leading-dimension offset).
+__device__ __forceinline__ uint32_t umma_offset(uint32_t r, uint32_t k, uint32_t K) {
+  return (r >> 3) * (16u * K) + (k >> 3) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
+}
+
+// Shared-memory matrix descriptor (start address, leading-dimension byte
+// offset = 128, stride-dimension byte offset, descriptor version 1, no swizzle).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B bf16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+constexpr uint32_t kUmmaM = 128, kUmmaN = 64;
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((kUmmaN >> 3) << 17) | ((kUmmaM >> 4) << 24);
+constexpr uint32_t kTmemCols = 64;  // D1, then D2, at columns 0..63
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, bool accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdescBf16), "r"((uint32_t)accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tc05_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc05_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
+struct alignas(1024) UmmaShared {
+  __nv_bfloat16 A1[kUmmaM * kF];  // this sub-tile's feature rows
+  __nv_bfloat16 B1[kH * kF];      // W1 [n][k]
+  __nv_bfloat16 A2[kUmmaM * kH];  // layer-1 activations
+  __nv_bfloat16 B2[kH * kH];      // W2 [n][k]
+  float b1[kH], b2[kH], W3[kH];   // W3 as bf16 values held in FP32
+  float b3;
+  uint64_t mbar;
+  uint32_t tmem;
+  uint32_t err;
+  unsigned long long red[4];
+};
+// At least 30 KB of shared memory per block, so that at most seven blocks
+// share an SM (8 x 31 KB exceeds the SM's 228 KB): their TMEM (kTmemCols
+// each) then always fits the 512 columns of an SM and no allocation waits.
+constexpr size_t kUmmaSmemBytes =
+    sizeof(UmmaShared) + 1024 > 30 * 1024 ? sizeof(UmmaShared) + 1024 : 30 * 1024;
+static_assert(7 * kTmemCols <= 512, "TMEM of the blocks one SM can hold");
+constexpr int kUmmaSubTiles = 16;                         // 128-row sub-tiles per tile
+constexpr uint64_t kUmmaTile = kUmmaSubTiles * kUmmaM;     // 2048 rows: the scan's tile
+constexpr uint64_t kUmmaWaitNs = 1000000000ull;            // bound of each completion wait: 1 s
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the MMAs committed to the barrier (phase parity), at most
+// kUmmaWaitNs of wall time; false when the wait gave up.  The MMAs of one
+// sub-tile take well under a microsecond.
+__device__ __forceinline__ bool umma_wait(uint64_t* mbar, uint32_t parity) {
+  if (mbar_try_wait(mbar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(mbar, parity))
+    if (global_ns() - t0 > kUmmaWaitNs) return false;
+  return true;
+}
+
+// Proposal: for the rows of the tiles this block takes (rows[i] or i index
+// the feature rows), the logits (Proposal = false: into logits) or h, q = w h
+// and each 2048-row tile's sum of q (Proposal = true), as k_proposal does.
+template <bool Proposal>
+__global__ void __launch_bounds__(kUmmaM, 4) k_mlp_umma(const float* __restrict__ params,
+                                                      const __nv_bfloat16* __restrict__ feat,
+                                                      const uint32_t* __restrict__ rows, uint64_t n,
+                                                      float* __restrict__ logits, const uint64_t* __restrict__ prefix,
+                                                      float eps, float scale, uint16_t* __restrict__ h,
+                                                      uint64_t* __restrict__ q, uint64_t* __restrict__ tile_sums,
+                                                      uint32_t* __restrict__ hrange, uint32_t* __restrict__ d_err) {
+  extern __shared__ __align__(1024) unsigned char umma_raw[];
+  UmmaShared& S = *reinterpret_cast<UmmaShared*>(
+      umma_raw + ((1024u - (smem_u32(umma_raw) & 1023u)) & 1023u));  // 1024-byte aligned in the window
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the weights as bf16 operands in the canonical layout, biases and W3
+  for (int i = tid; i < kH * kF; i += kUmmaM)
+    S.B1[umma_offset(i / kF, i % kF, kF) / 2] = __float2bfloat16_rn(params[kOffW1 + i]);
+  for (int i = tid; i < kH * kH; i += kUmmaM)
+    S.B2[umma_offset(i / kH, i % kH, kH) / 2] = __float2bfloat16_rn(params[kOffW2 + i]);
+  if (tid < kH) {
+    S.b1[tid] = params[kOffB1 + tid];
+    S.b2[tid] = params[kOffB2 + tid];
+    S.W3[tid] = __bfloat162float(__float2bfloat16_rn(params[kOffW3 + tid]));
+  }
+  if (tid == 0) {
+    S.b3 = params[kOffB3];
+    S.err = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  const uint32_t tmem = S.tmem;
+  const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;  // this warp's 32 TMEM lanes (= rows)
+  const uint32_t a1 = smem_u32(S.A1), b1 = smem_u32(S.B1), a2 = smem_u32(S.A2), b2 = smem_u32(S.B2);
+  uint32_t parity = 0, err = 0, hlo = 0xFFFFFFFFu, hhi = 0;
+  bool ok = true;
+  const uint64_t T = (n + kUmmaTile - 1) / kUmmaTile;
+  for (uint64_t tile = blockIdx.x; tile < T && ok; tile += gridDim.x) {
+    unsigned long long tsum = 0;
+    for (int sub = 0; sub < kUmmaSubTiles && ok; sub++) {
+      const uint64_t r0 = tile * kUmmaTile + (uint64_t)sub * kUmmaM;
+      if (r0 >= n) break;  // the same for the whole block
+      const uint64_t row = r0 + tid;
+      const bool valid = row < n;
+      uint4 xlo = make_uint4(0, 0, 0, 0), xhi = xlo;
+      if (valid) {
+        const uint4* src = reinterpret_cast<const uint4*>(feat + (uint64_t)(rows ? rows[row] : row) * kF);
+        xlo = __ldg(src);
+        xhi = __ldg(src + 1);
+      }
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.A1) + umma_offset(tid, 0, kF)) = xlo;
+      *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.A1) + umma_offset(tid, 8, kF)) = xhi;
+      fence_async_smem();
+      tc05_fence_before();
+      __syncthreads();
+      tc05_fence_after();
+      // layer 1: D1 [128 x 64] = X [128 x 16] W1^T
+      if (tid == 0) {
+        umma_bf16(tmem, umma_desc(a1, 16 * kF), umma_desc(b1, 16 * kF), false);
+        umma_commit(&S.mbar);
+      }
+      ok = __syncthreads_and(umma_wait(&S.mbar, parity));
+      if (!ok) break;  // parity stays that of the phase still pending
+      parity ^= 1;
+      tc05_fence_after();
+#pragma unroll
+      for (int c = 0; c < 4; c++) {  // bias, ReLU, bf16: the A operand of layer 2
+        float v[16];
+        tmem_ld16(tmem + lane_addr + (uint32_t)(c * 16), v);
+        uint32_t pk[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+          pk[j] = relu_bf16x2(v[2 * j] + S.b1[c * 16 + 2 * j], v[2 * j + 1] + S.b1[c * 16 + 2 * j + 1]);
+        char* dst = reinterpret_cast<char*>(S.A2);
+        *reinterpret_cast<uint4*>(dst + umma_offset(tid, c * 16, kH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(dst + umma_offset(tid, c * 16 + 8, kH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
+      fence_async_smem();
+      tc05_fence_before();
+      __syncthreads();
+      tc05_fence_after();
+      // layer 2: D2 [128 x 64] = A1 [128 x 64] W2^T, K in four steps of 16, into
+      // the columns of D1 (read by every thread before the barrier above)
+      if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++)
+          umma_bf16(tmem, umma_desc(a2 + kk * 256, 16 * kH), umma_desc(b2 + kk * 256, 16 * kH), kk > 0);
+        umma_commit(&S.mbar);
+      }
+      ok = __syncthreads_and(umma_wait(&S.mbar, parity));
+      if (!ok) break;  // parity stays that of the phase still pending
+      parity ^= 1;
+      tc05_fence_after();
+      float z = S.b3;  // layer 3 in FP32 on the bf16-rounded activations
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        float v[16];
+        tmem_ld16(tmem + lane_addr + (uint32_t)(c * 16), v);
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const float a = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + S.b2[c * 16 + j], 0.f)));
+          z = fmaf(a, S.W3[c * 16 + j], z);
+        }
+      }
+      tc05_fence_before();  // the next sub-tile's MMAs overwrite D1, D2 after the next barrier
+      if (valid) {
+        if (!Proposal) {
+          logits[row] = z;
+        } else {
+          const float fv = floorf(scale * (eps + sigmoidf_(z)) + 0.5f);
+          const uint32_t hv = fv < 1.f ? 1u : (uint32_t)fv;
+          const unsigned long long wv = __ldg(prefix + row + 1) - __ldg(prefix + row);
+          if (__umul64hi(wv, hv)) err |= kErrOverflow;
+          const unsigned long long qv = wv * hv;
+          q[row] = qv;
+          h[row] = (uint16_t)hv;
+          if (tsum + qv < tsum) err |= kErrOverflow;
+          tsum += qv;
+          hlo = hv < hlo ? hv : hlo;
+          hhi = hv > hhi ? hv : hhi;
+        }
+      }
+    }
+    if (Proposal && ok) {  // the tile's sum of q
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, tsum, o);
+        if (tsum + y < tsum) err |= kErrOverflow;
+        tsum += y;
+      }
+      if (lane == 0) S.red[warp] = tsum;
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kUmmaM / 32; w++) {
+          if (t + S.red[w] < t) err |= kErrOverflow;
+          t += S.red[w];
+        }
+        tile_sums[tile] = t;
+      }
+      __syncthreads();
+    }
+  }
+  if (!ok) err |= kErrTimeout;
+  if (Proposal) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      hlo = min(hlo, __shfl_xor_sync(0xffffffffu, hlo, o));
+      hhi = max(hhi, __shfl_xor_sync(0xffffffffu, hhi, o));
+    }
+    if (lane == 0 && hhi) {
+      atomicMin(hrange, hlo);
+      atomicMax(hrange + 1, hhi);
+    }
+  }
+  if (err) atomicOr(&S.err, err);
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  if (!ok && tid == 0) umma_wait(&S.mbar, parity);  // one more bounded wait for MMAs still in flight
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  if (tid == 0 && S.err) atomicOr(d_err, S.err);
+}
+
+// ---------------------------------------------------------------------------
 // Gradient of the mean closure loss over a batch (the binary cross-entropy
 // when every label is 0 or 1), or of any loss whose dloss/dz3 per row is
 // given.  Each warp runs the forward of a 16-row tile on the tensor cores and
@@ -628,7 +925,11 @@ struct TrainShared {
 // g_i = sigmoid(z_i), the per-sample second moment of the estimate under the
 // proposal is proportional to L = mean(h) * mean(X_i^2 / h_i) (the batch's
 // paths come from the plain sampler, so mean(h) estimates Q / W).  Writes
-// dL/dz_i into dz and L into *loss; sums in FP64.
+// dL/dz_i into dz and L into *loss.  The per-row terms are FP32 (the
+// objective is checked to 1e-3 and its gradient to 1e-2; FP64 arithmetic
+// runs at a small fraction of the FP32 rate on this GPU, and a division per
+// row in FP64 made this kernel the bulk of a training step); only the sums
+// over the batch accumulate in FP64.
 __global__ void __launch_bounds__(1024) k_variance_dz(const float* __restrict__ z, const float* __restrict__ X,
                                                       uint64_t n, float eps, float* __restrict__ dz,
                                                       float* __restrict__ loss) {
@@ -636,10 +937,10 @@ __global__ void __launch_bounds__(1024) k_variance_dz(const float* __restrict__ 
   __shared__ double s_A, s_B;
   double a = 0.0, b = 0.0;
   for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double h = (double)eps + (double)sigmoidf_(z[i]);
-    const double x = X[i];
-    a += h;
-    b += x * x / h;
+    const float h = eps + sigmoidf_(z[i]);
+    const float x = X[i];
+    a += (double)h;
+    b += (double)(x * x / h);
   }
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -661,12 +962,12 @@ __global__ void __launch_bounds__(1024) k_variance_dz(const float* __restrict__ 
     *loss = (float)(s_A * s_B);
   }
   __syncthreads();
-  const double A = s_A, B = s_B;
+  const float A = (float)s_A, B = (float)s_B, inv_n = (float)(1.0 / (double)n);
   for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double g = sigmoidf_(z[i]);
-    const double h = (double)eps + g;
-    const double x = X[i];
-    dz[i] = (float)(g * (1.0 - g) * (B - A * x * x / (h * h)) / (double)n);
+    const float g = sigmoidf_(z[i]);
+    const float h = eps + g;
+    const float x = X[i];
+    dz[i] = g * (1.f - g) * (B - A * (x / h) * (x / h)) * inv_n;
   }
 }
 
@@ -850,7 +1151,7 @@ tc_status mlp_create(uint64_t seed, tc_mlp** out) {
   std::memset(M, 0, sizeof(*M));
   cudaGetDevice(&M->device);
   float* buf = nullptr;
-  cudaError_t e = cudaMalloc(&buf, sizeof(float) * 4 * kNParams);
+  cudaError_t e = cudaMalloc(&buf, sizeof(float) * (4 * kNParams + 1));
   if (e != cudaSuccess) {
     delete M;
     return cuda_status(e, "cudaMalloc(mlp)");
@@ -859,7 +1160,8 @@ tc_status mlp_create(uint64_t seed, tc_mlp** out) {
   M->m1 = buf + kNParams;
   M->m2 = buf + 2 * kNParams;
   M->grad = buf + 3 * kNParams;
-  e = cudaMemset(buf, 0, sizeof(float) * 4 * kNParams);
+  M->err = reinterpret_cast<uint32_t*>(buf + 4 * kNParams);
+  e = cudaMemset(buf, 0, sizeof(float) * (4 * kNParams + 1));
   if (e == cudaSuccess) {
     k_mlp_init<<<(kNParams + 255) / 256, 256>>>(M->params, seed);
     TC_LAUNCHED(1);
@@ -943,9 +1245,60 @@ tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint6
   return s;
 }
 
+// Which network kernel runs inference: the tcgen05 one (TMEM accumulators,
+// one thread issuing the MMAs) or the warp-level mma.sync one.  The build
+// default is TC_MLP_TCGEN05; the environment variable of the same name
+// ("0" or "1") overrides it.
+#ifndef TC_MLP_TCGEN05
+#define TC_MLP_TCGEN05 0
+#endif
+static int g_mlp_kernel = -1;
+static bool use_tcgen05() {
+  if (g_mlp_kernel < 0) {
+    const char* e = getenv("TC_MLP_TCGEN05");
+    g_mlp_kernel = e && (e[0] == '0' || e[0] == '1') ? e[0] - '0' : TC_MLP_TCGEN05;
+  }
+  return g_mlp_kernel == 1;
+}
+int mlp_kernel(int kind) {
+  use_tcgen05();
+  if (kind > 1) return -1;
+  if (kind >= 0) g_mlp_kernel = kind;
+  return g_mlp_kernel;
+}
+
+template <bool Proposal>
+static tc_status launch_umma(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, uint64_t n, float* logits,
+                             const uint64_t* prefix, float eps, float scale, uint16_t* h, uint64_t* q,
+                             uint64_t* tile_sums, uint32_t* hrange, uint32_t* d_err, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    TC_CUDA(cudaFuncSetAttribute(k_mlp_umma<Proposal>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kUmmaSmemBytes));
+    attr = true;
+  }
+  static int bps = 0;
+  if (!bps) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_mlp_umma<Proposal>, kUmmaM, kUmmaSmemBytes);
+    if (bps <= 0) bps = 1;
+  }
+  const uint64_t T = (n + kUmmaTile - 1) / kUmmaTile;
+  uint64_t blocks = (uint64_t)num_sms() * bps;
+  if (blocks > T) blocks = T;
+  k_mlp_umma<Proposal><<<(unsigned)blocks, kUmmaM, kUmmaSmemBytes, st>>>(
+      M->params, reinterpret_cast<const __nv_bfloat16*>(feat), rows, n, logits, prefix, eps, scale, h, q, tile_sums,
+      hrange, d_err);
+  TC_LAUNCHED(1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
 tc_status launch_mlp_forward(const tc_mlp* M, const uint16_t* feat, const uint32_t* rows, uint64_t n, float* out,
                              cudaStream_t st) {
   if (!n) return TC_OK;
+  if (use_tcgen05())
+    return launch_umma<false>(M, feat, rows, n, out, nullptr, 0.f, 0.f, nullptr, nullptr, nullptr, nullptr, M->err,
+                              st);
   k_mlp_forward<<<grid_cap((n + 15) / 16, 4), 128, 0, st>>>(M->params, reinterpret_cast<const __nv_bfloat16*>(feat),
                                                              rows, n, out);
   TC_LAUNCHED(1);
@@ -995,6 +1348,15 @@ tc_status mlp_adam(tc_mlp* M, float lr, cudaStream_t st) {
 
 float* mlp_grad_buffer(tc_mlp* M) { return M->grad; }
 
+tc_status mlp_check_error(const tc_mlp* M, cudaStream_t st, const char* what) {
+  uint32_t bits = 0;
+  TC_CUDA(cudaMemcpyAsync(&bits, M->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  TC_CUDA(cudaStreamSynchronize(st));
+  if (!bits) return TC_OK;
+  TC_CUDA(cudaMemsetAsync(M->err, 0, sizeof(uint32_t), st));
+  return device_status(bits, what);
+}
+
 tc_status launch_clip_labels(const float* labels, uint64_t n, float* out, cudaStream_t st) {
   if (!n) return TC_OK;
   k_clip_labels<<<grid_cap(n, 256), 256, 0, st>>>(labels, n, out);
@@ -1033,6 +1395,10 @@ tc_status launch_proposal_scan(const tc_mlp* M, const uint16_t* feat, const uint
   uint64_t* q = (uint64_t*)p;
   uint64_t* sums = (uint64_t*)(p + scan_align256(8 * m));
   uint64_t* scan_scratch = (uint64_t*)(p + scan_align256(8 * m) + scan_align256(8 * T));
+  if (use_tcgen05()) {
+    TC_TRY(launch_umma<true>(M, feat, nullptr, m, nullptr, prefix, eps, scale, h, q, sums, hrange, d_err, st));
+    return scan_u64_from_tile_sums(q, qprefix, m, sums, d_err, scan_scratch, scan_u64_scratch_words(T) + 1, st);
+  }
   static int bps = 0;
   if (!bps) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_proposal, kPThreads, 0);

@@ -554,7 +554,7 @@ __device__ __forceinline__ uint64_t gaps_product(const SamplerArgs& A, const Pla
 // CheckMotif of a wedge (3-vertex motif): base (u, v, t0) and second edge
 // to or from y at time tj; the three vertices distinct, t0 < tj <= t0 + delta.
 __device__ __forceinline__ uint64_t check_wedge(const SamplerArgs& A, const Plan& P, int32_t y, int32_t u, int32_t v,
-                                                int64_t t0, int64_t tj, uint32_t* err, uint64_t* checked) {
+                                                int64_t t0, int64_t tj, uint32_t* err, uint32_t* checked) {
   if (u == v || y == u || y == v) return 0;
   if (!(t0 < tj) || (uint64_t)tj - (uint64_t)t0 > (uint64_t)A.delta) return 0;
   ++*checked;
@@ -566,7 +566,7 @@ __device__ __forceinline__ uint64_t check_wedge(const SamplerArgs& A, const Plan
 // wedge (u' -e1- u -e2- v) / (u -e2- v -e3- v') of a wedge anchor.
 __device__ __forceinline__ uint64_t check_motif(const SamplerArgs& A, const Plan& P, int32_t up, int32_t u,
                                                 int32_t v, int32_t vp, int64_t t1, int64_t t2, int64_t t3,
-                                                uint32_t* err, uint64_t* checked) {
+                                                uint32_t* err, uint32_t* checked) {
   if (P.wedge)
     return P.wedge == 1 ? check_wedge(A, P, up, u, v, t2, t1, err, checked)
                         : check_wedge(A, P, vp, u, v, t2, t3, err, checked);
@@ -603,7 +603,8 @@ __device__ __forceinline__ void end_edge(const SamplerArgs& A, int alpha, uint32
 
 // Per-thread running sums of a sampling kernel.
 struct ThreadSums {
-  uint64_t sx = 0, hits = 0, checked = 0;
+  uint64_t sx = 0, hits = 0;
+  uint32_t checked = 0;
   unsigned __int128 sx2 = 0;
   uint32_t err = 0;
 };
@@ -698,7 +699,8 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS_DECL) k_path_sum(con
     if (threadIdx.x == 0) atomicOr(&A.sums->err, bad);
     return;
   }
-  uint64_t sx = 0, hits = 0, checked = 0;
+  uint64_t sx = 0, hits = 0;
+  uint32_t checked = 0;
   unsigned __int128 sx2 = 0;
   uint32_t err = 0;
   const uint64_t end = first + count < W ? first + count : W;

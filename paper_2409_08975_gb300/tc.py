@@ -123,6 +123,8 @@ def lib():
         L.tc_last_sampler_ms.restype = ctypes.c_float
         L.tc_last_phase_ms.argtypes = [ctypes.c_int32]
         L.tc_last_phase_ms.restype = ctypes.c_float
+        L.tc_mlp_kernel.argtypes = [ctypes.c_int32]
+        L.tc_mlp_kernel.restype = ctypes.c_int32
         L.tc_last_error.argtypes = []
         L.tc_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -158,12 +160,24 @@ def tc_last_sampler_ms():
     return float(lib().tc_last_sampler_ms())
 
 
-PHASES = {"weights": 0, "index": 1, "order": 2, "sample": 3}
+PHASES = {"weights": 0, "index": 1, "order": 2, "sample": 3, "proposal": 4}
+
+
+MLP_KERNELS = {"mma": 0, "tcgen05": 1}
+
+
+def tc_mlp_kernel(kind=None):
+    """Select ("mma" or "tcgen05") or, with None, query the kernel that runs
+    the network's inference in this process; returns the name in effect."""
+    k = -1 if kind is None else MLP_KERNELS[kind]
+    r = int(lib().tc_mlp_kernel(k))
+    return {v: n for n, v in MLP_KERNELS.items()}[r]
 
 
 def tc_last_phase_ms(phase):
-    """Device ms of a phase ("weights": a1 + a2, "index", "order", "sample")
-    in the last call on this thread that ran it with timing enabled."""
+    """Device ms of a phase ("weights": a1 + a2, "index", "order", "sample",
+    "proposal": network + h + q + q-prefix) in the last call on this thread
+    that ran it with timing enabled."""
     return float(lib().tc_last_phase_ms(PHASES[phase]))
 
 

@@ -103,3 +103,11 @@ def test_estimate_from_sums_matches_the_oracle(libtc):
             assert math.isnan(se)
         else:
             assert se == pytest.approx(rse, rel=1e-12, abs=0.0)
+
+
+def test_mlp_kernel_selector_host_only(libtc):
+    before = libtc.tc_mlp_kernel(-1)
+    assert before in (0, 1)
+    assert libtc.tc_mlp_kernel(7) == -1 and libtc.tc_mlp_kernel(-1) == before
+    assert libtc.tc_mlp_kernel(1) == 1 and libtc.tc_mlp_kernel(0) == 0
+    assert libtc.tc_mlp_kernel(before) == before
