@@ -83,7 +83,8 @@ def parse():
     ap.add_argument("--eps", type=float, default=0.05, help="the learned proposal's mixture weight: q ~ w (eps + g)")
     ap.add_argument("--motif", default=None, choices=sorted(MOTIFS),
                     help="another motif on the workload's graph (default: the workload's own)")
-    ap.add_argument("--workload", default="large", choices=["large", "mid", "learned", "batch", "small", "batch_small"],
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "mid", "learned", "batch", "small", "large_small", "batch_small"],
                     help="large: n=1e8, m=3e8 (default); mid: the 20M-edge graph; learned: n=2e7, m=1e8")
     return ap.parse_args()
 
@@ -182,6 +183,8 @@ WORKLOADS = {
     "large": "large: n=100M m=300M, top degree ~1e6, pair multiplicities Zipf(1.8), daily periodicity over 1e8 s; "
              "directed 4-cycle (M4-0), delta=3600, k=1e9 samples per step",
     "small": "small (profiling case): the mid generator at n=5e5 m=1e7; path+chord, delta=3600, k=1e7",
+    "large_small": "large_small (profiling case): the large generator at n=1e7 m=3e7, top degree ~1e5, pair "
+                   "multiplicities Zipf(1.8), daily periodicity; directed 4-cycle (M4-0), delta=3600, k=3e7",
     "batch_small": "batch_small (profiling case): as batch with a 1e7-edge big graph, 8 small graphs and 1e5-1e7 "
                    "samples per query",
     "batch": "batch: 136 queries in one persistent launch replayed from a CUDA graph; a 50M-edge graph of the mid "
@@ -335,8 +338,9 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
     sample statistics (not for as_written) and training on n_train plain
     samples.  Per query: the inference, h, q and q-prefix with its guide
     (tc_proposal_weights), then the proposal's sampling.  The learned GPU time
-    is inference + q-scan + sampling, the plain one its sampling (key-order
-    sort and sampling launches: plain_ms per k samples).  Relative error at a
+    is inference + q-scan + sampling (a second figure adds the features and
+    sample statistics, a third all of the setup), the plain one its sampling
+    (key-order sort and sampling launches: plain_ms per k samples).  Relative error at a
     fixed GPU time follows from the per-sample variance (k SE^2) and the time
     per sample of each sampler; with the exact count C, it is also measured
     as the mean relative error of five seeds' runs at the GPU time of k plain
@@ -353,7 +357,9 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
         return out, a.elapsed_time(b)
 
     objective = {"closure": "closure", "variance": "variance", "as_written": "bce"}[variant]
-    feat, feat_ms = timed(lambda: tc.tc_edge_features(g, mot, delta, wts))
+    fbuf = tc.alloc_features(g)  # the 32 B per edge buffer is allocated outside the timed call
+    torch.cuda.synchronize()
+    feat, feat_ms = timed(lambda: tc.tc_edge_features(g, mot, delta, wts, out=fbuf))
     n_stats = 0 if variant == "as_written" else (n_stats or n_train)
     sfeat_ms = 0.0
     if n_stats:  # sample statistics from plain samples of another seed than the training paths
@@ -412,7 +418,7 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
             budget = {"budget_ms": plain_ms, "inference_ms": prop_ms, "k_learned": 0,
                       "note": "the inference and q-scan alone exceed the budget"}
     mlp.destroy()
-    del feat
+    del feat, fbuf
     return {"variant": variant, "objective": objective, "inputs": 12 if variant == "as_written" else 16, "eps": eps,
             "train_samples": n_train, "stats_samples": n_stats,
             "setup_ms": {"features": feat_ms, "sample_statistics": sfeat_ms, "training": train_ms},
@@ -425,6 +431,7 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
             "sampling_time_ratio": tl_sampling / tp,
             "time_to_plain_error_ms": {"plain": plain_ms, "learned": t_equal,
                                        "ratio": t_equal / plain_ms,
+                                       "ratio_with_features": (t_equal + feat_ms + sfeat_ms) / plain_ms,
                                        "ratio_with_setup": (t_equal + setup_ms) / plain_ms,
                                        "ratio_with_weights_both": (t_equal + weights_ms) / (plain_ms + weights_ms)},
             "fixed_budget": budget}

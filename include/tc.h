@@ -320,12 +320,14 @@ tc_status tc_mlp_get_params(const tc_mlp* mlp, float* h_params);
 tc_status tc_mlp_set_params(tc_mlp* mlp, const float* h_params);
 
 /*
- * Per canonical edge e = (u, v, t), bf16 features (row stride 16; columns
- * 12..15 are set to zero here and filled by tc_sample_features), each log1p
- * of a count: 0 d1, 1 d3, 2 w_e (the anchor's windows, Claim 1),
+ * Per canonical edge e = (u, v, t) with w_e > 0, bf16 features (row stride
+ * 16; columns 12..15 are set to zero here and filled by tc_sample_features),
+ * each log1p of a count: 0 d1, 1 d3, 2 w_e (the anchor's windows, Claim 1),
  * 3..6 in- and out-degree of u, then of v, over [t - delta, t + delta],
  * 7 sigma_{u,v}[t - delta, t + delta], 8 sigma_{v,u}[t - delta, t + delta]
  * (Def. 3), 9 out-degree of u, 10 in-degree of v, 11 in-degree of u.
+ * The row of an edge with w_e = 0 is all zero: such an edge is never drawn
+ * and never an input of the network (tc_proposal_weights skips it).
  *   d_index  as filled by tc_path_weights for the same graph, motif, delta
  *   d_feat   uint16 (bf16 bits) [m][16] output
  */
@@ -341,7 +343,8 @@ tc_status tc_edge_features(const tc_graph* g, const tc_motif* motif, int64_t del
  * K2 = (u, b(t)), K3 = (v, b(t)) of an edge: n_K = the samples whose middle
  * edge has key K, s_K = the sum of their X^2, prior = sum X^2 / n_samples.
  * Columns: log1p((s_K + prior) / (n_K + 1)) for K1, K2, K3, then
- * log1p(n_K1), in bf16.  The other columns are left as they are.  Draw
+ * log1p(n_K1), in bf16, for the rows of edges with w_e > 0 (the other rows
+ * and columns are left as they are).  Draw
  * these samples disjoint from those tc_mlp_train uses (another seed or id
  * range), so that no training path sees its own outcome.  d_feat must be
  * 16-byte aligned.  Synchronises the stream.  Errors as tc_sample_estimate.
@@ -412,8 +415,11 @@ tc_status tc_mlp_train_ex(tc_mlp* mlp, const tc_graph* g, const tc_motif* motif,
 tc_status tc_proposal_index_bytes(const tc_graph* g, size_t* h_bytes);
 
 /*
- * Proposal weights: d_h[m] (uint16) = max(1, floor(scale (eps + g_e) + 1/2)),
- * d_qprefix[m+1] the exact prefix sum of w_e h_e (w_e from d_prefix), and the
+ * Proposal weights: d_h[m] (uint16) = max(1, floor(scale (eps + g_e) + 1/2))
+ * for every edge with w_e > 0, and 1 for an edge with w_e = 0 (it is never
+ * drawn, so the network is not evaluated on it: only the rows of edges with
+ * w_e > 0 of d_feat are read), d_qprefix[m+1] the exact prefix sum of
+ * w_e h_e (w_e from d_prefix), and the
  * proposal's sampling index d_qindex (tc_proposal_index_bytes, 256-byte
  * aligned).  scale >= 1, eps >= 0, scale (1 + eps) + 1 <= TC_PROPOSAL_MAX_H.
  * h_Q (optional) receives Q = d_qprefix[m] and reports overflow.

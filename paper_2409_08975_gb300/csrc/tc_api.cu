@@ -255,7 +255,7 @@ tc_status compile_plan_checked(const tc_motif* motif, Plan* p) { return plan_of(
 static void free_graph_arrays(tc_graph* g) {
   void* ps[] = {g->out_off, g->out_e,  g->perm,     g->in_off,  g->in_e,    g->in_eid,  g->pair_off, g->pair_dst,
                 g->pair_eoff, g->pair_t, g->pair_eid, g->pair_hash, g->out_t32, g->in_t32, g->pair_t32, g->x_in,
-                g->x_out, g->out2in};
+                g->x_out, g->out2in, g->r_in, g->r_out, g->r_o2i, g->r_self};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -657,7 +657,7 @@ tc_status tc_sample_features(const tc_graph* g, const tc_motif* motif, int64_t d
   if (s == TC_OK) err = (uint32_t*)(sums + 1);
   if (s == TC_OK && n_samples)
     s = launch_sampler(g, plan, delta, d_prefix, d_index, n_samples, seed, sample_offset, trace, sums, st);
-  if (s == TC_OK) s = launch_sample_features(g, trace, n_samples, delta, d_feat, err, st);
+  if (s == TC_OK) s = launch_sample_features(g, d_prefix, trace, n_samples, delta, d_feat, err, st);
   SampleSums hs;
   uint32_t herr = 0;
   std::memset(&hs, 0, sizeof(hs));

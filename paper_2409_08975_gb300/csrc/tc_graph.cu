@@ -577,32 +577,44 @@ __global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
 
 // Window-search anchors (delta-independent; see tc_graph::x_in).  For
 // canonical edge i = (u, v, t): x_in[i] = the first position of u's in-list
-// with time >= t.  For in-list position p of edge c = in_eid[p] = (u, v, t):
-// out2in[c] = p and x_out[c] = the first position of v's out-list with
-// time >= t.  The searches of consecutive threads run in the same list
-// (edges of one vertex in time order), so their probes share sectors.
+// with time >= t, with its range word r_in[i], and the range word r_self[i]
+// of i itself in u's out-list.  For in-list position p of edge c = in_eid[p]
+// = (u, v, t): out2in[c] = p with its range word r_o2i[c] in v's in-list, and
+// x_out[c] = the first position of v's out-list with time >= t, with r_out[c].
+// The searches of consecutive threads run in the same list (edges of one
+// vertex in time order), so their probes share sectors.
 template <bool Compact>
 __global__ void k_anchor_in(const OutEdge* __restrict__ out_e, const InEdge* __restrict__ in_e,
-                            const uint32_t* __restrict__ in_off, const uint32_t* __restrict__ in_t32, int64_t tmin,
-                            uint64_t m, uint32_t* __restrict__ x_in) {
+                            const uint32_t* __restrict__ in_off, const uint32_t* __restrict__ out_off,
+                            const uint32_t* __restrict__ in_t32, int64_t tmin, uint64_t m,
+                            uint32_t* __restrict__ x_in, uint32_t* __restrict__ r_in, uint32_t* __restrict__ r_self) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
     const OutEdge e = out_e[i];
     auto tt = [&](uint32_t p) -> int64_t { return Compact ? (int64_t)__ldg(in_t32 + p) + tmin : in_e[p].t; };
-    x_in[i] = search_time<true>(__ldg(in_off + e.src), __ldg(in_off + e.src + 1), e.t, tt);
+    const uint32_t s = __ldg(in_off + e.src), f = __ldg(in_off + e.src + 1);
+    const uint32_t a = search_time<true>(s, f, e.t, tt);
+    x_in[i] = a;
+    r_in[i] = range_word(a, s, f);
+    r_self[i] = range_word((uint32_t)i, __ldg(out_off + e.src), __ldg(out_off + e.src + 1));
   }
 }
 
 template <bool Compact>
 __global__ void k_anchor_out(const OutEdge* __restrict__ out_e, const InEdge* __restrict__ in_e,
                              const uint32_t* __restrict__ in_eid, const uint32_t* __restrict__ out_off,
-                             const uint32_t* __restrict__ out_t32, int64_t tmin, uint64_t m,
-                             uint32_t* __restrict__ x_out, uint32_t* __restrict__ out2in) {
+                             const uint32_t* __restrict__ in_off, const uint32_t* __restrict__ out_t32, int64_t tmin,
+                             uint64_t m, uint32_t* __restrict__ x_out, uint32_t* __restrict__ out2in,
+                             uint32_t* __restrict__ r_out, uint32_t* __restrict__ r_o2i) {
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
     const InEdge e = in_e[p];
     auto tt = [&](uint32_t q) -> int64_t { return Compact ? (int64_t)__ldg(out_t32 + q) + tmin : out_e[q].t; };
     const uint32_t c = in_eid[p];
-    x_out[c] = search_time<true>(__ldg(out_off + e.dst), __ldg(out_off + e.dst + 1), e.t, tt);
+    const uint32_t s = __ldg(out_off + e.dst), f = __ldg(out_off + e.dst + 1);
+    const uint32_t a = search_time<true>(s, f, e.t, tt);
+    x_out[c] = a;
+    r_out[c] = range_word(a, s, f);
     out2in[c] = (uint32_t)p;
+    r_o2i[c] = range_word((uint32_t)p, __ldg(in_off + e.dst), __ldg(in_off + e.dst + 1));
   }
 }
 
@@ -769,19 +781,25 @@ tc_status build_graph(int64_t n, int64_t m, const int32_t* d_src, const int32_t*
   TC_LAUNCHED(1);
   TRY_C(cudaGetLastError(), "k_offsets");
 
-  // window-search anchors of the weights (x_in, x_out, out2in)
+  // window-search anchors of the weights (x_in, x_out, out2in) and their range words
   TRY_S(dmalloc(&g->x_in, M, st));
   TRY_S(dmalloc(&g->x_out, M, st));
   TRY_S(dmalloc(&g->out2in, M, st));
+  TRY_S(dmalloc(&g->r_in, M, st));
+  TRY_S(dmalloc(&g->r_out, M, st));
+  TRY_S(dmalloc(&g->r_o2i, M, st));
+  TRY_S(dmalloc(&g->r_self, M, st));
   if (M) {
     if (g->in_t32) {
-      k_anchor_in<true><<<gr, 256, 0, st>>>(g->out_e, g->in_e, g->in_off, g->in_t32, g->tmin, M, g->x_in);
-      k_anchor_out<true><<<gr, 256, 0, st>>>(g->out_e, g->in_e, g->in_eid, g->out_off, g->out_t32, g->tmin, M,
-                                             g->x_out, g->out2in);
+      k_anchor_in<true><<<gr, 256, 0, st>>>(g->out_e, g->in_e, g->in_off, g->out_off, g->in_t32, g->tmin, M, g->x_in,
+                                            g->r_in, g->r_self);
+      k_anchor_out<true><<<gr, 256, 0, st>>>(g->out_e, g->in_e, g->in_eid, g->out_off, g->in_off, g->out_t32,
+                                             g->tmin, M, g->x_out, g->out2in, g->r_out, g->r_o2i);
     } else {
-      k_anchor_in<false><<<gr, 256, 0, st>>>(g->out_e, g->in_e, g->in_off, nullptr, 0, M, g->x_in);
-      k_anchor_out<false><<<gr, 256, 0, st>>>(g->out_e, g->in_e, g->in_eid, g->out_off, nullptr, 0, M, g->x_out,
-                                              g->out2in);
+      k_anchor_in<false><<<gr, 256, 0, st>>>(g->out_e, g->in_e, g->in_off, g->out_off, nullptr, 0, M, g->x_in,
+                                             g->r_in, g->r_self);
+      k_anchor_out<false><<<gr, 256, 0, st>>>(g->out_e, g->in_e, g->in_eid, g->out_off, g->in_off, nullptr, 0, M,
+                                              g->x_out, g->out2in, g->r_out, g->r_o2i);
     }
     TC_LAUNCHED(2);
     TRY_C(cudaGetLastError(), "k_anchor");

@@ -33,6 +33,16 @@ struct __align__(16) EdgeWin {
   uint32_t lo3, d3;  // window of e3: positions [lo3, lo3 + d3) of v's alpha3 list
 };
 
+// Range word of a position a of the list [s, f): (min(a - s, 0xFFFF) << 16)
+// | min(f - a, 0xFFFF).  A field below 0xFFFF is the exact distance; 0xFFFF
+// means at least that far (the search then reads the list's offsets).
+constexpr uint32_t kRangeCap = 0xFFFFu;
+__host__ __device__ __forceinline__ uint32_t range_word(uint32_t a, uint32_t s, uint32_t f) {
+  const uint32_t ls = a - s < kRangeCap ? a - s : kRangeCap;
+  const uint32_t lf = f - a < kRangeCap ? f - a : kRangeCap;
+  return (ls << 16) | lf;
+}
+
 // Slot of the pair hash table: the pair list L_{x,y} occupies positions
 // [begin, end) of pair_t.  Empty slots have x = y = 0xFFFFFFFF.
 struct __align__(16) PairSlot {
@@ -145,6 +155,13 @@ struct tc_graph {
   uint32_t* x_in;    // first position p in u's in-list with in_e[p].t >= t
   uint32_t* x_out;   // first position p in v's out-list with out_e[p].t >= t
   uint32_t* out2in;  // canonical position -> in-list position (inverse of in_eid)
+  // Range words of the anchors (tc::range_word): how far the anchor lies
+  // from the start and the end of its list, so that a window search needs
+  // no load of the list's offsets unless it runs beyond 65,534 entries.
+  uint32_t* r_in;    // x_in[e] in u's in-list
+  uint32_t* r_out;   // x_out[e] in v's out-list
+  uint32_t* r_o2i;   // out2in[e] in v's in-list
+  uint32_t* r_self;  // e itself in u's out-list
 };
 
 namespace tc {
@@ -358,8 +375,9 @@ int mlp_kernel(int kind);  // tc_mlp_kernel
 // Synchronises st, then reports (and clears) the error bits the network's
 // inference kernel left in the network's device error word.
 tc_status mlp_check_error(const tc_mlp* M, cudaStream_t st, const char* what);
-tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint64_t n, int64_t delta,
-                                 uint16_t* feat, uint32_t* d_err, cudaStream_t st);
+// Columns 12..15 of the rows of edges with w > 0 (prefix: the plain prefix).
+tc_status launch_sample_features(const tc_graph* g, const uint64_t* prefix, const uint64_t* trace, uint64_t n,
+                                 int64_t delta, uint16_t* feat, uint32_t* d_err, cudaStream_t st);
 tc_status launch_trace_to_rows(const uint64_t* trace, uint64_t n, uint32_t* rows, float* labels, cudaStream_t st,
                                bool clip = false);
 tc_status launch_clip_labels(const float* labels, uint64_t n, float* out, cudaStream_t st);

@@ -85,6 +85,11 @@ __global__ void __launch_bounds__(256) k_features(const OutEdge* __restrict__ ou
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
     const EdgeWin r = win[i];
+    uint4* dst = reinterpret_cast<uint4*>(feat + i * kF);
+    if ((uint64_t)r.d1 * (uint64_t)r.d3 == 0) {  // w = 0: never drawn, never an input of the network
+      dst[0] = dst[1] = make_uint4(0, 0, 0, 0);
+      continue;
+    }
     const OutEdge e = out_e[i];
     const int64_t lo = sat_sub(e.t, delta), hi = sat_add(e.t, delta);
     float c[kNFeat];
@@ -105,7 +110,6 @@ __global__ void __launch_bounds__(256) k_features(const OutEdge* __restrict__ ou
     for (int j = 0; j < kNFeat; j++) row[j] = __float2bfloat16_rn(log1pf(c[j]));
 #pragma unroll
     for (int j = kNFeat; j < kF; j++) row[j] = __float2bfloat16_rn(0.0f);
-    uint4* dst = reinterpret_cast<uint4*>(feat + i * kF);
     dst[0] = reinterpret_cast<const uint4*>(row)[0];
     dst[1] = reinterpret_cast<const uint4*>(row)[1];
   }
@@ -183,13 +187,15 @@ __global__ void __launch_bounds__(256) k_te_insert(const uint64_t* __restrict__ 
   if (bad) atomicOr(err, bad);
 }
 
-__global__ void __launch_bounds__(256) k_te_lookup(const OutEdge* __restrict__ out_e, uint64_t m, uint64_t n,
+__global__ void __launch_bounds__(256) k_te_lookup(const OutEdge* __restrict__ out_e,
+                                                   const uint64_t* __restrict__ prefix, uint64_t m, uint64_t n,
                                                    int64_t D, int64_t b0, TeTables T,
                                                    const unsigned long long* __restrict__ total,
                                                    __nv_bfloat16* __restrict__ feat) {
   const float prior = n ? (float)((double)*total / (double)n) : 0.f;  // FP32 below: the result is log1p'd to bf16
   const uint64_t mask = T.cap - 1;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (__ldg(prefix + i + 1) == __ldg(prefix + i)) continue;  // w = 0: the row stays as it is (zero)
     const OutEdge r = out_e[i];
     uint64_t k[3];
     te_keys(r.src, r.dst, r.t, D, b0, k);
@@ -482,19 +488,22 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ p
   }
 }
 
-// Proposal: for every canonical edge e, h_e = max(1, floor(scale (eps +
-// g_e) + 1/2)) with g_e = sigmoid(network logit of e's feature row), and
-// q_e = w_e h_e with w_e = prefix[e + 1] - prefix[e]; each tile's sum of q
-// is the first level of the reduce-then-scan that writes the q-prefix.
+// Proposal: for every canonical edge e with w_e > 0, h_e = max(1,
+// floor(scale (eps + g_e) + 1/2)) with g_e = sigmoid(network logit of e's
+// feature row), and q_e = w_e h_e with w_e = prefix[e + 1] - prefix[e]; an
+// edge with w_e = 0 is never drawn under any proposal, so it gets h_e = 1,
+// q_e = 0 and the network is not evaluated on it.  Each tile's sum of q is
+// the first level of the reduce-then-scan that writes the q-prefix.
 // Persistent blocks (the network is staged in shared memory and its
 // fragments in registers once per block) take tiles of kPTile edges in
-// turn; each warp runs its 16-row sub-tiles on the tensor cores with the
-// next sub-tile's feature fragments loaded ahead, while the tile's prefix
-// entries arrive in shared memory by cp.async; h and q are then formed and
-// written coalesced.
+// turn; the tile's prefix entries arrive in shared memory by cp.async, each
+// warp lists the rows of its share of the tile with w > 0 and runs them in
+// 16-row sub-tiles on the tensor cores (the next sub-tile's feature rows
+// loaded ahead), and h and q are then formed and written coalesced.
 constexpr int kPThreads = 128;
 constexpr int kPRowsPerWarp = 512;
 constexpr int kPTile = (kPThreads / 32) * kPRowsPerWarp;  // 2048 edges: the scan's tile
+constexpr size_t kPDynSmem = 2 * (kPTile + 2) * sizeof(unsigned long long);  // the two prefix buffers
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
@@ -517,9 +526,10 @@ __global__ void __launch_bounds__(kPThreads, TC_PROPOSAL_MIN_BLOCKS) k_proposal(
                                                                               uint64_t* __restrict__ tile_sums,
                                                                               uint32_t* __restrict__ hrange,
                                                                               uint32_t* __restrict__ d_err) {
+  extern __shared__ unsigned long long s_pre2[];  // two buffers of kPTile + 1 prefix entries (kPDynSmem)
   __shared__ MlpFwdShared net;
-  __shared__ unsigned long long s_pre[kPTile + 1];
   __shared__ float s_z[kPTile];
+  __shared__ uint16_t s_rows[kPThreads / 32][kPRowsPerWarp];  // a warp's rows with w > 0 (tile offsets)
   __shared__ unsigned long long s_warp[kPThreads / 32];
   __shared__ uint32_t s_err;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, g = lane >> 2, qd = lane & 3;
@@ -530,45 +540,76 @@ __global__ void __launch_bounds__(kPThreads, TC_PROPOSAL_MIN_BLOCKS) k_proposal(
   load_mlp_frags(net, F);
   const uint64_t T = (m + kPTile - 1) / kPTile;
   uint32_t err = 0, hlo = 0xFFFFFFFFu, hhi = 0;
+  // the prefix entries of a tile (and the next one's after it) arrive by cp.async
+  auto prefetch = [&](uint64_t tl, unsigned long long* dst) {
+    const uint64_t b = tl * kPTile;
+    const uint32_t n = (uint32_t)(m - b < (uint64_t)kPTile ? m - b : (uint64_t)kPTile);
+    for (uint32_t i = tid; i <= n; i += kPThreads) cp_async8(dst + i, prefix + b + i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int buf = 0;
+  if ((uint64_t)blockIdx.x < T) prefetch(blockIdx.x, s_pre2);
   for (uint64_t tile = blockIdx.x; tile < T; tile += gridDim.x) {
     const uint64_t base = tile * kPTile;
     const uint32_t rows = (uint32_t)(m - base < (uint64_t)kPTile ? m - base : (uint64_t)kPTile);
+    unsigned long long* s_pre = s_pre2 + buf * (kPTile + 2);
     __syncthreads();  // the previous tile's shared arrays are consumed
-    for (uint32_t i = tid; i <= rows; i += kPThreads) cp_async8(s_pre + i, prefix + base + i);
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (tile + gridDim.x < T) {
+      prefetch(tile + gridDim.x, s_pre2 + (buf ^ 1) * (kPTile + 2));
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+    buf ^= 1;
+    // this warp's rows with w > 0, in order
     const uint32_t r0 = (uint32_t)wid * kPRowsPerWarp;
+    uint32_t nz = 0;
+    for (uint32_t r = 0; r < kPRowsPerWarp; r += 32) {
+      const uint32_t row = r0 + r + lane;
+      const bool live = row < rows && s_pre[row + 1] != s_pre[row];
+      const uint32_t mask = __ballot_sync(0xffffffffu, live);
+      if (live) s_rows[wid][nz + __popc(mask & ((1u << lane) - 1u))] = (uint16_t)row;
+      nz += __popc(mask);
+    }
+    __syncwarp();
     auto fetch = [&](uint32_t sub, uint32_t (&x)[4]) {
-      const uint32_t ra = r0 + sub * 16 + g, rb = ra + 8;
-      load_rows(feat, ra < rows ? (int64_t)(base + ra) : -1, rb < rows ? (int64_t)(base + rb) : -1, x);
+      const uint32_t ia = sub * 16 + g, ib = ia + 8;
+      load_rows(feat, ia < nz ? (int64_t)(base + s_rows[wid][ia]) : -1,
+                ib < nz ? (int64_t)(base + s_rows[wid][ib]) : -1, x);
     };
+    const uint32_t subs = (nz + 15) / 16;
     uint32_t xn[4];
-    fetch(0, xn);
+    if (subs) fetch(0, xn);
 #pragma unroll 1
-    for (uint32_t sub = 0; sub < kPRowsPerWarp / 16; sub++) {
+    for (uint32_t sub = 0; sub < subs; sub++) {
       uint32_t x[4] = {xn[0], xn[1], xn[2], xn[3]};
-      if (sub + 1 < kPRowsPerWarp / 16) fetch(sub + 1, xn);
+      if (sub + 1 < subs) fetch(sub + 1, xn);
       float za, zb;
       tile_logits(net, F, x, &za, &zb);
+      const uint32_t ia = sub * 16 + g, ib = ia + 8;
       if (qd == 0) {
-        s_z[r0 + sub * 16 + g] = za;
-        s_z[r0 + sub * 16 + g + 8] = zb;
+        if (ia < nz) s_z[s_rows[wid][ia]] = za;
+        if (ib < nz) s_z[s_rows[wid][ib]] = zb;
       }
     }
-    cp_async_wait_all();
     __syncthreads();
     unsigned long long sum = 0;
     for (uint32_t r = tid; r < rows; r += kPThreads) {
-      const float v = floorf(scale * (eps + sigmoidf_(s_z[r])) + 0.5f);
-      const uint32_t hv = v < 1.f ? 1u : (uint32_t)v;
       const unsigned long long wv = s_pre[r + 1] - s_pre[r];
+      uint32_t hv = 1;  // w = 0: never drawn, the network was not run on it
+      if (wv) {
+        const float v = floorf(scale * (eps + sigmoidf_(s_z[r])) + 0.5f);
+        hv = v < 1.f ? 1u : (uint32_t)v;
+        hlo = hv < hlo ? hv : hlo;
+        hhi = hv > hhi ? hv : hhi;
+      }
       if (__umul64hi(wv, hv)) err |= kErrOverflow;
       const unsigned long long qv = wv * hv;
       q[base + r] = qv;
       h[base + r] = (uint16_t)hv;
       if (sum + qv < sum) err |= kErrOverflow;
       sum += qv;
-      hlo = hv < hlo ? hv : hlo;
-      hhi = hv > hhi ? hv : hhi;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -587,7 +628,7 @@ __global__ void __launch_bounds__(kPThreads, TC_PROPOSAL_MIN_BLOCKS) k_proposal(
       tile_sums[tile] = t;
     }
   }
-  // the proposal's range of h, for the sampler's per-block bins
+  // the proposal's range of h over the edges with w > 0, for the sampler's per-block bins
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     hlo = min(hlo, __shfl_xor_sync(0xffffffffu, hlo, o));
@@ -832,17 +873,20 @@ __global__ void __launch_bounds__(kUmmaM, 4) k_mlp_umma(const float* __restrict_
         if (!Proposal) {
           logits[row] = z;
         } else {
-          const float fv = floorf(scale * (eps + sigmoidf_(z)) + 0.5f);
-          const uint32_t hv = fv < 1.f ? 1u : (uint32_t)fv;
           const unsigned long long wv = __ldg(prefix + row + 1) - __ldg(prefix + row);
+          uint32_t hv = 1;  // an edge with w = 0 is never drawn: h = 1, q = 0 (as k_proposal)
+          if (wv) {
+            const float fv = floorf(scale * (eps + sigmoidf_(z)) + 0.5f);
+            hv = fv < 1.f ? 1u : (uint32_t)fv;
+            hlo = hv < hlo ? hv : hlo;
+            hhi = hv > hhi ? hv : hhi;
+          }
           if (__umul64hi(wv, hv)) err |= kErrOverflow;
           const unsigned long long qv = wv * hv;
           q[row] = qv;
           h[row] = (uint16_t)hv;
           if (tsum + qv < tsum) err |= kErrOverflow;
           tsum += qv;
-          hlo = hv < hlo ? hv : hlo;
-          hhi = hv > hhi ? hv : hhi;
         }
       }
     }
@@ -1207,8 +1251,8 @@ tc_status launch_features(const tc_graph* g, const EdgeWin* win, int64_t delta, 
   return TC_OK;
 }
 
-tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint64_t n, int64_t delta,
-                                 uint16_t* feat, uint32_t* d_err, cudaStream_t st) {
+tc_status launch_sample_features(const tc_graph* g, const uint64_t* prefix, const uint64_t* trace, uint64_t n,
+                                 int64_t delta, uint16_t* feat, uint32_t* d_err, cudaStream_t st) {
   const uint64_t m = (uint64_t)g->m;
   if (!m) return TC_OK;
   const int64_t D = delta > 0 ? delta : 1;
@@ -1235,7 +1279,7 @@ tc_status launch_sample_features(const tc_graph* g, const uint64_t* trace, uint6
     if (e != cudaSuccess) s = cuda_status(e, "k_te_insert");
   }
   if (s == TC_OK) {
-    k_te_lookup<<<grid_cap(m, 256), 256, 0, st>>>(g->out_e, m, n, D, b0, T, total,
+    k_te_lookup<<<grid_cap(m, 256), 256, 0, st>>>(g->out_e, prefix, m, n, D, b0, T, total,
                                                    reinterpret_cast<__nv_bfloat16*>(feat));
     TC_LAUNCHED(1);
     e = cudaGetLastError();
@@ -1401,13 +1445,14 @@ tc_status launch_proposal_scan(const tc_mlp* M, const uint16_t* feat, const uint
   }
   static int bps = 0;
   if (!bps) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_proposal, kPThreads, 0);
+    TC_CUDA(cudaFuncSetAttribute(k_proposal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPDynSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_proposal, kPThreads, kPDynSmem);
     if (bps <= 0) bps = 1;
   }
   uint64_t blocks = (uint64_t)num_sms() * bps;
   if (blocks > T) blocks = T;
-  k_proposal<<<(unsigned)blocks, kPThreads, 0, st>>>(M->params, reinterpret_cast<const __nv_bfloat16*>(feat), prefix,
-                                                     m, eps, scale, h, q, sums, hrange, d_err);
+  k_proposal<<<(unsigned)blocks, kPThreads, kPDynSmem, st>>>(M->params, reinterpret_cast<const __nv_bfloat16*>(feat),
+                                                             prefix, m, eps, scale, h, q, sums, hrange, d_err);
   TC_LAUNCHED(1);
   TC_CUDA(cudaGetLastError());
   return scan_u64_from_tile_sums(q, qprefix, m, sums, d_err, scan_scratch, scan_u64_scratch_words(T) + 1, st);

@@ -20,8 +20,11 @@ namespace tc {
 // window bound is found by a galloping search (doubling steps, then
 // bisection) from a position where the list reaches time t, so a window of
 // d entries costs O(log d) probes near the anchor instead of O(log deg)
-// probes over the whole list.  The u side of consecutive edges (one source
-// vertex in time order) searches the same list at increasing positions.
+// probes over the whole list.  The anchors' range words give the list's
+// bounds (no random load of the destination's offsets), and an exact anchor
+// (the list's lower bound of t) is itself the window's bound at t in strict
+// mode.  The u side of consecutive edges (one source vertex in time order)
+// searches the same list at increasing positions.
 //
 // The weights pass also sums w over each tile of kWTile edges, the first
 // level of the reduce-then-scan that writes the prefix (so w is read once
@@ -120,6 +123,10 @@ struct WeightsArgs {
   const uint32_t* x_in;
   const uint32_t* x_out;
   const uint32_t* out2in;
+  const uint32_t* r_in;    // range words of x_in, x_out, out2in and of the edge in u's out-list
+  const uint32_t* r_out;
+  const uint32_t* r_o2i;
+  const uint32_t* r_self;
   int64_t tmin;
   uint64_t m;
   int64_t delta;
@@ -201,6 +208,83 @@ __global__ void __launch_bounds__(kWThreads, TC_WEIGHTS_MIN_BLOCKS) k_weights(co
   }
 }
 
+// Window of one side on the 32-bit list times, searched from anchor a: the
+// list [s, f) from the anchor's range word rw (the offsets of x's list are
+// read only where a field is saturated).  exact: a is the list's lower bound
+// of t (x_in, x_out), so "time >= t" needs no probe.
+__device__ __forceinline__ void side_window_rw(const WeightsArgs& A, int alpha, int beta, int32_t x, uint32_t a,
+                                               uint32_t rw, bool exact, int64_t t, uint32_t* lo, uint32_t* hi) {
+  const uint32_t* off = alpha < 0 ? A.in_off : A.out_off;
+  uint32_t s = a - (rw >> 16), f = a + (rw & 0xFFFFu);
+  if ((rw >> 16) == kRangeCap) s = __ldg(off + x);
+  if ((rw & 0xFFFFu) == kRangeCap) f = __ldg(off + x + 1);
+  const uint32_t* t32 = alpha < 0 ? A.in_t32 : A.out_t32;
+  auto tt = [&](uint32_t p) -> int64_t { return (int64_t)__ldg(t32 + p) + A.tmin; };
+  if (beta < 0) {
+    *hi = (exact && !A.closed) ? a : (A.closed ? gallop<true>(s, f, a, t, tt) : gallop<false>(s, f, a, t, tt));
+    *lo = gallop<false>(s, f, *hi, sat_sub(t, A.delta), tt);
+  } else {
+    *lo = (exact && A.closed) ? a : (A.closed ? gallop<false>(s, f, a, t, tt) : gallop<true>(s, f, a, t, tt));
+    *hi = gallop<true>(s, f, *lo, sat_add(t, A.delta), tt);
+  }
+}
+
+// Block b takes tile b (coalesced: edge b kWTile + j 256 + thread) on the
+// 32-bit list times: the list bounds from the anchors' range words (the
+// offsets are read only where a word is saturated), an exact anchor's
+// bound without a probe, the windows and w written with streaming stores,
+// and the tile's sum of w.
+__global__ void __launch_bounds__(kWThreads, TC_WEIGHTS_MIN_BLOCKS) k_weights_rw(const __grid_constant__ WeightsArgs A) {
+  __shared__ unsigned long long s_warp[kWThreads / 32];
+  __shared__ uint32_t s_ovf;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_ovf = 0;
+  const uint64_t base = (uint64_t)blockIdx.x * kWTile;
+  unsigned long long sum = 0;
+  bool ovf = false;
+#pragma unroll 1
+  for (int j = 0; j < kWItems; j++) {
+    const uint64_t i = base + (uint64_t)j * kWThreads + tid;
+    if (i >= A.m) break;
+    const OutEdge e = A.out_e[i];
+    uint32_t lo1 = 0, hi1 = 1, lo3 = 0, hi3 = 1;
+    // anchors: u's in-list (x_in, exact) or the edge itself in u's out-list;
+    // the edge itself in v's in-list (out2in) or v's out-list (x_out, exact)
+    if (A.alpha1 < 0)
+      side_window_rw(A, -1, A.beta1, e.src, __ldg(A.x_in + i), __ldg(A.r_in + i), true, e.t, &lo1, &hi1);
+    else if (A.alpha1 > 0)
+      side_window_rw(A, 1, A.beta1, e.src, (uint32_t)i, __ldg(A.r_self + i), false, e.t, &lo1, &hi1);
+    if (A.alpha3 < 0)
+      side_window_rw(A, -1, A.beta3, e.dst, __ldg(A.out2in + i), __ldg(A.r_o2i + i), false, e.t, &lo3, &hi3);
+    else if (A.alpha3 > 0)
+      side_window_rw(A, 1, A.beta3, e.dst, __ldg(A.x_out + i), __ldg(A.r_out + i), true, e.t, &lo3, &hi3);
+    __stcs(reinterpret_cast<uint4*>(A.win + i), make_uint4(lo1, hi1 - lo1, lo3, hi3 - lo3));
+    const unsigned long long wv = (unsigned long long)(hi1 - lo1) * (unsigned long long)(hi3 - lo3);
+    __stcs(reinterpret_cast<unsigned long long*>(A.w + i), wv);
+    if (sum + wv < sum) ovf = true;
+    sum += wv;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, sum, o);
+    if (sum + y < sum) ovf = true;
+    sum += y;
+  }
+  if (lane == 0) s_warp[wid] = sum;
+  if (ovf) s_ovf = 1;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long t = 0;
+    bool o2 = s_ovf != 0;
+    for (int v = 0; v < kWThreads / 32; v++) {
+      if (t + s_warp[v] < t) o2 = true;
+      t += s_warp[v];
+    }
+    A.tile_sums[blockIdx.x] = t;
+    if (o2) atomicOr(A.err, kErrOverflow);
+  }
+}
+
 static uint64_t weights_tiles(uint64_t m) { return (m + kWTile - 1) / kWTile; }
 
 // Scratch of launch_weights_scan: w (unless the caller keeps it), the tile
@@ -235,6 +319,10 @@ tc_status launch_weights_scan(const tc_graph* g, const Plan& plan, int64_t delta
   A.x_in = g->x_in;
   A.x_out = g->x_out;
   A.out2in = g->out2in;
+  A.r_in = g->r_in;
+  A.r_out = g->r_out;
+  A.r_o2i = g->r_o2i;
+  A.r_self = g->r_self;
   A.tmin = g->tmin;
   A.m = m;
   A.delta = delta;
@@ -249,7 +337,7 @@ tc_status launch_weights_scan(const tc_graph* g, const Plan& plan, int64_t delta
   A.err = d_err;
   const bool compact = TC_COMPACT_TIMES && g->out_t32 && g->in_t32;
   if (compact)
-    k_weights<true><<<(unsigned)T, kWThreads, 0, st>>>(A);
+    k_weights_rw<<<(unsigned)T, kWThreads, 0, st>>>(A);
   else
     k_weights<false><<<(unsigned)T, kWThreads, 0, st>>>(A);
   TC_LAUNCHED(1);

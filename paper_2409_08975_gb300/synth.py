@@ -221,6 +221,17 @@ def large(seed=1005):
     return g
 
 
+def large_small(seed=1105):
+    """Profiling case of the large graph's kernels: the same generator
+    (Zipf(1.8) pair multiplicities, daily periodicity) at n = 1e7, m = 3e7,
+    top degree about 1e5 (graph and indexes about 3 GB, many times L2),
+    directed 4-cycle, delta = 3600, k = 3e7."""
+    g = chung_lu(10_000_000, 30_000_000, gamma=2.1, max_deg=1e5, seed=seed, daily=True, zipf_repeats=1.8)
+    g.update({"name": "large_small", "motif": C4, "motifs": {"c4": C4, "path_chord": PATH_CHORD}, "delta": 3600,
+              "k": 30_000_000})
+    return g
+
+
 BATCH_DELTAS = (600, 3600, 86400)
 
 
@@ -295,4 +306,5 @@ def batch_small(seed=1008):
 
 
 CONFIGS = {"tiny": tiny, "mid": mid, "learned": learned, "large": large, "batch": batch, "small": small,
+           "large_small": large_small,
            "batch_small": batch_small}

@@ -411,9 +411,15 @@ class MLP:
         _check(lib().tc_mlp_set_params(self.handle, arr.ctypes.data_as(ctypes.c_void_p)), "tc_mlp_set_params")
 
 
-def tc_edge_features(g, motif, delta, weights, stream=None):
-    """bf16 feature rows [m, 16] (returned as a torch.bfloat16 CUDA tensor)."""
-    feat = torch.zeros((max(g.m, 1), FEATURE_STRIDE), dtype=torch.int16, device="cuda")
+def alloc_features(g):
+    """A zeroed feature buffer for tc_edge_features (int16 [m, 16], the bf16 bits)."""
+    return torch.zeros((max(g.m, 1), FEATURE_STRIDE), dtype=torch.int16, device="cuda")
+
+
+def tc_edge_features(g, motif, delta, weights, out=None, stream=None):
+    """bf16 feature rows [m, 16] (returned as a torch.bfloat16 CUDA tensor),
+    into out (from alloc_features) when given."""
+    feat = alloc_features(g) if out is None else out
     _check(lib().tc_edge_features(g.handle, ctypes.byref(motif), int(delta), _ptr(weights.index), _ptr(feat),
                                   _stream(stream)), "tc_edge_features")
     return feat[:g.m].view(torch.bfloat16)

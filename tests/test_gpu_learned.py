@@ -65,6 +65,11 @@ def test_features_within_one_bf16_step(tc):
     exp = L.features_bf16(L.edge_features(og, plan, 3600))
     assert got.shape == exp.shape
     assert (got[:, 12:] == 0).all()
+    # an edge with w = 0 is never drawn: its row is zero; the others are the oracle's
+    live = oracle.path_weights(og, plan, 3600)["w"] > 0
+    assert live.any() and not live.all()
+    assert (got[~live] == 0).all()
+    got, exp = got[live], exp[live]
     diff = np.abs(got - exp)
     step = np.maximum(np.abs(exp), 1e-30) * 2.0 ** -7
     assert (diff <= step).all()
@@ -80,8 +85,12 @@ def test_sample_features_match_oracle(tc):
     tc.tc_sample_features(g, mot, 3600, w, feat, 50_000, seed=11, offset=3)
     got = _f32(feat)
     assert (got[:, :12] == before).all()
-    pre = oracle.prefix_sum(oracle.path_weights(og, plan, 3600)["w"])
+    ow = oracle.path_weights(og, plan, 3600)["w"]
+    pre = oracle.prefix_sum(ow)
     exp = L.features_bf16(L.edge_features(og, plan, 3600), L.sample_features(og, plan, 3600, pre, 50_000, 11, 3))
+    live = ow > 0
+    assert (got[~live] == 0).all()  # rows of edges that are never drawn stay zero
+    got, exp = got[live], exp[live]
     diff = np.abs(got[:, 12:] - exp[:, 12:])
     step = np.maximum(np.abs(exp[:, 12:]), 1e-30) * 2.0 ** -7
     assert (diff <= step).all()
@@ -177,8 +186,11 @@ def test_proposal_prefix_and_sampler_bit_exact(tc):
     mlp, _, _ = _trained(tc, setup, 200_000)
     prop = tc.tc_proposal_weights(mlp, g, mot, 3600, w, feat)
     h = prop.h.cpu().numpy().view(np.uint16)
-    assert h.min() >= 51 and h.max() <= 1075       # eps = 0.05, scale = 1024
     ow = oracle.path_weights(og, plan, 3600)["w"]
+    live = ow > 0
+    assert live.any() and not live.all()
+    assert h[live].min() >= 51 and h[live].max() <= 1075   # eps = 0.05, scale = 1024
+    assert (h[~live] == 1).all()                            # never drawn: the network is not run on them
     qpre = L.qprefix(ow, h)
     assert prop.Q == int(qpre[-1])
     assert (prop.qprefix.cpu().numpy().view(np.uint64) == qpre).all()
