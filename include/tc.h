@@ -541,8 +541,8 @@ float tc_last_phase_ms(int32_t phase);
  * 1 = tcgen05 MMAs into TMEM accumulators issued by one thread per block;
  * kind < 0 only queries.  Both compute the same network in the same
  * precisions (bf16 operands, FP32 accumulation); sums may differ in
- * rounding order.  The default is the build's TC_MLP_TCGEN05, overridden by
- * the environment variable of the same name ("0" or "1").  Returns the kind
+ * rounding order.  The default is the build's TC_MLP_TCGEN05 (1: tcgen05),
+ * overridden by the environment variable of the same name ("0" or "1").  Returns the kind
  * in effect after the call; -1 for an unknown kind (nothing changes). */
 int32_t tc_mlp_kernel(int32_t kind);
 

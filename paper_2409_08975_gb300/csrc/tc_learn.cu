@@ -720,12 +720,17 @@ struct alignas(1024) UmmaShared {
   __nv_bfloat16 B1[kH * kF];      // W1 [n][k]
   __nv_bfloat16 A2[kUmmaM * kH];  // layer-1 activations
   __nv_bfloat16 B2[kH * kH];      // W2 [n][k]
-  float b1[kH], b2[kH], W3[kH];   // W3 as bf16 values held in FP32
+  alignas(16) float b1[kH];
+  alignas(16) float b2[kH];
+  alignas(16) float W3[kH];        // W3 as bf16 values held in FP32
   float b3;
   uint64_t mbar;
   uint32_t tmem;
   uint32_t err;
   unsigned long long red[4];
+  uint32_t wcnt[4];                          // rows with w > 0 in each warp's quarter of the tile
+  unsigned long long pre[16 * kUmmaM + 1];   // the tile's prefix entries (proposal)
+  uint16_t live[16 * kUmmaM];                // the tile's rows with w > 0, in order (proposal)
 };
 // At least 30 KB of shared memory per block, so that at most seven blocks
 // share an SM (8 x 31 KB exceeds the SM's 228 KB): their TMEM (kTmemCols
@@ -733,8 +738,10 @@ struct alignas(1024) UmmaShared {
 constexpr size_t kUmmaSmemBytes =
     sizeof(UmmaShared) + 1024 > 30 * 1024 ? sizeof(UmmaShared) + 1024 : 30 * 1024;
 static_assert(7 * kTmemCols <= 512, "TMEM of the blocks one SM can hold");
+static_assert(kUmmaSmemBytes * 4 <= 227 * 1024, "four blocks per SM");
 constexpr int kUmmaSubTiles = 16;                         // 128-row sub-tiles per tile
 constexpr uint64_t kUmmaTile = kUmmaSubTiles * kUmmaM;     // 2048 rows: the scan's tile
+constexpr int kUmmaBlocksPerSm = 4;                        // resident blocks (launch bounds, shared memory)
 constexpr uint64_t kUmmaWaitNs = 1000000000ull;            // bound of each completion wait: 1 s
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -754,11 +761,14 @@ __device__ __forceinline__ bool umma_wait(uint64_t* mbar, uint32_t parity) {
   return true;
 }
 
-// Proposal: for the rows of the tiles this block takes (rows[i] or i index
-// the feature rows), the logits (Proposal = false: into logits) or h, q = w h
-// and each 2048-row tile's sum of q (Proposal = true), as k_proposal does.
+// For the rows of the tiles this block takes (rows[i] or i index the
+// feature rows), the logits (Proposal = false: into logits), or (Proposal =
+// true) h, q = w h and each 2048-row tile's sum of q as k_proposal computes
+// them: the tile's prefix entries are staged in shared memory, the rows with
+// w > 0 listed in order, and only those go through the network, 128 to a
+// sub-tile (rows with w = 0 get h = 1, q = 0).
 template <bool Proposal>
-__global__ void __launch_bounds__(kUmmaM, 4) k_mlp_umma(const float* __restrict__ params,
+__global__ void __launch_bounds__(kUmmaM, kUmmaBlocksPerSm) k_mlp_umma(const float* __restrict__ params,
                                                       const __nv_bfloat16* __restrict__ feat,
                                                       const uint32_t* __restrict__ rows, uint64_t n,
                                                       float* __restrict__ logits, const uint64_t* __restrict__ prefix,
@@ -802,12 +812,42 @@ __global__ void __launch_bounds__(kUmmaM, 4) k_mlp_umma(const float* __restrict_
   bool ok = true;
   const uint64_t T = (n + kUmmaTile - 1) / kUmmaTile;
   for (uint64_t tile = blockIdx.x; tile < T && ok; tile += gridDim.x) {
+    const uint64_t base = tile * kUmmaTile;
+    const uint32_t trows = (uint32_t)(n - base < kUmmaTile ? n - base : kUmmaTile);
+    // the rows that go through the network: every row of the tile (logits),
+    // or the rows with w > 0, listed in order (proposal)
+    uint32_t nrun = trows;
+    if (Proposal) {
+      __syncthreads();  // the previous tile's lists are consumed
+      for (uint32_t i = tid; i <= trows; i += kUmmaM) S.pre[i] = __ldg(prefix + base + i);
+      __syncthreads();
+      const uint32_t q0 = (uint32_t)warp * (kUmmaTile / 4);  // this warp's quarter of the tile
+      uint32_t cnt = 0;
+      for (uint32_t r = 0; r < kUmmaTile / 4; r += 32) {
+        const uint32_t row = q0 + r + lane;
+        const bool live = row < trows && S.pre[row + 1] != S.pre[row];
+        cnt += __popc(__ballot_sync(0xffffffffu, live));
+      }
+      if (lane == 0) S.wcnt[warp] = cnt;
+      __syncthreads();
+      uint32_t at = 0;
+      for (int v = 0; v < warp; v++) at += S.wcnt[v];
+      for (uint32_t r = 0; r < kUmmaTile / 4; r += 32) {
+        const uint32_t row = q0 + r + lane;
+        const bool live = row < trows && S.pre[row + 1] != S.pre[row];
+        const uint32_t mask = __ballot_sync(0xffffffffu, live);
+        if (live) S.live[at + __popc(mask & ((1u << lane) - 1u))] = (uint16_t)row;
+        at += __popc(mask);
+      }
+      nrun = S.wcnt[0] + S.wcnt[1] + S.wcnt[2] + S.wcnt[3];
+      __syncthreads();
+    }
     unsigned long long tsum = 0;
-    for (int sub = 0; sub < kUmmaSubTiles && ok; sub++) {
-      const uint64_t r0 = tile * kUmmaTile + (uint64_t)sub * kUmmaM;
-      if (r0 >= n) break;  // the same for the whole block
-      const uint64_t row = r0 + tid;
-      const bool valid = row < n;
+    for (uint32_t r0 = 0; r0 < nrun && ok; r0 += kUmmaM) {  // 128-row sub-tiles
+      const uint32_t idx = r0 + tid;
+      const bool valid = idx < nrun;
+      const uint32_t local = Proposal ? (valid ? (uint32_t)S.live[idx] : 0u) : idx;
+      const uint64_t row = base + local;
       uint4 xlo = make_uint4(0, 0, 0, 0), xhi = xlo;
       if (valid) {
         const uint4* src = reinterpret_cast<const uint4*>(feat + (uint64_t)(rows ? rows[row] : row) * kF);
@@ -833,10 +873,13 @@ __global__ void __launch_bounds__(kUmmaM, 4) k_mlp_umma(const float* __restrict_
       for (int c = 0; c < 4; c++) {  // bias, ReLU, bf16: the A operand of layer 2
         float v[16];
         tmem_ld16(tmem + lane_addr + (uint32_t)(c * 16), v);
+        float b[16];  // the bias as four 16-byte shared loads
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+          *reinterpret_cast<float4*>(b + 4 * j) = reinterpret_cast<const float4*>(S.b1)[c * 4 + j];
         uint32_t pk[8];
 #pragma unroll
-        for (int j = 0; j < 8; j++)
-          pk[j] = relu_bf16x2(v[2 * j] + S.b1[c * 16 + 2 * j], v[2 * j + 1] + S.b1[c * 16 + 2 * j + 1]);
+        for (int j = 0; j < 8; j++) pk[j] = relu_bf16x2(v[2 * j] + b[2 * j], v[2 * j + 1] + b[2 * j + 1]);
         char* dst = reinterpret_cast<char*>(S.A2);
         *reinterpret_cast<uint4*>(dst + umma_offset(tid, c * 16, kH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         *reinterpret_cast<uint4*>(dst + umma_offset(tid, c * 16 + 8, kH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
@@ -860,12 +903,18 @@ __global__ void __launch_bounds__(kUmmaM, 4) k_mlp_umma(const float* __restrict_
       float z = S.b3;  // layer 3 in FP32 on the bf16-rounded activations
 #pragma unroll
       for (int c = 0; c < 4; c++) {
-        float v[16];
+        float v[16], b[16], w3[16];
         tmem_ld16(tmem + lane_addr + (uint32_t)(c * 16), v);
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-          const float a = __bfloat162float(__float2bfloat16_rn(fmaxf(v[j] + S.b2[c * 16 + j], 0.f)));
-          z = fmaf(a, S.W3[c * 16 + j], z);
+        for (int j = 0; j < 4; j++) {
+          *reinterpret_cast<float4*>(b + 4 * j) = reinterpret_cast<const float4*>(S.b2)[c * 4 + j];
+          *reinterpret_cast<float4*>(w3 + 4 * j) = reinterpret_cast<const float4*>(S.W3)[c * 4 + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {  // ReLU and bf16 rounding of a pair in one instruction, then widened
+          const uint32_t pk = relu_bf16x2(v[2 * j] + b[2 * j], v[2 * j + 1] + b[2 * j + 1]);
+          z = fmaf(__uint_as_float(pk << 16), w3[2 * j], z);
+          z = fmaf(__uint_as_float(pk & 0xFFFF0000u), w3[2 * j + 1], z);
         }
       }
       tc05_fence_before();  // the next sub-tile's MMAs overwrite D1, D2 after the next barrier
@@ -873,14 +922,11 @@ __global__ void __launch_bounds__(kUmmaM, 4) k_mlp_umma(const float* __restrict_
         if (!Proposal) {
           logits[row] = z;
         } else {
-          const unsigned long long wv = __ldg(prefix + row + 1) - __ldg(prefix + row);
-          uint32_t hv = 1;  // an edge with w = 0 is never drawn: h = 1, q = 0 (as k_proposal)
-          if (wv) {
-            const float fv = floorf(scale * (eps + sigmoidf_(z)) + 0.5f);
-            hv = fv < 1.f ? 1u : (uint32_t)fv;
-            hlo = hv < hlo ? hv : hlo;
-            hhi = hv > hhi ? hv : hhi;
-          }
+          const unsigned long long wv = S.pre[local + 1] - S.pre[local];  // > 0: a listed row
+          const float fv = floorf(scale * (eps + sigmoidf_(z)) + 0.5f);
+          const uint32_t hv = fv < 1.f ? 1u : (uint32_t)fv;
+          hlo = hv < hlo ? hv : hlo;
+          hhi = hv > hhi ? hv : hhi;
           if (__umul64hi(wv, hv)) err |= kErrOverflow;
           const unsigned long long qv = wv * hv;
           q[row] = qv;
@@ -890,7 +936,14 @@ __global__ void __launch_bounds__(kUmmaM, 4) k_mlp_umma(const float* __restrict_
         }
       }
     }
-    if (Proposal && ok) {  // the tile's sum of q
+    if (Proposal && ok) {
+      // rows with w = 0 are never drawn: h = 1, q = 0 (as k_proposal)
+      for (uint32_t r = tid; r < trows; r += kUmmaM)
+        if (S.pre[r + 1] == S.pre[r]) {
+          q[base + r] = 0;
+          h[base + r] = 1;
+        }
+      // the tile's sum of q
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, tsum, o);
@@ -1294,7 +1347,7 @@ tc_status launch_sample_features(const tc_graph* g, const uint64_t* prefix, cons
 // default is TC_MLP_TCGEN05; the environment variable of the same name
 // ("0" or "1") overrides it.
 #ifndef TC_MLP_TCGEN05
-#define TC_MLP_TCGEN05 0
+#define TC_MLP_TCGEN05 1
 #endif
 static int g_mlp_kernel = -1;
 static bool use_tcgen05() {
@@ -1321,13 +1374,10 @@ static tc_status launch_umma(const tc_mlp* M, const uint16_t* feat, const uint32
                                  (int)kUmmaSmemBytes));
     attr = true;
   }
-  static int bps = 0;
-  if (!bps) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_mlp_umma<Proposal>, kUmmaM, kUmmaSmemBytes);
-    if (bps <= 0) bps = 1;
-  }
+  // kUmmaBlocksPerSm blocks per SM: what the launch bounds' registers and the
+  // shared memory allow (their TMEM, 64 columns each, fits an SM's 512)
   const uint64_t T = (n + kUmmaTile - 1) / kUmmaTile;
-  uint64_t blocks = (uint64_t)num_sms() * bps;
+  uint64_t blocks = (uint64_t)num_sms() * kUmmaBlocksPerSm;
   if (blocks > T) blocks = T;
   k_mlp_umma<Proposal><<<(unsigned)blocks, kUmmaM, kUmmaSmemBytes, st>>>(
       M->params, reinterpret_cast<const __nv_bfloat16*>(feat), rows, n, logits, prefix, eps, scale, h, q, tile_sums,
