@@ -47,10 +47,12 @@ MOTIFS = {  # name -> edges in time-rank order
 }
 MOTIF_NAMES = {str(v): k for k, v in MOTIFS.items()}
 # DRAM bytes (read + write) per unit of a kernel, from one ncu capture of the
-# benchmark's own launches (dram__bytes_read.sum + dram__bytes_write.sum);
-# valid while the kernel is unchanged, null for workloads not captured
-SAMPLER_TRAFFIC_PER_SAMPLE = {}
-WEIGHTS_TRAFFIC_PER_EDGE = {}
+# benchmark's own launches (dram__bytes_read.sum + dram__bytes_write.sum, one
+# pass over the default workload's list build and five steps: the launch list
+# summarised in profiles/launch_list_large_bench.md); valid while the kernel
+# is unchanged, null for workloads not captured
+SAMPLER_TRAFFIC_PER_SAMPLE = {("large", "c4"): 73.33}   # k_sample
+WEIGHTS_TRAFFIC_PER_EDGE = {("large", "c4"): 83.13}     # k_weights_rw
 UNIT = "samples/s"
 SECTOR = 32
 LEARNED_VARIANTS = ("closure", "variance", "as_written")
@@ -375,7 +377,10 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
         guide_ms.append(tc.tc_last_phase_ms("index"))
     tc.tc_set_timing(False)
     prop = props[-1][0]
-    prop_ms = statistics.median(ms for _, ms in props)
+    prop_call_ms = statistics.median(ms for _, ms in props)
+    # GPU time of the inference: its kernels (network, h, q and q-prefix; the
+    # guide of the q index), as the plain side counts its sampling kernels
+    prop_ms = statistics.median(a + b for a, b in zip(net_ms, guide_ms))
     # the network on the tensor cores: 2 (16 x 64 + 64 x 64 + 64) FLOP per edge
     flops = 2 * (16 * 64 + 64 * 64 + 64) * g.m
     tflops_peak = load_bf16_peak()
@@ -387,11 +392,15 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
                         "path": ("tcgen05.mma kind::f16 M128 N64 (TMEM accumulators, one issuing thread)"
                                  if tc.tc_mlp_kernel() == "tcgen05" else
                                  "mma.sync m16n8k16 bf16 (warp-level tensor-core MMA)")}
-    runs = []
+    runs, q_phase = [], []
+    tc.tc_set_timing(True)
     for i in range(4):
         r, ms = timed(lambda: tc.tc_sample_estimate_q(g, mot, delta, wts, prop, k, seed=0, offset=(50 + i) * k))
         runs.append((r, ms))
-    q_ms = statistics.median(ms for _, ms in runs[1:])
+        q_phase.append(tc.tc_last_phase_ms("order") + tc.tc_last_phase_ms("sample"))
+    tc.tc_set_timing(False)
+    q_call_ms = statistics.median(ms for _, ms in runs[1:])
+    q_ms = statistics.median(q_phase[1:])  # the key-order sort and sampling kernels, as plain_ms
     rq = runs[-1][0]
     var_plain = plain["std_err"] ** 2 * k
     var_learned = rq["std_err"] ** 2 * k
@@ -422,7 +431,8 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
     return {"variant": variant, "objective": objective, "inputs": 12 if variant == "as_written" else 16, "eps": eps,
             "train_samples": n_train, "stats_samples": n_stats,
             "setup_ms": {"features": feat_ms, "sample_statistics": sfeat_ms, "training": train_ms},
-            "inference_ms": prop_ms, "inference_phases": inference_phases, "sampler_ms": q_ms,
+            "inference_ms": prop_ms, "inference_call_ms": prop_call_ms, "inference_phases": inference_phases,
+            "sampler_ms": q_ms, "sampler_call_ms": q_call_ms,
             "samples_per_s": k / (q_ms / 1e3),
             "loss_first_batch": losses[0], "loss_last_batch": losses[1],
             "estimate": c, "std_err": rq["std_err"], "plain_estimate": plain["estimate"],
@@ -711,7 +721,7 @@ def main():
     weights = {"ms": ph["weights"], "alg_bytes_per_edge": {"a1": a1, "a2": 16}, "alg_bytes": a12,
                "achieved_gbs": a12 / (ph["weights"] / 1e3) / 1e9,
                "frac": a12 / (ph["weights"] / 1e3) / 1e9 / peak, "peak": peak, "peak_kind": peak_kind,
-               "dram_bytes_per_edge": wtr,
+               "dram_bytes_per_edge": wtr, "kernel": "k_weights_rw, then the scan of w (k_tile_scan)",
                "index_ms": ph["index"], "order_ms": ph["order"], "sample_ms": ph["sample"]}
 
     # end to end through the host entry point, pinned host buffers

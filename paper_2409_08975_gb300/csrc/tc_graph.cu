@@ -117,13 +117,22 @@ __global__ void k_tile_scan(const T* in, uint64_t n, const T* __restrict__ offse
                             uint32_t* err) {
   __shared__ T s_warp[kScanThreads / 32 + 1];
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  // a thread's items as 16-byte loads when they are whole and aligned
+  const bool vec = base + kScanItems <= n && ((reinterpret_cast<uintptr_t>(in + base) |
+                                               reinterpret_cast<uintptr_t>(out + base)) & 15) == 0;
   T v[kScanItems];
+  if (vec) {
+#pragma unroll
+    for (int j = 0; j < (int)(kScanItems * sizeof(T) / 16); j++)
+      reinterpret_cast<uint4*>(v)[j] = __ldcs(reinterpret_cast<const uint4*>(in + base) + j);
+  } else {
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++) v[j] = base + j < n ? in[base + j] : T(0);
+  }
   T acc = 0;
   bool ovf = false;
 #pragma unroll
   for (int j = 0; j < kScanItems; j++) {
-    const uint64_t i = base + j;
-    v[j] = i < n ? in[i] : T(0);
     const T s = acc + v[j];
     if (s < acc) ovf = true;
     acc = s;
@@ -137,10 +146,19 @@ __global__ void k_tile_scan(const T* in, uint64_t n, const T* __restrict__ offse
   T ex = block_exclusive_scan<T>(acc, s_warp, &total);
   T run = off + ex;
 #pragma unroll
-  for (int j = 0; j < kScanItems; j++) {
-    const uint64_t i = base + j;
-    if (i < n) out[i] = run;
-    run += v[j];
+  for (int j = 0; j < kScanItems; j++) {  // the exclusive prefix in place of the items
+    const T x = v[j];
+    v[j] = run;
+    run += x;
+  }
+  if (vec) {
+#pragma unroll
+    for (int j = 0; j < (int)(kScanItems * sizeof(T) / 16); j++)
+      reinterpret_cast<uint4*>(out + base)[j] = reinterpret_cast<const uint4*>(v)[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < kScanItems; j++)
+      if (base + j < n) out[base + j] = v[j];
   }
   if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
 }

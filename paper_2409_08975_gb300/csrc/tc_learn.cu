@@ -810,10 +810,13 @@ __global__ void __launch_bounds__(kUmmaM, kUmmaBlocksPerSm) k_mlp_umma(const flo
   const uint32_t a1 = smem_u32(S.A1), b1 = smem_u32(S.B1), a2 = smem_u32(S.A2), b2 = smem_u32(S.B2);
   uint32_t parity = 0, err = 0, hlo = 0xFFFFFFFFu, hhi = 0;
   bool ok = true;
-  const uint64_t T = (n + kUmmaTile - 1) / kUmmaTile;
+  // a block's unit of work: a 2048-row scan tile (proposal) or one 128-row
+  // sub-tile (logits, so that small row sets still spread over the SMs)
+  constexpr uint64_t kTile = Proposal ? kUmmaTile : kUmmaM;
+  const uint64_t T = (n + kTile - 1) / kTile;
   for (uint64_t tile = blockIdx.x; tile < T && ok; tile += gridDim.x) {
-    const uint64_t base = tile * kUmmaTile;
-    const uint32_t trows = (uint32_t)(n - base < kUmmaTile ? n - base : kUmmaTile);
+    const uint64_t base = tile * kTile;
+    const uint32_t trows = (uint32_t)(n - base < kTile ? n - base : kTile);
     // the rows that go through the network: every row of the tile (logits),
     // or the rows with w > 0, listed in order (proposal)
     uint32_t nrun = trows;
@@ -843,17 +846,26 @@ __global__ void __launch_bounds__(kUmmaM, kUmmaBlocksPerSm) k_mlp_umma(const flo
       __syncthreads();
     }
     unsigned long long tsum = 0;
+    // this thread's feature row of a sub-tile (zero past the rows to run); the
+    // next sub-tile's row is loaded while the current one is on the tensor cores
+    auto fetch = [&](uint32_t at, uint4& lo, uint4& hi) {
+      lo = hi = make_uint4(0, 0, 0, 0);
+      if (at < nrun) {
+        const uint64_t r = base + (Proposal ? (uint32_t)S.live[at] : at);
+        const uint4* src = reinterpret_cast<const uint4*>(feat + (uint64_t)(rows ? rows[r] : r) * kF);
+        lo = __ldg(src);
+        hi = __ldg(src + 1);
+      }
+    };
+    uint4 nlo, nhi;
+    fetch(tid, nlo, nhi);
     for (uint32_t r0 = 0; r0 < nrun && ok; r0 += kUmmaM) {  // 128-row sub-tiles
       const uint32_t idx = r0 + tid;
       const bool valid = idx < nrun;
       const uint32_t local = Proposal ? (valid ? (uint32_t)S.live[idx] : 0u) : idx;
       const uint64_t row = base + local;
-      uint4 xlo = make_uint4(0, 0, 0, 0), xhi = xlo;
-      if (valid) {
-        const uint4* src = reinterpret_cast<const uint4*>(feat + (uint64_t)(rows ? rows[row] : row) * kF);
-        xlo = __ldg(src);
-        xhi = __ldg(src + 1);
-      }
+      const uint4 xlo = nlo, xhi = nhi;
+      fetch(idx + kUmmaM, nlo, nhi);
       *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.A1) + umma_offset(tid, 0, kF)) = xlo;
       *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.A1) + umma_offset(tid, 8, kF)) = xhi;
       fence_async_smem();
@@ -865,7 +877,8 @@ __global__ void __launch_bounds__(kUmmaM, kUmmaBlocksPerSm) k_mlp_umma(const flo
         umma_bf16(tmem, umma_desc(a1, 16 * kF), umma_desc(b1, 16 * kF), false);
         umma_commit(&S.mbar);
       }
-      ok = __syncthreads_and(umma_wait(&S.mbar, parity));
+      // one thread polls the barrier; the others wait at the block barrier
+      ok = __syncthreads_and(tid != 0 || umma_wait(&S.mbar, parity));
       if (!ok) break;  // parity stays that of the phase still pending
       parity ^= 1;
       tc05_fence_after();
@@ -896,7 +909,8 @@ __global__ void __launch_bounds__(kUmmaM, kUmmaBlocksPerSm) k_mlp_umma(const flo
           umma_bf16(tmem, umma_desc(a2 + kk * 256, 16 * kH), umma_desc(b2 + kk * 256, 16 * kH), kk > 0);
         umma_commit(&S.mbar);
       }
-      ok = __syncthreads_and(umma_wait(&S.mbar, parity));
+      // one thread polls the barrier; the others wait at the block barrier
+      ok = __syncthreads_and(tid != 0 || umma_wait(&S.mbar, parity));
       if (!ok) break;  // parity stays that of the phase still pending
       parity ^= 1;
       tc05_fence_after();
@@ -1007,16 +1021,40 @@ constexpr int kTrainWarps = 4;
 #endif
 constexpr int kTrainRows = 16 * kTrainWarps;
 
+// Row strides of the backward's per-row arrays (FP32), padded so that the
+// TF32 fragment loads of a warp fall in distinct banks or at worst pairs.
+constexpr int kXS = kF + 4, kAS = kH + 4;
+
 struct TrainShared {
   MlpShared net;
-  float x[kTrainRows][kF];
-  float a1[kTrainRows][kH];
-  float a2[kTrainRows][kH];
-  float dz1[kTrainRows][kH];
-  float dz2[kTrainRows][kH];
+  float x[kTrainRows][kXS];
+  float a1[kTrainRows][kAS];
+  float a2[kTrainRows][kAS];
+  float dz1[kTrainRows][kAS];
+  float dz2[kTrainRows][kAS];
   float dz3[kTrainRows];
   float loss[kTrainWarps];
 };
+
+// D += A B on the tensor cores with TF32 operands (FP32 values rounded to
+// TF32, nearest with ties away) and FP32 accumulation, m16n8k8.  Fragment
+// layout (g = lane / 4, q = lane % 4): A (16 x 8, row-major) (g, q),
+// (g + 8, q), (g, q + 4), (g + 8, q + 4); B (8 x 8) (k = q, n = g),
+// (k = q + 4, n = g); C (16 x 8) as the m16n8k16 tile: (g, 2q), (g, 2q + 1),
+// (g + 8, 2q), (g + 8, 2q + 1).
+__device__ __forceinline__ uint32_t tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
 
 // Estimator-variance objective over a batch of n rows: with h_i = eps + g_i,
 // g_i = sigmoid(z_i), the per-sample second moment of the estimate under the
@@ -1078,10 +1116,16 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_mlp_grad(const float* __re
   TrainShared& S = *reinterpret_cast<TrainShared*>(smem_raw);
   load_mlp_shared(S.net, params);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
-  constexpr int kOwn = (kNParams + 32 * kTrainWarps - 1) / (32 * kTrainWarps);
-  float acc[kOwn];
+  // parameter gradients held across the block's row tiles: warp w owns the
+  // rows n = 16 w .. 16 w + 15 of dW2 (8 column tiles) and of dW1 (2 column
+  // tiles) in C-fragment layout; thread t owns db1[t] (t < 64) or db2[t - 64],
+  // and dW3[t] (t < 64) or db3 (t = 64)
+  float gw2[8][4], gw1[2][4];
 #pragma unroll
-  for (int j = 0; j < kOwn; j++) acc[j] = 0.f;
+  for (int j = 0; j < 8; j++) gw2[j][0] = gw2[j][1] = gw2[j][2] = gw2[j][3] = 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; j++) gw1[j][0] = gw1[j][1] = gw1[j][2] = gw1[j][3] = 0.f;
+  float gb = 0.f, g3 = 0.f;
   float loss_acc = 0.f;
   __syncthreads();
   for (uint64_t base = (uint64_t)blockIdx.x * kTrainRows; base < n; base += (uint64_t)gridDim.x * kTrainRows) {
@@ -1107,7 +1151,8 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_mlp_grad(const float* __re
       auto loss = [&](float z, float y) { return y > 0.f ? y * softplus(-z) : softplus(z); };
       if (!given_dz) loss_acc += (va ? loss(T.z3g, ya) : 0.f) + (vb ? loss(T.z3g8, yb) : 0.f);
     }
-    // inputs and activations of the rows (bf16 values held as FP32)
+    // inputs and activations of the rows (bf16 values held as FP32), and
+    // dz2 = dz3 W3 [z2 > 0]
     {
       const __nv_bfloat162* xa = reinterpret_cast<const __nv_bfloat162*>(x);
       S.x[ra][2 * q] = __low2float(xa[0]);
@@ -1125,60 +1170,93 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_mlp_grad(const float* __re
 #pragma unroll
       for (int r = 0; r < 4; r++) {
         const int row = r < 2 ? ra : rb, col = c0 + (r & 1);
-        const float z1 = T.z1[j][r], z2 = T.z2[j][r];
-        S.a1[row][col] = __bfloat162float(__float2bfloat16_rn(fmaxf(z1, 0.f)));
+        const float z2 = T.z2[j][r];
+        S.a1[row][col] = __bfloat162float(__float2bfloat16_rn(fmaxf(T.z1[j][r], 0.f)));
         S.a2[row][col] = __bfloat162float(__float2bfloat16_rn(fmaxf(z2, 0.f)));
-        const float dz3 = r < 2 ? dza : dzb;
-        S.dz2[row][col] = z2 > 0.f ? dz3 * S.net.W3[col] : 0.f;
-        S.dz1[row][col] = z1 > 0.f ? 1.f : 0.f;  // mask; completed below
+        S.dz2[row][col] = z2 > 0.f ? (r < 2 ? dza : dzb) * S.net.W3[col] : 0.f;
       }
     }
     __syncwarp();
-    // dz1[row][k] *= sum_n dz2[row][n] W2[n][k]: lane owns columns k = lane, lane + 32
-    for (int rr = 0; rr < 16; rr++) {
-      const int row = warp * 16 + rr;
+    // dz1 = (dz2 W2) [z1 > 0] for the warp's 16 rows on the tensor cores:
+    // [16 x 64] (dz2) x [64 x 64] (W2 as (n, k), the layer's bf16 weights)
+    {
+      const int r0 = warp * 16;
+      float d[8][4];
 #pragma unroll
-      for (int h2 = 0; h2 < 2; h2++) {
-        const int k = lane + 32 * h2;
-        float s = 0.f;
-#pragma unroll 8
-        for (int nn = 0; nn < kH; nn++) s += S.dz2[row][nn] * __bfloat162float(S.net.W2T[k * kW2TS + nn]);
-        S.dz1[row][k] *= s;
+      for (int j = 0; j < 8; j++) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 8; kk++) {  // n = 8 kk .. 8 kk + 7
+        const uint32_t a0 = tf32(S.dz2[r0 + g][8 * kk + q]), a1 = tf32(S.dz2[r0 + g + 8][8 * kk + q]);
+        const uint32_t a2 = tf32(S.dz2[r0 + g][8 * kk + q + 4]), a3 = tf32(S.dz2[r0 + g + 8][8 * kk + q + 4]);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {  // k = 8 j .. 8 j + 7: B(n, k) = W2[n][k], exact in TF32
+          const uint32_t b0 = __float_as_uint(__bfloat162float(S.net.W2[(8 * kk + q) * kW2S + 8 * j + g]));
+          const uint32_t b1 = __float_as_uint(__bfloat162float(S.net.W2[(8 * kk + q + 4) * kW2S + 8 * j + g]));
+          mma_tf32(d[j], a0, a1, a2, a3, b0, b1);
+        }
       }
+#pragma unroll
+      for (int j = 0; j < 8; j++)
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          const int row = r < 2 ? ra : rb, col = j * 8 + 2 * q + (r & 1);
+          S.dz1[row][col] = T.z1[j][r] > 0.f ? d[j][r] : 0.f;
+        }
     }
     __syncthreads();
-    // ---- block: accumulate the owned parameters over the block's rows
+    // ---- block: the parameter gradients over the block's 64 rows
+    {
+      const int m0 = warp * 16;  // this warp's rows n of dW2 and dW1
 #pragma unroll
-    for (int j = 0; j < kOwn; j++) {
-      const int p = threadIdx.x + j * 32 * kTrainWarps;
-      if (p >= kNParams) break;
-      float s = 0.f;
-      if (p < kOffB1) {
-        const int nn = p / kF, k = p % kF;
-        for (int r = 0; r < kTrainRows; r++) s += S.dz1[r][nn] * S.x[r][k];
-      } else if (p < kOffW2) {
-        const int nn = p - kOffB1;
-        for (int r = 0; r < kTrainRows; r++) s += S.dz1[r][nn];
-      } else if (p < kOffB2) {
-        const int nn = (p - kOffW2) / kH, k = (p - kOffW2) % kH;
-        for (int r = 0; r < kTrainRows; r++) s += S.dz2[r][nn] * S.a1[r][k];
-      } else if (p < kOffW3) {
-        const int nn = p - kOffB2;
-        for (int r = 0; r < kTrainRows; r++) s += S.dz2[r][nn];
-      } else if (p < kOffB3) {
-        const int k = p - kOffW3;
-        for (int r = 0; r < kTrainRows; r++) s += S.dz3[r] * S.a2[r][k];
-      } else {
-        for (int r = 0; r < kTrainRows; r++) s += S.dz3[r];
+      for (int kk = 0; kk < kTrainRows / 8; kk++) {  // rows 8 kk .. 8 kk + 7
+        const int rq = 8 * kk + q, rq4 = rq + 4;
+        // dW2[n][k] += sum_row dz2[row][n] a1[row][k]: A(n, row) = dz2[row][n]
+        const uint32_t a0 = tf32(S.dz2[rq][m0 + g]), a1 = tf32(S.dz2[rq][m0 + g + 8]);
+        const uint32_t a2 = tf32(S.dz2[rq4][m0 + g]), a3 = tf32(S.dz2[rq4][m0 + g + 8]);
+#pragma unroll
+        for (int j = 0; j < 8; j++)  // a1 values are bf16, exact in TF32
+          mma_tf32(gw2[j], a0, a1, a2, a3, __float_as_uint(S.a1[rq][8 * j + g]),
+                   __float_as_uint(S.a1[rq4][8 * j + g]));
+        // dW1[n][k] += sum_row dz1[row][n] x[row][k]
+        const uint32_t c0 = tf32(S.dz1[rq][m0 + g]), c1 = tf32(S.dz1[rq][m0 + g + 8]);
+        const uint32_t c2 = tf32(S.dz1[rq4][m0 + g]), c3 = tf32(S.dz1[rq4][m0 + g + 8]);
+#pragma unroll
+        for (int j = 0; j < 2; j++)
+          mma_tf32(gw1[j], c0, c1, c2, c3, __float_as_uint(S.x[rq][8 * j + g]), __float_as_uint(S.x[rq4][8 * j + g]));
       }
-      acc[j] += s;
+      // the biases and the last layer: sums over the rows (FP32)
+      const int t = threadIdx.x;
+      float sb = 0.f, s3 = 0.f;
+      for (int r = 0; r < kTrainRows; r++) {
+        sb += t < kH ? S.dz1[r][t] : S.dz2[r][t - kH];
+        if (t < kH) s3 += S.dz3[r] * S.a2[r][t];
+        else if (t == kH) s3 += S.dz3[r];
+      }
+      gb += sb;
+      g3 += s3;
     }
     __syncthreads();
   }
+  {
+    const int m0 = warp * 16;
 #pragma unroll
-  for (int j = 0; j < kOwn; j++) {
-    const int p = threadIdx.x + j * 32 * kTrainWarps;
-    if (p < kNParams) atomicAdd(grad + p, acc[j]);
+    for (int j = 0; j < 8; j++)
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const int nn = m0 + g + (r < 2 ? 0 : 8), k = 8 * j + 2 * q + (r & 1);
+        atomicAdd(grad + kOffW2 + nn * kH + k, gw2[j][r]);
+      }
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const int nn = m0 + g + (r < 2 ? 0 : 8), k = 8 * j + 2 * q + (r & 1);
+        atomicAdd(grad + kOffW1 + nn * kF + k, gw1[j][r]);
+      }
+    const int t = threadIdx.x;
+    atomicAdd(grad + (t < kH ? kOffB1 + t : kOffB2 + (t - kH)), gb);
+    if (t < kH) atomicAdd(grad + kOffW3 + t, g3);
+    else if (t == kH) atomicAdd(grad + kOffB3, g3);
   }
   for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
   if (lane == 0) S.loss[warp] = loss_acc;
@@ -1376,7 +1454,7 @@ static tc_status launch_umma(const tc_mlp* M, const uint16_t* feat, const uint32
   }
   // kUmmaBlocksPerSm blocks per SM: what the launch bounds' registers and the
   // shared memory allow (their TMEM, 64 columns each, fits an SM's 512)
-  const uint64_t T = (n + kUmmaTile - 1) / kUmmaTile;
+  const uint64_t T = Proposal ? (n + kUmmaTile - 1) / kUmmaTile : (n + kUmmaM - 1) / kUmmaM;
   uint64_t blocks = (uint64_t)num_sms() * kUmmaBlocksPerSm;
   if (blocks > T) blocks = T;
   k_mlp_umma<Proposal><<<(unsigned)blocks, kUmmaM, kUmmaSmemBytes, st>>>(

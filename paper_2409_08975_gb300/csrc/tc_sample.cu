@@ -212,12 +212,19 @@ __global__ void __launch_bounds__(kWThreads, TC_WEIGHTS_MIN_BLOCKS) k_weights(co
 // list [s, f) from the anchor's range word rw (the offsets of x's list are
 // read only where a field is saturated).  exact: a is the list's lower bound
 // of t (x_in, x_out), so "time >= t" needs no probe.
-__device__ __forceinline__ void side_window_rw(const WeightsArgs& A, int alpha, int beta, int32_t x, uint32_t a,
-                                               uint32_t rw, bool exact, int64_t t, uint32_t* lo, uint32_t* hi) {
+// The vertex x (the edge's source, or its destination when dst_side) is
+// read from the edge record only then.
+__device__ __forceinline__ void side_window_rw(const WeightsArgs& A, int alpha, int beta, uint64_t i, bool dst_side,
+                                               uint32_t a, uint32_t rw, bool exact, int64_t t, uint32_t* lo,
+                                               uint32_t* hi) {
   const uint32_t* off = alpha < 0 ? A.in_off : A.out_off;
   uint32_t s = a - (rw >> 16), f = a + (rw & 0xFFFFu);
-  if ((rw >> 16) == kRangeCap) s = __ldg(off + x);
-  if ((rw & 0xFFFFu) == kRangeCap) f = __ldg(off + x + 1);
+  if ((rw >> 16) == kRangeCap || (rw & 0xFFFFu) == kRangeCap) {
+    const int2 sd = __ldg(reinterpret_cast<const int2*>(A.out_e + i));  // (src, dst)
+    const int32_t x = dst_side ? sd.y : sd.x;
+    if ((rw >> 16) == kRangeCap) s = __ldg(off + x);
+    if ((rw & 0xFFFFu) == kRangeCap) f = __ldg(off + x + 1);
+  }
   const uint32_t* t32 = alpha < 0 ? A.in_t32 : A.out_t32;
   auto tt = [&](uint32_t p) -> int64_t { return (int64_t)__ldg(t32 + p) + A.tmin; };
   if (beta < 0) {
@@ -230,7 +237,8 @@ __device__ __forceinline__ void side_window_rw(const WeightsArgs& A, int alpha, 
 }
 
 // Block b takes tile b (coalesced: edge b kWTile + j 256 + thread) on the
-// 32-bit list times: the list bounds from the anchors' range words (the
+// 32-bit list times: the edge's time from the 32-bit out-list times, the
+// list bounds from the anchors' range words (the edge record and the
 // offsets are read only where a word is saturated), an exact anchor's
 // bound without a probe, the windows and w written with streaming stores,
 // and the tile's sum of w.
@@ -246,18 +254,18 @@ __global__ void __launch_bounds__(kWThreads, TC_WEIGHTS_MIN_BLOCKS) k_weights_rw
   for (int j = 0; j < kWItems; j++) {
     const uint64_t i = base + (uint64_t)j * kWThreads + tid;
     if (i >= A.m) break;
-    const OutEdge e = A.out_e[i];
+    const int64_t t = (int64_t)__ldg(A.out_t32 + i) + A.tmin;  // the edge's time (4 bytes, not the record)
     uint32_t lo1 = 0, hi1 = 1, lo3 = 0, hi3 = 1;
     // anchors: u's in-list (x_in, exact) or the edge itself in u's out-list;
     // the edge itself in v's in-list (out2in) or v's out-list (x_out, exact)
     if (A.alpha1 < 0)
-      side_window_rw(A, -1, A.beta1, e.src, __ldg(A.x_in + i), __ldg(A.r_in + i), true, e.t, &lo1, &hi1);
+      side_window_rw(A, -1, A.beta1, i, false, __ldg(A.x_in + i), __ldg(A.r_in + i), true, t, &lo1, &hi1);
     else if (A.alpha1 > 0)
-      side_window_rw(A, 1, A.beta1, e.src, (uint32_t)i, __ldg(A.r_self + i), false, e.t, &lo1, &hi1);
+      side_window_rw(A, 1, A.beta1, i, false, (uint32_t)i, __ldg(A.r_self + i), false, t, &lo1, &hi1);
     if (A.alpha3 < 0)
-      side_window_rw(A, -1, A.beta3, e.dst, __ldg(A.out2in + i), __ldg(A.r_o2i + i), false, e.t, &lo3, &hi3);
+      side_window_rw(A, -1, A.beta3, i, true, __ldg(A.out2in + i), __ldg(A.r_o2i + i), false, t, &lo3, &hi3);
     else if (A.alpha3 > 0)
-      side_window_rw(A, 1, A.beta3, e.dst, __ldg(A.x_out + i), __ldg(A.r_out + i), true, e.t, &lo3, &hi3);
+      side_window_rw(A, 1, A.beta3, i, true, __ldg(A.x_out + i), __ldg(A.r_out + i), true, t, &lo3, &hi3);
     __stcs(reinterpret_cast<uint4*>(A.win + i), make_uint4(lo1, hi1 - lo1, lo3, hi3 - lo3));
     const unsigned long long wv = (unsigned long long)(hi1 - lo1) * (unsigned long long)(hi3 - lo3);
     __stcs(reinterpret_cast<unsigned long long*>(A.w + i), wv);
