@@ -51,8 +51,8 @@ MOTIF_NAMES = {str(v): k for k, v in MOTIFS.items()}
 # pass over the default workload's list build and five steps: the launch list
 # summarised in profiles/launch_list_large_bench.md); valid while the kernel
 # is unchanged, null for workloads not captured
-SAMPLER_TRAFFIC_PER_SAMPLE = {("large", "c4"): 73.33}   # k_sample
-WEIGHTS_TRAFFIC_PER_EDGE = {("large", "c4"): 83.13}     # k_weights_rw
+SAMPLER_TRAFFIC_PER_SAMPLE = {("large", "c4"): 76.3}   # k_sample
+WEIGHTS_TRAFFIC_PER_EDGE = {("large", "c4"): 89.9}     # k_weights_rw 74.1 + the scan of w 15.8
 UNIT = "samples/s"
 SECTOR = 32
 LEARNED_VARIANTS = ("closure", "variance", "as_written")

@@ -242,7 +242,8 @@ __device__ __forceinline__ void side_window_rw(const WeightsArgs& A, int alpha, 
 // offsets are read only where a word is saturated), an exact anchor's
 // bound without a probe, the windows and w written with streaming stores,
 // and the tile's sum of w.
-__global__ void __launch_bounds__(kWThreads, TC_WEIGHTS_MIN_BLOCKS) k_weights_rw(const __grid_constant__ WeightsArgs A) {
+__global__ void __launch_bounds__(kWThreads, TC_WEIGHTS_MIN_BLOCKS)
+    k_weights_rw(const __grid_constant__ WeightsArgs A) {
   __shared__ unsigned long long s_warp[kWThreads / 32];
   __shared__ uint32_t s_ovf;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -838,7 +839,7 @@ __device__ __forceinline__ bool bounded_draw_slow(uint64_t seed, uint64_t s, uin
 }
 
 // One sample (Alg. 2, 3): sample index i within the call (id offset + i).
-constexpr uint32_t kSmemBins = 1024;  // per-block bins of the proposal sampler (see k_sample)
+constexpr uint32_t kSmemBins = 1088;  // per-block bins of the proposal sampler (see k_sample): the 1,025 h of S = 1024
 constexpr size_t kSmemBinBytes = 3 * sizeof(unsigned long long) * kSmemBins;
 
 // Adds X and X^2 to bin h: three 64-bit words (sum X, sum X^2 low, high).
@@ -936,7 +937,7 @@ __global__ void __launch_bounds__(256, TC_SAMPLE_MIN_BLOCKS) k_sample(const __gr
   bool local_bins = false;
   if (A.h && A.hrange) {
     hmin = A.hrange[0];
-    local_bins = A.hrange[1] >= hmin && A.hrange[1] - hmin < kSmemBins;
+    local_bins = A.hrange[1] >= hmin;  // h beyond hmin + kSmemBins - 1 (a wider range) goes to the global bins
     if (local_bins)
       for (uint32_t b = threadIdx.x; b < 3 * kSmemBins; b += blockDim.x) s_bins[b] = 0;
   }
