@@ -382,10 +382,17 @@ def learned_comparison(tc, g, mot, delta, wts, k, plain, plain_ms, weights_ms, n
     # guide of the q index), as the plain side counts its sampling kernels
     prop_ms = statistics.median(a + b for a, b in zip(net_ms, guide_ms))
     # the network on the tensor cores: 2 (16 x 64 + 64 x 64 + 64) FLOP per edge
-    flops = 2 * (16 * 64 + 64 * 64 + 64) * g.m
+    # with w > 0 (the proposal runs only those; counted here from the prefix)
+    live = int(torch.count_nonzero(wts.prefix[1:g.m + 1] != wts.prefix[:g.m]).item())
+    flops = 2 * (16 * 64 + 64 * 64 + 64) * live
     tflops_peak = load_bf16_peak()
     net = statistics.median(net_ms)
+    # the inference's HBM bytes: per edge the prefix entry read (8), h and q
+    # written (2 + 8), the q-prefix scan (16); per live edge its feature row (32)
+    hbm_bytes = (8 + 2 + 8 + 16) * g.m + 32 * live
     inference_phases = {"network_h_q_prefix_ms": net, "guide_ms": statistics.median(guide_ms),
+                        "live_edges": live, "hbm_gbs": hbm_bytes / (net / 1e3) / 1e9 if net > 0 else None,
+                        "frac_of_hbm": hbm_bytes / (net / 1e3) / 1e9 / load_peaks()[0] if net > 0 else None,
                         "tensor_tflops": flops / (net / 1e3) / 1e12 if net > 0 else None,
                         "bf16_peak_tflops": tflops_peak,
                         "frac_of_bf16_peak": flops / (net / 1e3) / 1e12 / tflops_peak if net > 0 else None,
