@@ -469,7 +469,7 @@ def config_dict(cfg, k, world):
             "delta": int(cfg["delta"]),
             "k": int(k), "seed": 0, "parallelism": "dp%d (sample-id ranges)" % world,
             "l2": "inputs larger than L2: resident graph lists ~%.1f GB, sampling index %.1f GB, prefix %.1f GB "
-                  "(L2 129 MB); no flush between steps" % (60e-9 * m, 32e-9 * m, 8e-9 * m)}
+                  "(L2 129 MB); no flush between steps" % (110e-9 * m, 23e-9 * m, 8e-9 * m)}
 
 
 def run_batch(args, rank, world, local):
